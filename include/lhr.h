@@ -1,0 +1,205 @@
+/*
+ * lhr.h -- C ABI of the GB300 library for hierarchical panoramic-feature
+ * retrieval and 2-D multi-frame candidate aggregation (indoor localization,
+ * arXiv 2006.08861).
+ *
+ * The paper states the problem this interface follows:
+ *   - a server-side database of landmark features, each tied to floor-plan
+ *     coordinates by a geo-referenced table made while modelling (§3, §3.2);
+ *     the database may be divided into n_s subspaces, e.g. one per floor,
+ *     searched independently (§3.1);
+ *   - a localization request of M frames: q_m plus (M-1)/2 frames before and
+ *     after it (§3.1, Algorithm 1 "selectNearbyFrames");
+ *   - each frame is compared with every database frame by Euclidean distance
+ *     and its top N candidates are kept, per subspace (§3.1, Algorithm 1
+ *     "calculateDistance", "selectTopCandidates"; §4);
+ *   - the candidates of all M frames are fused into one floor-plan position by
+ *     tile-density aggregation (§3.2, Algorithm 2).
+ *
+ * Conventions (every entry point):
+ *   - Array arguments are DEVICE pointers owned by the caller unless the
+ *     argument says otherwise; the library never frees caller memory.
+ *   - Calls are asynchronous on `cuda_stream` (a cudaStream_t; NULL = the
+ *     legacy default stream) unless stated otherwise. Output arrays are valid
+ *     once that stream reaches the end of the call's work.
+ *   - Distances are SQUARED Euclidean distances (same order as Euclidean).
+ *   - Top-N lists are ascending by (distance, database row): ties go to the
+ *     lower row. A list longer than its subspace is padded with row -1 and
+ *     distance +inf.
+ *   - Argument errors are found on the host before any launch and return
+ *     LHR_ERR_INVALID_ARG (nothing is launched, outputs are untouched).
+ *     CUDA launch / allocation failures return LHR_ERR_CUDA / LHR_ERR_OOM.
+ *     No C++ exception crosses this interface. lhr_last_error() returns a
+ *     thread-local description of the last non-OK return.
+ *   - Device-side waits are bounded; a wait that gives up records
+ *     LHR_ERR_TIMEOUT in the database's error word (see lhr_db_error).
+ */
+#ifndef LHR_H
+#define LHR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lhr_db lhr_db; /* opaque; owns every device buffer it allocates */
+
+typedef enum {
+    LHR_OK = 0,
+    LHR_WARN_LOW_CONFIDENCE = 1, /* per-window status: no TopC tile passed the threshold */
+    LHR_ERR_INVALID_ARG = -1,
+    LHR_ERR_CUDA = -2,
+    LHR_ERR_OOM = -3,
+    LHR_ERR_TIMEOUT = -4,
+    LHR_ERR_UNSUPPORTED = -5
+} lhr_status;
+
+typedef enum { LHR_F32 = 0, LHR_BF16 = 1, LHR_FP8_E4M3 = 2 } lhr_dtype;
+
+typedef enum {
+    LHR_AGG_TILE = 0,          /* Algorithm 2: centre of the winning 2-D tile */
+    LHR_AGG_TILE_CENTROID = 1, /* mean position of the candidates in the winning tile's circle */
+    LHR_AGG_SOFTMAX = 2        /* sum_i p_i xy_i, p = softmax(-d_i / tau) over the window */
+} lhr_agg_mode;
+
+/* Low-precision copies to build (bit mask for lhr_db_config.lowp). */
+#define LHR_LOWP_BF16 1u
+#define LHR_LOWP_FP8 2u
+
+typedef struct {
+    int32_t dim;        /* D: feature length, 4 <= D <= 512, D % 4 == 0 */
+    int32_t coarse_dim; /* Dc: prefix length of the coarse level; 0 = none; else 4 <= Dc <= D, Dc % 4 == 0 */
+    uint32_t lowp;      /* LHR_LOWP_* copies to build (need D % 32 == 0, D <= 512) */
+    int32_t reserved;   /* must be 0 */
+    double tile_m;      /* floor-plan tile edge in metres (paper: 0.30); > 0 */
+} lhr_db_config;
+
+typedef struct {
+    int32_t k;            /* N of "top N" per frame and subspace: 1 <= k <= 32 */
+    int32_t shortlist;    /* 0: exhaustive scan; S > 0: coarse-to-fine with an S-row shortlist (k <= S <= 4096) */
+    lhr_dtype score;      /* LHR_F32: direct FP32 distances; LHR_BF16 / LHR_FP8_E4M3: tensor-core scores */
+    int32_t rerank_width; /* low-precision scores only: W rows kept per query and re-ranked in FP32 (k <= W <= 128) */
+} lhr_query_params;
+
+typedef struct {
+    lhr_agg_mode mode;
+    int32_t top_c;     /* TopC tiles tested (paper: 10); >= 1 */
+    double radius_m;   /* tolerance-circle radius in metres (paper: 3.0); >= 0 */
+    int32_t toler_pct; /* tolerPer in percent (paper: 20); 0..100 */
+    float tau;         /* softmax temperature (LHR_AGG_SOFTMAX only); > 0 */
+} lhr_agg_params;
+
+/*
+ * lhr_build_db -- environment modelling (§3: every landmark is one feature,
+ * stored server-side; §3.2: the geo-referenced index -> floor-plan table).
+ *
+ *   feats    n x D float32, row-major; host or device memory (detected).
+ *            Every value must be finite.
+ *   xy       n x 2 float64 floor-plan coordinates (x west->east, y
+ *            south->north, metres); host or device memory.
+ *   subspace n int32 subspace ids in [0, n_s) (§3.1 "subspaces"), host or
+ *            device; NULL = one subspace.
+ *   n        number of rows, 1 <= n < 2^31.
+ *   cfg      dimensions, coarse prefix, low-precision copies, tile edge.
+ *   out      receives the new handle; unchanged on error.
+ * The library copies everything it needs; the caller keeps ownership of its
+ * inputs. Synchronizes `cuda_stream` before returning.
+ */
+lhr_status lhr_build_db(const float* feats, const double* xy, const int32_t* subspace, int64_t n,
+                        const lhr_db_config* cfg, void* cuda_stream, lhr_db** out);
+
+/* Frees every device buffer of `db` (after synchronizing the device). NULL is a no-op. */
+lhr_status lhr_free_db(lhr_db* db);
+
+/* Shape of a database: rows, D, Dc, number of subspaces (any pointer may be NULL). */
+lhr_status lhr_db_info(const lhr_db* db, int64_t* n, int32_t* dim, int32_t* coarse_dim,
+                       int32_t* n_subspaces);
+
+/*
+ * lhr_query -- per-frame top-N retrieval (§3.1, Algorithm 1 steps
+ * "calculateDistance" and "selectTopCandidates"; §4 "smallest Euclidean
+ * distance", "top N").
+ *
+ *   q     nq x D float32 query frames (device), row-major, 16-byte aligned.
+ *   nq    number of frames, >= 1.
+ *   p     k, and the form: exhaustive FP32 (shortlist 0, score F32),
+ *         coarse-to-fine (shortlist S > 0, needs a database built with
+ *         coarse_dim > 0 and one subspace), or low-precision tensor-core
+ *         scores + FP32 re-rank (score BF16/FP8, needs that copy, one
+ *         subspace).
+ *   idx   nq x n_s x k int64 (device): database rows (caller's numbering).
+ *   dist  nq x n_s x k float32 (device): squared distances, FP32 direct form.
+ */
+lhr_status lhr_query(const lhr_db* db, const float* q, int32_t nq, const lhr_query_params* p,
+                     int64_t* idx, float* dist, void* cuda_stream);
+
+/*
+ * lhr_query_window -- the whole localization request: Algorithm 1 over every
+ * frame of every window, then Algorithm 2 per window (§3.1, §3.2).
+ *
+ *   frames   W x D float32 (device): the frames of all windows back to back.
+ *   offsets  nw + 1 int32 (device): window w holds frames
+ *            [offsets[w], offsets[w+1]); offsets[0] = 0, offsets[nw] = W,
+ *            non-decreasing. Window lengths may differ. A window that is
+ *            empty, reaches outside [0, W], or holds more than 8192
+ *            candidates (frames x n_s x k) gets status LHR_ERR_INVALID_ARG.
+ *   W        total number of frames (= offsets[nw]), >= 1.
+ *   nw       number of windows, >= 1.
+ *   p, a     retrieval and aggregation parameters.
+ *   idx/dist W x n_s x k (device): every frame's candidates, as lhr_query.
+ *   xy       nw x 2 float64 (device): the final position of each window.
+ *   status   nw int32 (device): LHR_OK, LHR_WARN_LOW_CONFIDENCE or an error.
+ */
+lhr_status lhr_query_window(const lhr_db* db, const float* frames, const int32_t* offsets, int32_t W,
+                            int32_t nw, const lhr_query_params* p, const lhr_agg_params* a,
+                            int64_t* idx, float* dist, double* xy, int32_t* status, void* cuda_stream);
+
+/*
+ * lhr_aggregate_2d -- Algorithm 2 alone (§3.2) on caller-supplied candidates.
+ *
+ *   idx           n_cand candidate rows (device int64); row -1 is padding and
+ *                 is skipped; any other row must be in [0, n) (a row outside
+ *                 is skipped and recorded as LHR_ERR_INVALID_ARG in the
+ *                 database's error word).
+ *   dist          n_cand candidate squared distances (device float32), read
+ *                 only in LHR_AGG_SOFTMAX mode (may be NULL otherwise).
+ *   n_cand        length of idx / dist, >= 1.
+ *   cand_offsets  nw + 1 int32 (device): window w owns candidates
+ *                 [cand_offsets[w], cand_offsets[w+1]); 1..8192 per window and
+ *                 inside [0, n_cand], else that window's status is
+ *                 LHR_ERR_INVALID_ARG.
+ *   xy, status    as lhr_query_window.
+ */
+lhr_status lhr_aggregate_2d(const lhr_db* db, const int64_t* idx, const float* dist, int64_t n_cand,
+                            const int32_t* cand_offsets, int32_t nw, const lhr_agg_params* a,
+                            double* xy, int32_t* status, void* cuda_stream);
+
+/*
+ * lhr_db_error -- reads and clears the database's device error word, which
+ * kernels set when a bounded device-side wait gives up (LHR_ERR_TIMEOUT) or a
+ * candidate row is out of range (LHR_ERR_INVALID_ARG). Synchronizes the stream.
+ * *err receives LHR_OK when nothing was recorded.
+ */
+lhr_status lhr_db_error(const lhr_db* db, int32_t* err, void* cuda_stream);
+
+/*
+ * Instrumentation (no counterpart in the paper): per-kernel CUDA-event timing.
+ * lhr_profile_enable(1) makes every later launch record an event pair on its
+ * stream around each kernel; lhr_profile_read synchronizes those events and
+ * returns, for kernels whose name contains `kernel` (NULL = all), the number
+ * of launches and their summed device time in milliseconds, then forgets them
+ * when `reset` is non-zero. Off by default; costs two event records per
+ * kernel when on. Process-wide.
+ */
+lhr_status lhr_profile_enable(int32_t on);
+lhr_status lhr_profile_read(const char* kernel, int64_t* launches, double* total_ms, int32_t reset);
+
+/* Thread-local message describing the last non-OK return on this thread. */
+const char* lhr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LHR_H */

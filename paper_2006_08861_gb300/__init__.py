@@ -1,0 +1,262 @@
+"""Python binding of liblhr.so (include/lhr.h): argument marshalling only.
+
+Every step of retrieval and aggregation runs in the library's CUDA kernels;
+this module passes pointers, sizes and torch's current CUDA stream. PyTorch
+supplies device memory and streams. There is no CPU fallback: if liblhr.so
+is missing or fails to load, import raises.
+
+Names follow the C ABI: lhr_build_db, lhr_query, lhr_query_window,
+lhr_aggregate_2d, lhr_db_error, lhr_last_error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblhr.so")
+
+LHR_OK = 0
+LHR_WARN_LOW_CONFIDENCE = 1
+LHR_ERR_INVALID_ARG = -1
+LHR_ERR_CUDA = -2
+LHR_ERR_OOM = -3
+LHR_ERR_TIMEOUT = -4
+LHR_ERR_UNSUPPORTED = -5
+
+LHR_F32, LHR_BF16, LHR_FP8_E4M3 = 0, 1, 2
+LHR_AGG_TILE, LHR_AGG_TILE_CENTROID, LHR_AGG_SOFTMAX = 0, 1, 2
+LHR_LOWP_BF16, LHR_LOWP_FP8 = 1, 2
+
+_SCORE = {"f32": LHR_F32, "bf16": LHR_BF16, "fp8": LHR_FP8_E4M3, "e4m3": LHR_FP8_E4M3}
+_MODE = {"tile": LHR_AGG_TILE, "centroid": LHR_AGG_TILE_CENTROID, "softmax": LHR_AGG_SOFTMAX}
+
+
+class DbConfig(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("coarse_dim", ctypes.c_int32), ("lowp", ctypes.c_uint32),
+                ("reserved", ctypes.c_int32), ("tile_m", ctypes.c_double)]
+
+
+class QueryParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("shortlist", ctypes.c_int32), ("score", ctypes.c_int32),
+                ("rerank_width", ctypes.c_int32)]
+
+
+class AggParams(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("top_c", ctypes.c_int32), ("radius_m", ctypes.c_double),
+                ("toler_pct", ctypes.c_int32), ("tau", ctypes.c_float)]
+
+
+class LhrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lhr status {status}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "(paper_2006_08861_gb300.build_ext.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "lhr_build_db": [P, P, P, I64, ctypes.POINTER(DbConfig), P, ctypes.POINTER(P)],
+        "lhr_free_db": [P],
+        "lhr_db_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)],
+        "lhr_query": [P, P, I32, ctypes.POINTER(QueryParams), P, P, P],
+        "lhr_query_window": [P, P, P, I32, I32, ctypes.POINTER(QueryParams), ctypes.POINTER(AggParams),
+                             P, P, P, P, P],
+        "lhr_aggregate_2d": [P, P, P, I64, P, I32, ctypes.POINTER(AggParams), P, P, P],
+        "lhr_db_error": [P, ctypes.POINTER(I32), P],
+        "lhr_profile_enable": [I32],
+        "lhr_profile_read": [ctypes.c_char_p, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double), I32],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.lhr_last_error.argtypes = []
+    lib.lhr_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def lhr_last_error() -> str:
+    return _lib.lhr_last_error().decode()
+
+
+def _check(st: int):
+    if st < 0:
+        raise LhrError(st, lhr_last_error())
+    return st
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _dev_tensor(x, dtype, name):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != dtype or not x.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    return x
+
+
+class Database:
+    """Owns an lhr_db handle (freed with the object)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        n, d, dc, ns = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.lhr_db_info(self._h, ctypes.byref(n), ctypes.byref(d), ctypes.byref(dc), ctypes.byref(ns)))
+        self.n, self.dim, self.coarse_dim, self.n_subspaces = n.value, d.value, dc.value, ns.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.lhr_free_db(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_or_dev(x, np_dtype, torch_dtype, name):
+    torch = _torch()
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch_dtype or not x.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous {torch_dtype} tensor")
+        return x
+    a = np.ascontiguousarray(x, dtype=np_dtype)
+    return a
+
+
+def lhr_build_db(feats, xy, subspace=None, coarse_dim: int = 0, lowp: int = 0, tile_m: float = 0.30,
+                 stream=None) -> Database:
+    """Builds a device database from features (n x D float32) and floor-plan
+    coordinates (n x 2 float64), host arrays or CUDA tensors."""
+    torch = _torch()
+    f = _host_or_dev(feats, np.float32, torch.float32, "feats")
+    c = _host_or_dev(xy, np.float64, torch.float64, "xy")
+    s = None if subspace is None else _host_or_dev(subspace, np.int32, torch.int32, "subspace")
+    n, dim = f.shape
+    cfg = DbConfig(dim, coarse_dim, lowp, 0, tile_m)
+    h = ctypes.c_void_p()
+    _check(_lib.lhr_build_db(_ptr(f), _ptr(c), _ptr(s), n, ctypes.byref(cfg), _stream(stream), ctypes.byref(h)))
+    return Database(h)
+
+
+def query_params(k: int, shortlist: int = 0, score: str = "f32", rerank_width: int = 64) -> QueryParams:
+    return QueryParams(k, shortlist, _SCORE[score], rerank_width)
+
+
+def agg_params(mode: str = "tile", top_c: int = 10, radius_m: float = 3.0, toler_pct: int = 20,
+               tau: float = 1.0) -> AggParams:
+    return AggParams(_MODE[mode], top_c, radius_m, toler_pct, tau)
+
+
+def lhr_query(db: Database, q, k: int, shortlist: int = 0, score: str = "f32", rerank_width: int = 64,
+              out=None, stream=None):
+    """Top-k rows per query frame: returns (idx int64 [nq, n_s, k], dist float32 [nq, n_s, k])."""
+    torch = _torch()
+    q = _dev_tensor(q, torch.float32, "q")
+    nq = q.shape[0]
+    if out is None:
+        idx = torch.empty((nq, db.n_subspaces, k), dtype=torch.int64, device=q.device)
+        dist = torch.empty((nq, db.n_subspaces, k), dtype=torch.float32, device=q.device)
+    else:
+        idx, dist = out
+    p = query_params(k, shortlist, score, rerank_width)
+    _check(_lib.lhr_query(db.handle, _ptr(q), nq, ctypes.byref(p), _ptr(idx), _ptr(dist), _stream(stream)))
+    return idx, dist
+
+
+def lhr_query_window(db: Database, frames, offsets, k: int, shortlist: int = 0, score: str = "f32",
+                     rerank_width: int = 64, mode: str = "tile", top_c: int = 10, radius_m: float = 3.0,
+                     toler_pct: int = 20, tau: float = 1.0, out=None, stream=None):
+    """Retrieval for every frame, then Algorithm 2 per window.
+    Returns (idx, dist, xy float64 [nw, 2], status int32 [nw])."""
+    torch = _torch()
+    frames = _dev_tensor(frames, torch.float32, "frames")
+    offsets = _dev_tensor(offsets, torch.int32, "offsets")
+    W, nw = frames.shape[0], offsets.shape[0] - 1
+    if out is None:
+        dev = frames.device
+        idx = torch.empty((W, db.n_subspaces, k), dtype=torch.int64, device=dev)
+        dist = torch.empty((W, db.n_subspaces, k), dtype=torch.float32, device=dev)
+        xy = torch.empty((nw, 2), dtype=torch.float64, device=dev)
+        status = torch.empty((nw,), dtype=torch.int32, device=dev)
+    else:
+        idx, dist, xy, status = out
+    p = query_params(k, shortlist, score, rerank_width)
+    a = agg_params(mode, top_c, radius_m, toler_pct, tau)
+    _check(_lib.lhr_query_window(db.handle, _ptr(frames), _ptr(offsets), W, nw, ctypes.byref(p), ctypes.byref(a),
+                                 _ptr(idx), _ptr(dist), _ptr(xy), _ptr(status), _stream(stream)))
+    return idx, dist, xy, status
+
+
+def lhr_aggregate_2d(db: Database, idx, cand_offsets, dist=None, mode: str = "tile", top_c: int = 10,
+                     radius_m: float = 3.0, toler_pct: int = 20, tau: float = 1.0, out=None, stream=None):
+    """Algorithm 2 on caller candidates. Returns (xy float64 [nw, 2], status int32 [nw])."""
+    torch = _torch()
+    idx = _dev_tensor(idx, torch.int64, "idx")
+    cand_offsets = _dev_tensor(cand_offsets, torch.int32, "cand_offsets")
+    if dist is not None:
+        dist = _dev_tensor(dist, torch.float32, "dist")
+    nw = cand_offsets.shape[0] - 1
+    if out is None:
+        xy = torch.empty((nw, 2), dtype=torch.float64, device=idx.device)
+        status = torch.empty((nw,), dtype=torch.int32, device=idx.device)
+    else:
+        xy, status = out
+    a = agg_params(mode, top_c, radius_m, toler_pct, tau)
+    _check(_lib.lhr_aggregate_2d(db.handle, _ptr(idx), _ptr(dist), idx.numel(), _ptr(cand_offsets), nw,
+                                 ctypes.byref(a), _ptr(xy), _ptr(status), _stream(stream)))
+    return xy, status
+
+
+def lhr_profile_enable(on: bool) -> None:
+    """Per-kernel CUDA-event timing of every later launch (process-wide)."""
+    _check(_lib.lhr_profile_enable(1 if on else 0))
+
+
+def lhr_profile_read(kernel: str | None = None, reset: bool = True):
+    """(launches, total device ms) of profiled kernels whose name contains `kernel`."""
+    n, ms = ctypes.c_int64(), ctypes.c_double()
+    _check(_lib.lhr_profile_read(None if kernel is None else kernel.encode(), ctypes.byref(n), ctypes.byref(ms),
+                                 1 if reset else 0))
+    return n.value, ms.value
+
+
+def lhr_db_error(db: Database, stream=None) -> int:
+    """Reads and clears the database's device error word (synchronizes)."""
+    e = ctypes.c_int32()
+    _check(_lib.lhr_db_error(db.handle, ctypes.byref(e), _stream(stream)))
+    return e.value

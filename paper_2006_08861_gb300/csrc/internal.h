@@ -1,0 +1,124 @@
+// Host-side internals shared by the library's translation units: the
+// database handle, scratch allocation, and the launchers each kernel file
+// exports to the C ABI layer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lhr.h"
+
+constexpr int kSnPad = 256;
+
+struct lhr_db {
+    int device = 0;
+    int64_t n = 0;
+    int dim = 0;
+    int coarse_dim = 0;
+    uint32_t lowp = 0;
+    double tile_m = 0.3;
+    int n_sub = 1;
+    int sms = 1;  // multiprocessors of `device`
+
+    // Rows in internal order: grouped by subspace (stable), so each subspace is
+    // one contiguous range. perm[i] is the caller's row of internal row i
+    // (nullptr when the order is the caller's).
+    float* X = nullptr;         // n x dim
+    float* Xc = nullptr;        // n x coarse_dim (coarse prefix slab), or nullptr
+    int32_t* perm = nullptr;    // n, or nullptr
+    // Caller's order.
+    double* xy = nullptr;       // n x 2
+    int32_t* tile = nullptr;    // n x 2 (tx, ty) = floor(xy / tile_m)
+
+    // Scan partition: chunk c covers internal rows [chunks[c].x, chunks[c].y) of
+    // subspace chunks[c].z; chunks of subspace s are [chunk_off[s], chunk_off[s+1]).
+    int nchunks = 0;
+    int chunk_rows = 0;
+    int4* chunks = nullptr;
+    int32_t* chunk_off = nullptr;
+    std::vector<int32_t> chunk_off_h;
+    std::vector<int64_t> sub_rows_h;  // rows per subspace
+
+    // Low-precision copies (internal order) and, per row, (FP32 scale s,
+    // FP32 norm s^2 ||x^||^2 of the quantised row); the (s, norm) arrays carry
+    // kSnPad rows of zero padding so whole-tile bulk copies stay in bounds.
+    void* Xb = nullptr;   float2* snb = nullptr;   // BF16
+    void* X8 = nullptr;   float2* sn8 = nullptr;   // FP8 e4m3
+
+    int32_t* err = nullptr;  // device error word (lhr_db_error)
+};
+
+namespace lhr {
+
+// Thread-local error message plumbing.
+lhr_status fail(lhr_status st, const std::string& msg);
+lhr_status cuda_fail(cudaError_t e, const char* what);
+
+// Stream-ordered scratch from a library-owned memory pool of the current
+// device. Freed (stream-ordered) by release().
+struct Scratch {
+    void* ptr = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaError_t alloc(size_t bytes, cudaStream_t s);
+    void release();
+    ~Scratch() { release(); }
+};
+
+// Opt-in per-kernel event timing (lhr_profile_enable). A scope records an
+// event pair around the launches it encloses when profiling is on.
+struct ProfScope {
+    int slot = -1;
+    cudaStream_t stream = nullptr;
+    ProfScope(const char* kernel, cudaStream_t s);
+    ~ProfScope();
+};
+
+// Exhaustive FP32 scan + fused top-k (scan.cu).
+size_t scan_scratch_bytes(const lhr_db* db, int nq, int k);
+cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t* idx, float* dist,
+                        void* scratch, cudaStream_t stream);
+
+// Low-precision tensor-core scores + FP32 re-rank (lowp.cu).
+size_t lowp_scratch_bytes(const lhr_db* db, int nq, bool fp8, int W);
+cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int W, int k, int64_t* idx, float* dist,
+                        void* scratch, cudaStream_t stream);
+
+// Coarse-to-fine (coarse.cu).
+size_t coarse_scratch_bytes(const lhr_db* db, int nq, int shortlist);
+cudaError_t launch_coarse(const lhr_db* db, const float* q, int nq, int shortlist, int k, int64_t* idx,
+                          float* dist, void* scratch, cudaStream_t stream);
+
+// Algorithm 2 (aggregate.cu). Candidates of window w: rows idx[c] for c in
+// [cand_begin(w), cand_end(w)) where the range is cand_offsets[w]..[w+1]
+// scaled by `per_frame` (frame offsets times candidates per frame) when
+// per_frame > 0.
+struct AggArgs {
+    const int64_t* idx;
+    const float* dist;
+    const int32_t* offsets;
+    int per_frame;  // > 0: offsets are frame offsets, each frame owns per_frame candidates
+    long long limit;  // candidates available in idx / dist; a window reaching past it is an error
+    int nw;
+    int mode;
+    int top_c;
+    int toler_pct;
+    long long r2max;
+    float tau;
+    double tile_m;
+    double* xy_out;
+    int32_t* status;
+};
+cudaError_t launch_aggregate(const lhr_db* db, const AggArgs& a, cudaStream_t stream);
+long long circle_r2_limit(double radius_m, double tile_m);
+
+// Database construction helpers (build.cu).
+cudaError_t launch_build_derived(lhr_db* db, cudaStream_t stream);
+cudaError_t launch_check_finite(const float* x, int64_t count, int32_t* flag, cudaStream_t stream);
+cudaError_t launch_gather_rows(const float* src, const int32_t* perm, int64_t n, int dim, float* dst,
+                               cudaStream_t stream);
+cudaError_t launch_tiles(const double* xy, int64_t n, double t, int32_t* tile, int32_t* flag, cudaStream_t stream);
+
+}  // namespace lhr

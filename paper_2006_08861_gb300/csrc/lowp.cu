@@ -1,0 +1,654 @@
+// Low-precision form: tensor-core scores over a BF16 / FP8-e4m3 copy of the
+// database with per-row scales, a fused per-query top-W shortlist, and an
+// FP32 re-rank of the shortlist on the FP32 rows (the paper scores FP
+// features directly, §3.1; this form trades a widened shortlist for
+// tensor-core throughput when many query frames are batched).
+//
+// score(q, x_j) = n_j - 2 s_q s_j (q^ . x^_j)        (||q||^2 dropped: constant per query)
+//   q^, x^_j : quantised codes, s_q, s_j : per-vector scales,
+//   n_j = s_j^2 ||x^_j||^2 (built with the database).
+//
+// tc_topw_kernel, one CTA per (128-query block, database chunk), 6 warps:
+//   warp 0  producer: TMA (cp.async.bulk.tensor.2d, 128-byte swizzle) of the
+//           block's 128 query codes once, then the chunk's 128-row tiles, one
+//           128-byte K slice per stage, through a 6-stage mbarrier ring; plus
+//           a 1-D bulk copy of each tile's (s_j, n_j) pairs.
+//   warp 1  TMEM allocator and MMA issuer: tcgen05.mma (M = 128 queries,
+//           N = 128 rows, K = 16 BF16 / 32 FP8 per instruction) into two
+//           128-column FP32 accumulators in TMEM, alternating per tile;
+//           tcgen05.commit frees smem stages and publishes accumulators.
+//   warps 2-5 epilogue: thread = query (TMEM lane); tcgen05.ld 32 columns at a
+//           time, score = fma(-2 s_q, s_j dot, n_j), compare with the thread's
+//           running W-th best and append survivors to a 32-entry shared-memory
+//           buffer, merged into the thread's sorted top-W list (local memory)
+//           only when full. Scores never leave the SM.
+// merge_rerank_kernel, one warp per query: the per-chunk top-W lists are cut
+//   at the smallest chunk's W-th key (a bound on the global W-th), sorted,
+//   the first W rows are re-scored with the exact FP32 direct form and the
+//   top k kept (warp-register list).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace lhr {
+namespace {
+
+constexpr int kTile = 128;        // queries per CTA (UMMA M) and rows per tile (UMMA N)
+constexpr int kSliceBytes = 128;  // K bytes per smem row (one 128-byte swizzle atom)
+constexpr int kSliceTile = kTile * kSliceBytes;  // 16 KB per tile slice
+constexpr int kStages = 6;
+constexpr int kBuf = 32;          // survivor buffer entries per epilogue thread
+constexpr int kThreads = 192;
+constexpr int kMergeCap = 512;    // candidate keys sorted per query in the merge
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, u64* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(u64* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+template <bool kFp8>
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, u64 adesc, u64 bdesc, uint32_t idesc, uint32_t accum) {
+    if (kFp8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row core groups 1024 bytes apart.
+__device__ __forceinline__ u64 sw128_desc(uint32_t saddr) {
+    u64 d = (u64)((saddr >> 4) & 0x3FFFu);
+    d |= (u64)1 << 16;              // leading-dimension offset (unused with this swizzle)
+    d |= (u64)(1024 >> 4) << 32;    // stride-dimension offset: 1024 B between 8-row groups
+    d |= (u64)1 << 46;              // descriptor version for tcgen05
+    d |= (u64)2 << 61;              // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: dense, FP32 accumulate, A/B K-major, M = N = 128.
+// BF16 inputs: format 1 in both operand fields (kind::f16); E4M3: format 0
+// (kind::f8f6f4).
+__host__ __device__ constexpr uint32_t tc_idesc(bool fp8) {
+    return (1u << 4)                      // D format: F32
+           | ((fp8 ? 0u : 1u) << 7)       // A format
+           | ((fp8 ? 0u : 1u) << 10)      // B format
+           | ((uint32_t)(kTile >> 3) << 17)  // N >> 3
+           | ((uint32_t)(kTile >> 4) << 24); // M >> 4
+}
+
+// Orderable key of a (possibly negative) FP32 score and a row.
+__device__ __forceinline__ u64 score_key(float t, uint32_t row) {
+    uint32_t u = __float_as_uint(t);
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((u64)u << 32) | row;
+}
+
+struct TcParams {
+    int64_t n;
+    int slices;       // D * elem / 128
+    int chunk_rows;   // multiple of kTile
+    int nchunks;
+    const float2* sn; // per row (s_j, n_j), padded
+    const float* qm;  // per padded query: -2 s_q (0 for padding)
+    int nq;
+    int W;
+    u64* partial;     // [query][chunk][W]
+    int* err;
+};
+
+template <int WMAX>
+__device__ __noinline__ void flush_buffer(u64* list, const u64* buf, int stride, int nb, int W) {
+    u64 tmp[kBuf];
+    for (int i = 0; i < nb; ++i) {
+        const u64 v = buf[i * stride];
+        int j = i;
+        while (j > 0 && tmp[j - 1] > v) {
+            tmp[j] = tmp[j - 1];
+            --j;
+        }
+        tmp[j] = v;
+    }
+    u64 out[WMAX];
+    int a = 0, b = 0;
+    for (int o = 0; o < W; ++o) {
+        const u64 x = list[a];
+        const u64 y = b < nb ? tmp[b] : kKeyEmpty;
+        if (y < x) {
+            out[o] = y;
+            ++b;
+        } else {
+            out[o] = x;
+            ++a;
+        }
+    }
+    for (int o = 0; o < W; ++o) list[o] = out[o];
+}
+
+template <bool kFp8, int WMAX>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_topw_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const TcParams p) {
+    extern __shared__ unsigned char smem_raw[];
+    // 1024-byte alignment for the 128-byte swizzle pattern
+    unsigned char* smem =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA = smem;                                   // slices x 16 KB
+    unsigned char* sB = sA + (size_t)p.slices * kSliceTile;     // kStages x 16 KB
+    float2* sSN = reinterpret_cast<float2*>(sB + (size_t)kStages * kSliceTile);  // 2 x 128
+    u64* sBuf = reinterpret_cast<u64*>(sSN + 2 * kTile);        // kBuf x 128 (slot-major)
+    u64* bars = sBuf + kBuf * kTile;
+    u64* full = bars;
+    u64* empty = full + kStages;
+    u64* a_full = empty + kStages;
+    u64* acc_full = a_full + 1;
+    u64* acc_empty = acc_full + 2;
+    u64* sn_full = acc_empty + 2;
+    u64* sn_empty = sn_full + 2;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sn_empty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int chunk = blockIdx.x, qblock = blockIdx.y;
+    const int64_t row0 = (int64_t)chunk * p.chunk_rows;
+    const int64_t row1 = min(p.n, row0 + p.chunk_rows);
+    const int ntiles = (int)((row1 - row0 + kTile - 1) / kTile);
+    constexpr int kElemPerSlice = kFp8 ? 128 : 64;
+    constexpr int kMmaK = kFp8 ? 32 : 16;                       // elements per MMA
+    constexpr int kMmaPerSlice = kElemPerSlice / kMmaK;         // 4
+    constexpr uint32_t kIdesc = tc_idesc(kFp8);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(a_full, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 4);
+            mbar_init(&sn_full[i], 1);
+            mbar_init(&sn_empty[i], 4);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(2 * kTile)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // queries of this block, all K slices, once
+            mbar_arrive_expect_tx(a_full, (uint32_t)p.slices * kSliceTile);
+            for (int s = 0; s < p.slices; ++s)
+                tma_load_2d(sA + (size_t)s * kSliceTile, &tmA, s * kElemPerSlice, qblock * kTile, a_full);
+            for (int t = 0; t < ntiles && !*abort_flag; ++t) {
+                const int64_t r = row0 + (int64_t)t * kTile;
+                const int slot = t & 1;
+                if (!mbar_wait(&sn_empty[slot], (uint32_t)((t >> 1) & 1) ^ 1u, abort_flag)) {
+                    *abort_flag = 1;
+                    record_error(p.err, kErrTimeout);
+                    break;
+                }
+                const int nr = (int)((row1 - r) < kTile ? (row1 - r) : kTile);
+                const uint32_t snb = (uint32_t)((nr + 1) / 2) * 16u;
+                mbar_arrive_expect_tx(&sn_full[slot], snb);
+                bulk_g2s(sSN + slot * kTile, p.sn + r, snb, &sn_full[slot]);
+                for (int s = 0; s < p.slices; ++s) {
+                    const int it = t * p.slices + s;
+                    const int st = it % kStages;
+                    if (!mbar_wait(&empty[st], (uint32_t)((it / kStages) & 1) ^ 1u, abort_flag)) {
+                        *abort_flag = 1;
+                        record_error(p.err, kErrTimeout);
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[st], kSliceTile);
+                    tma_load_2d(sB + (size_t)st * kSliceTile, &tmB, s * kElemPerSlice, (int)r, &full[st]);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = mbar_wait(a_full, 0u, abort_flag);
+            int t = 0;
+            for (; ok && t < ntiles; ++t) {
+                const int a = t & 1;
+                if (!mbar_wait(&acc_empty[a], (uint32_t)((t >> 1) & 1) ^ 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(a * kTile);
+                for (int s = 0; s < p.slices; ++s) {
+                    const int it = t * p.slices + s;
+                    const int st = it % kStages;
+                    if (!mbar_wait(&full[st], (uint32_t)((it / kStages) & 1), abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_base = smem_u32(sA + (size_t)s * kSliceTile);
+                    const uint32_t b_base = smem_u32(sB + (size_t)st * kSliceTile);
+#pragma unroll
+                    for (int kk = 0; kk < kMmaPerSlice; ++kk) {
+                        const uint32_t off = (uint32_t)(kk * kMmaK * (kFp8 ? 1 : 2));
+                        tc_mma<kFp8>(d_tmem, sw128_desc(a_base + off), sw128_desc(b_base + off), kIdesc,
+                                     (s | kk) != 0 ? 1u : 0u);
+                    }
+                    tc_commit(&empty[st]);
+                }
+                if (!ok) break;
+                tc_commit(&acc_full[a]);
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                record_error(p.err, kErrTimeout);
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue
+        const int quad = warp & 3;                 // TMEM lane quadrant this warp may access
+        const int qrow = quad * 32 + lane;         // query row within the block
+        const int et = (warp - 2) * 32 + lane;     // epilogue thread index (buffer column)
+        const int64_t qi = (int64_t)qblock * kTile + qrow;
+        const bool qvalid = qi < p.nq;
+        const float m = qvalid ? p.qm[qi] : 0.f;
+        u64 list[WMAX];
+        for (int i = 0; i < WMAX; ++i) list[i] = kKeyEmpty;
+        u64 thr = kKeyEmpty;
+        int nb = 0;
+        u64* buf = sBuf + et;
+        for (int t = 0; t < ntiles; ++t) {
+            const int a = t & 1;
+            const uint32_t par = (uint32_t)((t >> 1) & 1);
+            if (!mbar_wait(&acc_full[a], par, abort_flag) || !mbar_wait(&sn_full[a], par, abort_flag)) {
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    record_error(p.err, kErrTimeout);
+                }
+                break;
+            }
+            tc_fence_after();
+            const int64_t r = row0 + (int64_t)t * kTile;
+            const int nr = (int)((row1 - r) < kTile ? (row1 - r) : kTile);
+            const float2* snt = sSN + a * kTile;
+#pragma unroll 1
+            for (int c0 = 0; c0 < kTile; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kTile + c0), v);
+                if (qvalid) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = c0 + j;
+                        const float2 sn = snt[col];
+                        const float score = fmaf(m, sn.x * __uint_as_float(v[j]), sn.y);
+                        const u64 key = score_key(score, (uint32_t)(r + col));
+                        if (col < nr && key < thr) {
+                            buf[nb * kTile] = key;
+                            if (++nb == kBuf) {
+                                flush_buffer<WMAX>(list, buf, kTile, nb, p.W);
+                                nb = 0;
+                                thr = list[p.W - 1];
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&acc_empty[a]);
+                mbar_arrive(&sn_empty[a]);
+            }
+        }
+        if (nb) flush_buffer<WMAX>(list, buf, kTile, nb, p.W);
+        if (qvalid) {
+            u64* dst = p.partial + ((size_t)qi * p.nchunks + chunk) * p.W;
+            for (int i = 0; i < p.W; ++i) dst[i] = list[i];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTile) : "memory");
+}
+
+// Per query: per-vector scale s_q = amax / qmax, codes, and -2 s_q. Rows past
+// nq (padding to the 128-query block) get zero codes.
+template <bool kFp8>
+__global__ void quantize_queries_kernel(const float* Q, int nq, int nq_pad, int D, void* codes, float* qm) {
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= nq_pad) return;
+    const float qmax = kFp8 ? 448.0f : 1.0f;
+    float amax = 0.f;
+    if (w < nq)
+        for (int j = lane; j < D; j += 32) amax = fmaxf(amax, fabsf(Q[(size_t)w * D + j]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(kFull, amax, o));
+    const float s = amax > 0.f ? __fdiv_rn(amax, qmax) : 1.0f;
+    for (int j = lane; j < D; j += 32) {
+        const float v = w < nq ? __fdiv_rn(Q[(size_t)w * D + j], s) : 0.f;
+        if (kFp8)
+            reinterpret_cast<__nv_fp8_storage_t*>(codes)[(size_t)w * D + j] =
+                __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+        else
+            reinterpret_cast<__nv_bfloat16*>(codes)[(size_t)w * D + j] = __float2bfloat16_rn(v);
+    }
+    if (lane == 0) qm[w] = w < nq ? -2.0f * s : 0.f;
+}
+
+__device__ __forceinline__ u64 warp_min_u64(u64 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const u64 w = __shfl_xor_sync(kFull, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+// Warp bitonic sort of n (power of two) keys in shared memory, ascending.
+__device__ void warp_sort(u64* a, int n, int lane) {
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < n / 2; i += 32) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const u64 x = a[lo], y = a[hi];
+                if ((x > y) == up) {
+                    a[lo] = y;
+                    a[hi] = x;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Number of keys <= x among the query's per-chunk lists.
+__device__ int count_le(const u64* P, int total, u64 x, int lane) {
+    int c = 0;
+    for (int i = lane; i < total; i += 32) {
+        const u64 key = __ldcg(P + i);
+        c += (key != kKeyEmpty && key <= x) ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    return c;
+}
+
+template <int CPL>
+__global__ void __launch_bounds__(256) merge_rerank_kernel(const u64* __restrict__ partial, int nchunks, int W,
+                                                           const float* __restrict__ X, int D,
+                                                           const float* __restrict__ Q, int nq, int k,
+                                                           int64_t* __restrict__ idx, float* __restrict__ dist) {
+    __shared__ u64 cand[8][kMergeCap];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int qi = blockIdx.x * 8 + warp;
+    if (qi >= nq) return;
+    u64* cw = cand[warp];
+    const u64* P = partial + (size_t)qi * nchunks * W;
+    const int total = nchunks * W;
+    // every key of the global top W is <= the smallest chunk's W-th key
+    u64 bound = kKeyEmpty;
+    for (int c = lane; c < nchunks; c += 32) {
+        const u64 v = __ldcg(P + (size_t)c * W + W - 1);
+        bound = v < bound ? v : bound;
+    }
+    bound = warp_min_u64(bound);
+    int cnt = count_le(P, total, bound, lane);
+    if (cnt > kMergeCap) {
+        // many keys share the bound's neighbourhood: bisect for the W-th smallest key
+        u64 lo = 0, hi = bound;
+        while (lo < hi) {
+            const u64 mid = lo + (hi - lo) / 2;
+            if (count_le(P, total, mid, lane) >= W) hi = mid;
+            else lo = mid + 1;
+        }
+        bound = lo;
+        cnt = count_le(P, total, bound, lane);
+    }
+    int n = 0;
+    for (int base = 0; base < total; base += 32) {
+        const int i = base + lane;
+        const u64 key = i < total ? __ldcg(P + i) : kKeyEmpty;
+        const bool take = key != kKeyEmpty && key <= bound;
+        const unsigned m = __ballot_sync(kFull, take);
+        const int pos = n + __popc(m & ((1u << lane) - 1u));
+        if (take && pos < kMergeCap) cw[pos] = key;
+        n += __popc(m);
+    }
+    n = min(n, kMergeCap);
+    int p2 = 32;
+    while (p2 < n) p2 <<= 1;
+    for (int i = n + lane; i < p2; i += 32) cw[i] = kKeyEmpty;
+    __syncwarp();
+    warp_sort(cw, p2, lane);
+    const int take = min(n, W);
+    // FP32 direct re-rank of the shortlist
+    const int D4 = D / 4;
+    float4 qv[CPL];
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+        const int c = lane + 32 * j;
+        qv[j] = c < D4 ? reinterpret_cast<const float4*>(Q + (size_t)qi * D)[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float2 neg1 = make_float2(-1.f, -1.f);
+    u64 L = kKeyEmpty, thr = kKeyEmpty;
+    for (int i = 0; i < take; ++i) {
+        const uint32_t r = (uint32_t)cw[i];
+        const float4* xr = reinterpret_cast<const float4*>(X + (size_t)r * D);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            const int c = lane + 32 * j;
+            if (c < D4) {
+                const float4 x = __ldg(xr + c);
+                float2 a = __ffma2_rn(make_float2(x.x, x.y), neg1, make_float2(qv[j].x, qv[j].y));
+                float2 b = __ffma2_rn(make_float2(x.z, x.w), neg1, make_float2(qv[j].z, qv[j].w));
+                acc = __ffma2_rn(a, a, acc);
+                acc = __ffma2_rn(b, b, acc);
+            }
+        }
+        float d = acc.x + acc.y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+        const u64 key = make_key(d, r);
+        if (key < thr) {
+            list_insert(L, key, k, lane);
+            thr = __shfl_sync(kFull, L, k - 1);
+        }
+    }
+    if (lane < k) {
+        const size_t o = (size_t)qi * k + lane;
+        if (L == kKeyEmpty) {
+            idx[o] = -1;
+            dist[o] = __int_as_float(0x7f800000);
+        } else {
+            idx[o] = (int64_t)key_row(L);
+            dist[o] = key_dist(L);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+// 2-D map over a row-major rows x D array of 1- or 2-byte codes; box = 128
+// bytes of K by 128 rows, 128-byte swizzle, zero fill past the last row.
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int D, bool fp8) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const int elem = fp8 ? 1 : 2;
+    cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)D * elem};
+    cuuint32_t box[2] = {(cuuint32_t)(kSliceBytes / elem), (cuuint32_t)kTile};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                          const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+struct LowpPlan {
+    int nq_pad, qblocks, chunk_rows, nchunks, wmax;
+    size_t codes_bytes, qm_bytes, partial_bytes, smem;
+};
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+LowpPlan plan(const lhr_db* db, int nq, bool fp8, int W) {
+    LowpPlan pl{};
+    pl.nq_pad = (nq + kTile - 1) / kTile * kTile;
+    pl.qblocks = pl.nq_pad / kTile;
+    int target = std::max(1, db->sms / pl.qblocks);
+    int64_t cr = (db->n + target - 1) / target;
+    cr = (cr + kTile - 1) / kTile * kTile;
+    pl.chunk_rows = (int)cr;
+    pl.nchunks = (int)((db->n + cr - 1) / cr);
+    pl.wmax = W <= 32 ? 32 : (W <= 64 ? 64 : 128);
+    const int elem = fp8 ? 1 : 2;
+    pl.codes_bytes = a256((size_t)pl.nq_pad * db->dim * elem);
+    pl.qm_bytes = a256((size_t)pl.nq_pad * sizeof(float));
+    pl.partial_bytes = a256((size_t)nq * pl.nchunks * W * sizeof(u64));
+    const int slices = db->dim * elem / kSliceBytes;
+    pl.smem = 1024 + (size_t)slices * kSliceTile + (size_t)kStages * kSliceTile + 2 * kTile * sizeof(float2) +
+              (size_t)kBuf * kTile * sizeof(u64) + (2 * kStages + 9) * sizeof(u64) + 16;
+    return pl;
+}
+
+template <bool kFp8, int WMAX>
+cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& tp, const LowpPlan& pl,
+                      cudaStream_t stream) {
+    auto kern = tc_topw_kernel<kFp8, WMAX>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+    if (e != cudaSuccess) return e;
+    ProfScope ps(kFp8 ? "tc_topw_kernel_fp8" : "tc_topw_kernel_bf16", stream);
+    kern<<<dim3(pl.nchunks, pl.qblocks), kThreads, pl.smem, stream>>>(ma, mb, tp);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t lowp_scratch_bytes(const lhr_db* db, int nq, bool fp8, int W) {
+    const LowpPlan pl = plan(db, nq, fp8, W);
+    return pl.codes_bytes + pl.qm_bytes + pl.partial_bytes;
+}
+
+cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int W, int k, int64_t* idx, float* dist,
+                        void* scratch, cudaStream_t stream) {
+    const LowpPlan pl = plan(db, nq, fp8, W);
+    unsigned char* base = reinterpret_cast<unsigned char*>(scratch);
+    void* codes = base;
+    float* qm = reinterpret_cast<float*>(base + pl.codes_bytes);
+    u64* partial = reinterpret_cast<u64*>(base + pl.codes_bytes + pl.qm_bytes);
+    {
+        ProfScope ps("quantize_queries_kernel", stream);
+        const int blocks = (pl.nq_pad * 32 + 255) / 256;
+        if (fp8)
+            quantize_queries_kernel<true><<<blocks, 256, 0, stream>>>(q, nq, pl.nq_pad, db->dim, codes, qm);
+        else
+            quantize_queries_kernel<false><<<blocks, 256, 0, stream>>>(q, nq, pl.nq_pad, db->dim, codes, qm);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, codes, pl.nq_pad, db->dim, fp8) || !make_map(&mb, fp8 ? db->X8 : db->Xb, db->n, db->dim, fp8))
+        return cudaErrorInvalidValue;
+    TcParams tp{};
+    tp.n = db->n;
+    tp.slices = db->dim * (fp8 ? 1 : 2) / kSliceBytes;
+    tp.chunk_rows = pl.chunk_rows;
+    tp.nchunks = pl.nchunks;
+    tp.sn = fp8 ? db->sn8 : db->snb;
+    tp.qm = qm;
+    tp.nq = nq;
+    tp.W = W;
+    tp.partial = partial;
+    tp.err = db->err;
+    cudaError_t e;
+    if (fp8) {
+        e = pl.wmax == 32 ? launch_tc<true, 32>(ma, mb, tp, pl, stream)
+                          : (pl.wmax == 64 ? launch_tc<true, 64>(ma, mb, tp, pl, stream)
+                                           : launch_tc<true, 128>(ma, mb, tp, pl, stream));
+    } else {
+        e = pl.wmax == 32 ? launch_tc<false, 32>(ma, mb, tp, pl, stream)
+                          : (pl.wmax == 64 ? launch_tc<false, 64>(ma, mb, tp, pl, stream)
+                                           : launch_tc<false, 128>(ma, mb, tp, pl, stream));
+    }
+    if (e != cudaSuccess) return e;
+    const int d4 = db->dim / 4;
+    const int cpl = d4 <= 32 ? 1 : (d4 <= 64 ? 2 : 4);
+    ProfScope ps("merge_rerank_kernel", stream);
+    const int blocks = (nq + 7) / 8;
+    if (cpl == 1)
+        merge_rerank_kernel<1><<<blocks, 256, 0, stream>>>(partial, pl.nchunks, W, db->X, db->dim, q, nq, k, idx, dist);
+    else if (cpl == 2)
+        merge_rerank_kernel<2><<<blocks, 256, 0, stream>>>(partial, pl.nchunks, W, db->X, db->dim, q, nq, k, idx, dist);
+    else
+        merge_rerank_kernel<4><<<blocks, 256, 0, stream>>>(partial, pl.nchunks, W, db->X, db->dim, q, nq, k, idx, dist);
+    return cudaGetLastError();
+}
+
+}  // namespace lhr

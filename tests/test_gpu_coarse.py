@@ -1,0 +1,110 @@
+"""Coarse-to-fine retrieval (prefix over every row -> S-row shortlist ->
+full re-rank -> top k) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import aggregate as oagg
+from oracle import retrieval as oret
+from tests.parity import GAP, XY_ATOL, check_list
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lhr():
+    import paper_2006_08861_gb300 as m
+    return m
+
+
+def _shortlist_separated(q, X, dc, S):
+    d = np.sort(oret.sq_dist(q[:dc], X[:, :dc]))
+    return S >= X.shape[0] or (d[S] - d[S - 1]) > GAP * max(d[S - 1], 1e-12)
+
+
+def test_full_shortlist_equals_exhaustive(lhr):
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((600, 64)).astype(np.float32)
+    Q = (X[rng.integers(0, 600, 6)] + 0.3 * rng.standard_normal((6, 64))).astype(np.float32)
+    db = lhr.lhr_build_db(X, np.zeros((600, 2)), coarse_dim=16)
+    q = torch.from_numpy(Q).cuda()
+    hi, hd = lhr.lhr_query(db, q, 10, shortlist=600)
+    ei, ed = lhr.lhr_query(db, q, 10)
+    torch.cuda.synchronize()
+    assert np.array_equal(hi.cpu().numpy(), ei.cpu().numpy())
+    assert np.array_equal(hd.cpu().numpy(), ed.cpu().numpy())
+
+
+@pytest.mark.parametrize("n,dim,dc,S,k,nq", [
+    (20_000, 64, 16, 256, 10, 5),
+    (9_001, 128, 32, 100, 20, 3),
+    (3_000, 36, 4, 64, 7, 9),      # prefix of one float4, more than 8 frames
+    (5_000, 256, 128, 4096, 32, 2),  # widest prefix, largest shortlist
+])
+def test_against_oracle(lhr, n, dim, dc, S, k, nq):
+    rng = np.random.default_rng(n + S)
+    X = rng.standard_normal((n, dim)).astype(np.float32)
+    Q = (X[rng.integers(0, n, nq)] + 0.3 * rng.standard_normal((nq, dim))).astype(np.float32)
+    db = lhr.lhr_build_db(X, np.zeros((n, 2)), coarse_dim=dc)
+    idx, dist = lhr.lhr_query(db, torch.from_numpy(Q).cuda(), k, shortlist=S)
+    torch.cuda.synchronize()
+    gi, gd = idx.cpu().numpy()[:, 0], dist.cpu().numpy()[:, 0]
+    o_idx, o_dist, _ = oret.hierarchical_topk(Q, X, dc, S, k + 1)
+    checked = 0
+    for qi in range(nq):
+        if not _shortlist_separated(Q[qi], X, dc, S):
+            continue
+        # the oracle's k+1 list comes from the same shortlist
+        check_list(Q[qi], X, gi[qi], gd[qi], o_idx[qi], o_dist[qi], k, where=f"q{qi}")
+        checked += 1
+    assert checked >= nq - 1
+
+
+def test_boundary_bin_overflow_refines_to_rows(lhr):
+    # Every row has the same prefix, so all coarse distances are equal and the
+    # shortlist is decided by the row tie rule alone: rows 0..S-1.
+    rng = np.random.default_rng(2)
+    n, dim, dc, S, k = 12_000, 64, 8, 300, 10
+    X = rng.standard_normal((n, dim)).astype(np.float32)
+    X[:, :dc] = 0.5
+    Q = rng.standard_normal((3, dim)).astype(np.float32)
+    db = lhr.lhr_build_db(X, np.zeros((n, 2)), coarse_dim=dc)
+    idx, dist = lhr.lhr_query(db, torch.from_numpy(Q).cuda(), k, shortlist=S)
+    torch.cuda.synchronize()
+    gi = idx.cpu().numpy()[:, 0]
+    o_idx, o_dist, short = oret.hierarchical_topk(Q, X, dc, S, k + 1)
+    assert np.array_equal(short, np.tile(np.arange(S), (3, 1)))
+    for qi in range(3):
+        check_list(Q[qi], X, gi[qi], dist.cpu().numpy()[qi, 0], o_idx[qi], o_dist[qi], k)
+        assert np.all(gi[qi] < S)
+
+
+def test_hierarchical_configuration_windows(lhr):
+    # Building scale: N = 100,000, D = 256, coarse prefix 32, shortlist 512,
+    # k = 20, windows of m = 5 frames 0.3 m apart, aggregated in 2-D.
+    cfg = synth.CONFIGS["hierarchical"]
+    db = synth.make_database(cfg["n"], cfg["dim"], seed=1001)
+    win = synth.make_windows(db, 8, cfg["m"], seed=2001)
+    h = lhr.lhr_build_db(db.feats, db.xy, coarse_dim=cfg["coarse_dim"])
+    frames = torch.from_numpy(win.frames).cuda()
+    offs = torch.from_numpy(win.offsets).cuda()
+    idx, dist, xy, st = lhr.lhr_query_window(h, frames, offs, cfg["k"], shortlist=cfg["shortlist"],
+                                             mode="tile")
+    torch.cuda.synchronize()
+    gi, gd = idx.cpu().numpy()[:, 0], dist.cpu().numpy()[:, 0]
+    o_idx, o_dist, _ = oret.hierarchical_topk(win.frames, db.feats, cfg["coarse_dim"], cfg["shortlist"],
+                                              cfg["k"] + 1)
+    for f in range(win.frames.shape[0]):
+        if _shortlist_separated(win.frames[f], db.feats, cfg["coarse_dim"], cfg["shortlist"]):
+            check_list(win.frames[f], db.feats, gi[f], gd[f], o_idx[f], o_dist[f], cfg["k"], where=f"f{f}")
+    # Algorithm 2 on the GPU's candidates equals the oracle's on the same candidates
+    cands = oret.window_candidates(gi, win.offsets)
+    o_xy, o_st = oagg.aggregate_windows(cands, db.xy, mode="tile")
+    assert np.array_equal(st.cpu().numpy(), o_st)
+    assert np.max(np.abs(xy.cpu().numpy() - o_xy)) <= XY_ATOL
+    # and the localization is right for most windows (error < 3 m)
+    err = np.hypot(*(xy.cpu().numpy() - win.true_xy).T)
+    assert np.mean(err < 3.0) >= 0.75
+    h.close()
