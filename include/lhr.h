@@ -184,6 +184,38 @@ lhr_status lhr_aggregate_2d(const lhr_db* db, const int64_t* idx, const float* d
 lhr_status lhr_db_error(const lhr_db* db, int32_t* err, void* cuda_stream);
 
 /*
+ * lhr_query_static -- the exhaustive FP32 lhr_query (shortlist 0, score F32)
+ * for callers that cannot allocate device memory. The paper has no
+ * counterpart; this entry point exists for the caller, not for the method.
+ *
+ * Who needs it: code that must not call cudaMalloc / cudaMallocAsync or any
+ * allocating routine, for instance a host thread working under a memory
+ * budget that another allocator already owns in full (a framework's caching
+ * allocator), or a real-time loop in which an allocation's implicit
+ * synchronization or failure is not acceptable. lhr_query instead takes its
+ * per-call scratch from a stream-ordered memory pool.
+ *
+ * How: the scratch (per-chunk candidate lists and per-query-block counters)
+ * is a fixed 4 MiB array in the library's device code. Every GPU that loads
+ * the library holds that array until the process exits. A request whose
+ * scratch would exceed 4 MiB (it grows with nq, k and the database's chunk
+ * count, about nq x k x 8 x 152 bytes on a 152-SM GPU) is rejected with
+ * LHR_ERR_INVALID_ARG before anything is launched; use fewer frames per call.
+ * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine (keep lhr_profile_enable off, which creates CUDA events).
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, that device current); make that first call before any stream
+ * capture. All calls share the one array and each call clears the parts that
+ * must start at zero, so calls whose work overlaps on the GPU (other streams,
+ * other threads) race and corrupt each other's results: serialize them.
+ *
+ * Arguments, outputs and errors as lhr_query with p = {k, 0, LHR_F32, 0}.
+ */
+lhr_status lhr_query_static(const lhr_db* db, const float* q, int32_t nq, int32_t k, int64_t* idx, float* dist,
+                            void* cuda_stream);
+
+/*
  * Instrumentation (no counterpart in the paper): per-kernel CUDA-event timing.
  * lhr_profile_enable(1) makes every later launch record an event pair on its
  * stream around each kernel; lhr_profile_read synchronizes those events and

@@ -70,6 +70,7 @@ def _load():
                              P, P, P, P, P],
         "lhr_aggregate_2d": [P, P, P, I64, P, I32, ctypes.POINTER(AggParams), P, P, P],
         "lhr_db_error": [P, ctypes.POINTER(I32), P],
+        "lhr_query_static": [P, P, I32, I32, P, P, P],
         "lhr_profile_enable": [I32],
         "lhr_profile_read": [ctypes.c_char_p, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double), I32],
     }
@@ -195,6 +196,18 @@ def lhr_query(db: Database, q, k: int, shortlist: int = 0, score: str = "f32", r
         idx, dist = out
     p = query_params(k, shortlist, score, rerank_width)
     _check(_lib.lhr_query(db.handle, _ptr(q), nq, ctypes.byref(p), _ptr(idx), _ptr(dist), _stream(stream)))
+    return idx, dist
+
+
+def lhr_query_static(db: Database, q, k: int, out, stream=None):
+    """Exhaustive FP32 top-k that allocates nothing: scratch is the library's
+    fixed 4 MiB device array, shared by every call (serialize overlapping
+    calls). ``out`` = (idx int64 [nq, n_s, k], dist float32 [nq, n_s, k]),
+    preallocated by the caller."""
+    torch = _torch()
+    q = _dev_tensor(q, torch.float32, "q")
+    idx, dist = out
+    _check(_lib.lhr_query_static(db.handle, _ptr(q), q.shape[0], k, _ptr(idx), _ptr(dist), _stream(stream)))
     return idx, dist
 
 

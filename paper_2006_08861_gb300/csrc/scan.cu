@@ -21,6 +21,9 @@
 //   * Warp lists merge into a per-CTA list written to scratch; the last CTA of
 //     a query block (atomic ticket) merges every chunk of each subspace and
 //     writes the final lists. One launch per call.
+#include <mutex>
+#include <string>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -343,3 +346,64 @@ cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t
 }
 
 }  // namespace lhr
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the exhaustive scan (lhr_query_static).
+//
+// Its scratch (per-chunk candidate lists and per-query-block tickets) lives in
+// this fixed device array instead of memory allocated per call. The array is
+// part of the library's device code, so every GPU that loads the library
+// holds these bytes until the process exits. All calls share it.
+static constexpr size_t kStaticScratchBytes = (size_t)4 << 20;  // 4 MiB
+static __device__ __align__(256) unsigned char g_scan_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+// Device address of g_scan_static_scratch, looked up once per device. In host
+// code the array's name only stands in for the symbol: it is not a device
+// address and must never be handed to a kernel.
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+
+cudaError_t static_scratch_address(int dev, void** out) {
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (g_static_addr[dev] == nullptr) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_scan_static_scratch);  // `dev` is current here
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" lhr_status lhr_query_static(const lhr_db* db, const float* q, int32_t nq, int32_t k, int64_t* idx,
+                                       float* dist, void* cuda_stream) {
+    using namespace lhr;
+    if (!db) return fail(LHR_ERR_INVALID_ARG, "db is NULL");
+    if (!q || !idx || !dist) return fail(LHR_ERR_INVALID_ARG, "q, idx and dist must be non-NULL");
+    if (reinterpret_cast<uintptr_t>(q) % 16) return fail(LHR_ERR_INVALID_ARG, "q must be 16-byte aligned");
+    if (nq < 1) return fail(LHR_ERR_INVALID_ARG, "nq must be >= 1");
+    if (k < 1 || k > 32) return fail(LHR_ERR_INVALID_ARG, "k must be in [1, 32]");
+    const size_t need = scan_scratch_bytes(db, nq, k);
+    if (need > kStaticScratchBytes)
+        return fail(LHR_ERR_INVALID_ARG, "lhr_query_static: this request needs " + std::to_string(need) +
+                                             " bytes of scratch, more than the fixed " +
+                                             std::to_string(kStaticScratchBytes) +
+                                             "-byte device array; use fewer query frames or lhr_query");
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return fail(LHR_ERR_CUDA, "cudaGetDevice failed");
+    if (prev != db->device && cudaSetDevice(db->device) != cudaSuccess)
+        return fail(LHR_ERR_CUDA, "cudaSetDevice failed");
+    void* scratch = nullptr;
+    cudaError_t e = static_scratch_address(db->device, &scratch);
+    if (e == cudaSuccess)
+        e = launch_scan(db, q, nq, k, idx, dist, scratch, reinterpret_cast<cudaStream_t>(cuda_stream));
+    if (prev != db->device) cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(e, "lhr_query_static");
+    return LHR_OK;
+}
