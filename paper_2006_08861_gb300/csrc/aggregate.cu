@@ -22,26 +22,15 @@
 #include "common.cuh"
 #include "internal.h"
 
+#include "aggregate.cuh"
+
 namespace lhr {
 namespace {
 
+using namespace agg;
+
 constexpr int kAggThreads = 256;
 constexpr int kMaxCand = 8192;
-
-struct AggParams {
-    AggArgs a;
-    const int32_t* tile;  // n x 2
-    const double* xy;     // n x 2
-    int64_t n;
-    long long rlim;       // floor(sqrt(r2max)): larger |dx| or |dy| is outside the circle
-    int* err;
-};
-
-__device__ __forceinline__ u64 tile_key(int tx, int ty) {
-    return ((u64)((uint32_t)ty ^ 0x80000000u) << 32) | (u64)((uint32_t)tx ^ 0x80000000u);
-}
-__device__ __forceinline__ int key_tx(u64 k) { return (int)((uint32_t)k ^ 0x80000000u); }
-__device__ __forceinline__ int key_ty(u64 k) { return (int)((uint32_t)(k >> 32) ^ 0x80000000u); }
 
 template <typename T>
 __device__ T block_sum(T v, T* red) {
@@ -86,6 +75,10 @@ __global__ void __launch_bounds__(kAggThreads) aggregate_kernel(const AggParams 
             a.status[w] = kErrInvalidArg;
             a.xy_out[2 * w] = a.xy_out[2 * w + 1] = __longlong_as_double(0x7ff8000000000000ll);
         }
+        return;
+    }
+    if (total <= kWarpCand) {
+        if (t < 32) aggregate_warp(p, w, b0, total, keys, cand_rows, cand_d, cnt);
         return;
     }
     if (t == 0) ctl[0] = 0;

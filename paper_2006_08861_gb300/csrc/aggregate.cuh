@@ -1,0 +1,207 @@
+// Algorithm 2 (§3.2) for one window by a single warp -- shared by the
+// aggregation kernel and the fused coarse-to-fine kernel. See aggregate.cu for
+// the steps, tie rules and integer tests.
+#pragma once
+
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace lhr {
+namespace agg {
+
+struct AggParams {
+    AggArgs a;
+    const int32_t* tile;  // n x 2
+    const double* xy;     // n x 2
+    int64_t n;
+    long long rlim;       // floor(sqrt(r2max)): larger |dx| or |dy| is outside the circle
+    int* err;
+};
+
+__device__ __forceinline__ u64 tile_key(int tx, int ty) {
+    return ((u64)((uint32_t)ty ^ 0x80000000u) << 32) | (u64)((uint32_t)tx ^ 0x80000000u);
+}
+__device__ __forceinline__ int key_tx(u64 k) { return (int)((uint32_t)k ^ 0x80000000u); }
+__device__ __forceinline__ int key_ty(u64 k) { return (int)((uint32_t)(k >> 32) ^ 0x80000000u); }
+
+constexpr int kWarpCand = 1024;  // windows with at most this many candidate slots take the warp path
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void write_invalid(const AggArgs& a, int w) {
+    a.status[w] = kErrInvalidArg;
+    a.xy_out[2 * w] = a.xy_out[2 * w + 1] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// Algorithm 2 for one window of at most kWarpCand candidate slots, by a single
+// warp: the same steps, tie rules and integer tests as the block path below,
+// with warp shuffles in place of block barriers.
+__device__ void aggregate_warp(const AggParams& p, int w, long long b0, long long total, u64* keys, int* cand_rows,
+                               float* cand_d, int* cnt) {
+    const AggArgs& a = p.a;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    // initialization: rows -> tiles, padding rows skipped, compacted in order
+    int C = 0;
+    for (long long base = 0; base < total; base += 32) {
+        const long long i = base + lane;
+        const int64_t r = i < total ? a.idx[b0 + i] : -1;
+        const bool bad = r >= p.n;
+        if (bad) record_error(p.err, kErrInvalidArg);
+        const bool take = r >= 0 && !bad;
+        const unsigned m = __ballot_sync(kFull, take);
+        const int pos = C + __popc(m & below);
+        if (take) {
+            cand_rows[pos] = (int)r;
+            cand_d[pos] = a.dist != nullptr ? a.dist[b0 + i] : 0.f;
+            keys[pos] = tile_key(p.tile[2 * r], p.tile[2 * r + 1]);
+        }
+        C += __popc(m);
+    }
+    __syncwarp();
+    if (C == 0) {
+        if (lane == 0) write_invalid(a, w);
+        return;
+    }
+    const double tm = a.tile_m;
+    int status = 0;
+    int win_tx = 0, win_ty = 0;
+    if (a.mode != 2) {
+        // step 2: binning = sort the tile keys, count runs
+        int p2 = 2;
+        while (p2 < C) p2 <<= 1;
+        for (int i = C + lane; i < p2; i += 32) keys[i] = kKeyEmpty;
+        __syncwarp();
+        for (int size = 2; size <= p2; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = lane; i < p2 / 2; i += 32) {
+                    const int lo = 2 * i - (i & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const u64 x = keys[lo], y = keys[hi];
+                    if ((x > y) == up) {
+                        keys[lo] = y;
+                        keys[hi] = x;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        int U = 0;
+        for (int base = 0; base < C; base += 32) {
+            const int i = base + lane;
+            const bool st = i < C && (i == 0 || keys[i] != keys[i - 1]);
+            const unsigned m = __ballot_sync(kFull, st);
+            if (st) cnt[U + __popc(m & below)] = i;
+            U += __popc(m);
+        }
+        if (lane == 0) cnt[U] = C;
+        int* taken = reinterpret_cast<int*>(cand_d);  // tile modes do not read distances
+        for (int u = lane; u < U; u += 32) taken[u] = 0;
+        __syncwarp();
+        // steps 5-7: draw tiles by (count desc, ty asc, tx asc); first circle above the threshold wins
+        const int ntop = min(a.top_c, U);
+        int first_tx = 0, first_ty = 0;
+        bool found = false;
+        for (int r = 0; r < ntop; ++r) {
+            long long best = -1;
+            for (int u = lane; u < U; u += 32) {
+                if (taken[u]) continue;
+                const long long c = cnt[u + 1] - cnt[u];
+                const long long v = (c << 32) | (long long)(0xffffffffu - (unsigned)u);
+                best = v > best ? v : best;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long ov = __shfl_xor_sync(kFull, best, o);
+                best = ov > best ? ov : best;
+            }
+            const int us = (int)(0xffffffffu - (unsigned)(best & 0xffffffffll));
+            __syncwarp();
+            if (lane == 0) taken[us] = 1;
+            __syncwarp();
+            const u64 ks = keys[cnt[us]];
+            const int tx0 = key_tx(ks), ty0 = key_ty(ks);
+            if (r == 0) {
+                first_tx = tx0;
+                first_ty = ty0;
+            }
+            long long circ = 0;
+            for (int u = lane; u < U; u += 32) {
+                const u64 ku = keys[cnt[u]];
+                const long long dx = (long long)key_tx(ku) - tx0, dy = (long long)key_ty(ku) - ty0;
+                if (dx > p.rlim || dx < -p.rlim || dy > p.rlim || dy < -p.rlim) continue;
+                if (dx * dx + dy * dy <= a.r2max) circ += cnt[u + 1] - cnt[u];
+            }
+            circ = warp_sum(circ);
+            if (100ll * circ > (long long)a.toler_pct * (long long)C) {
+                win_tx = tx0;
+                win_ty = ty0;
+                found = true;
+                break;
+            }
+        }
+        if (!found) {
+            win_tx = first_tx;
+            win_ty = first_ty;
+            status = 1;
+        }
+    }
+    double ox, oy;
+    if (a.mode == 0) {
+        ox = ((double)win_tx + 0.5) * tm;
+        oy = ((double)win_ty + 0.5) * tm;
+    } else if (a.mode == 1) {
+        double sx = 0.0, sy = 0.0;
+        long long m = 0;
+        for (int i = lane; i < C; i += 32) {
+            const int r = cand_rows[i];
+            const long long dx = (long long)p.tile[2 * r] - win_tx, dy = (long long)p.tile[2 * r + 1] - win_ty;
+            if (dx > p.rlim || dx < -p.rlim || dy > p.rlim || dy < -p.rlim) continue;
+            if (dx * dx + dy * dy <= a.r2max) {
+                sx += p.xy[2 * r];
+                sy += p.xy[2 * r + 1];
+                ++m;
+            }
+        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        m = warp_sum(m);
+        ox = sx / (double)m;
+        oy = sy / (double)m;
+    } else {
+        double mx = -INFINITY;
+        for (int i = lane; i < C; i += 32) mx = fmax(mx, -(double)cand_d[i] / (double)a.tau);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, o));
+        double z = 0.0, sx = 0.0, sy = 0.0;
+        for (int i = lane; i < C; i += 32) {
+            const double e = exp(-(double)cand_d[i] / (double)a.tau - mx);
+            const int r = cand_rows[i];
+            z += e;
+            sx += e * p.xy[2 * r];
+            sy += e * p.xy[2 * r + 1];
+        }
+        z = warp_sum(z);
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        ox = sx / z;
+        oy = sy / z;
+    }
+    if (lane == 0) {
+        a.xy_out[2 * w] = ox;
+        a.xy_out[2 * w + 1] = oy;
+        a.status[w] = status;
+    }
+}
+
+
+}  // namespace agg
+}  // namespace lhr

@@ -127,8 +127,8 @@ static bool is_device_ptr(const void* p) {
 
 static void free_db(lhr_db* db) {
     if (!db) return;
-    void* bufs[] = {db->X, db->Xc, db->perm, db->xy, db->tile, db->chunks, db->chunk_off,
-                    db->Xb, db->snb, db->X8, db->sn8, db->err};
+    void* bufs[] = {db->X, db->xnorm, db->Xc, db->perm, db->xy, db->tile, db->chunks, db->chunk_off,
+                    db->Xb, db->snb, db->X8, db->sn8, db->Xb_s, db->snb_s, db->X8_s, db->sn8_s, db->err};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete db;
@@ -300,7 +300,10 @@ lhr_status lhr_build_db(const float* feats, const double* xy, const int32_t* sub
     if ((e = dalloc(&db->xy, (size_t)n * 2)) != cudaSuccess) return bail(cuda_fail(e, "allocate xy"));
     if ((e = dalloc(&db->tile, (size_t)n * 2)) != cudaSuccess) return bail(cuda_fail(e, "allocate tiles"));
     if ((e = dalloc(&db->err, 1)) != cudaSuccess) return bail(cuda_fail(e, "allocate error word"));
-    if ((e = dalloc(&flag, 1)) != cudaSuccess) return bail(cuda_fail(e, "allocate flag"));
+    if ((e = dalloc(&flag, 2)) != cudaSuccess) return bail(cuda_fail(e, "allocate flag"));
+    if ((e = dalloc(&db->xnorm, (size_t)n + kSnPad)) != cudaSuccess ||
+        (e = cudaMemsetAsync(db->xnorm, 0, ((size_t)n + kSnPad) * sizeof(float), s)) != cudaSuccess)
+        return bail(cuda_fail(e, "allocate norms"));
     if (Dc && (e = dalloc(&db->Xc, (size_t)n * Dc)) != cudaSuccess) return bail(cuda_fail(e, "allocate coarse slab"));
     if (cfg->lowp & LHR_LOWP_BF16) {
         if ((e = cudaMalloc(&db->Xb, (size_t)n * D * 2)) != cudaSuccess ||
@@ -314,8 +317,24 @@ lhr_status lhr_build_db(const float* feats, const double* xy, const int32_t* sub
             (e = cudaMemsetAsync(db->sn8, 0, ((size_t)n + kSnPad) * sizeof(float2), s)) != cudaSuccess)
             return bail(cuda_fail(e, "allocate FP8 copy"));
     }
+    if (cfg->lowp && n >= (int64_t)kSampleStride * kSampleMinRows) {
+        // every 64th row of each copy, for the pilot pass of the low-precision path
+        db->sample_stride = kSampleStride;
+        db->n_sample = (n + kSampleStride - 1) / kSampleStride;
+        const size_t ns = (size_t)db->n_sample;
+        if ((cfg->lowp & LHR_LOWP_BF16) &&
+            ((e = cudaMalloc(&db->Xb_s, ns * D * 2)) != cudaSuccess ||
+             (e = dalloc(&db->snb_s, ns + kSnPad)) != cudaSuccess ||
+             (e = cudaMemsetAsync(db->snb_s, 0, (ns + kSnPad) * sizeof(float2), s)) != cudaSuccess))
+            return bail(cuda_fail(e, "allocate BF16 sample"));
+        if ((cfg->lowp & LHR_LOWP_FP8) &&
+            ((e = cudaMalloc(&db->X8_s, ns * D)) != cudaSuccess ||
+             (e = dalloc(&db->sn8_s, ns + kSnPad)) != cudaSuccess ||
+             (e = cudaMemsetAsync(db->sn8_s, 0, (ns + kSnPad) * sizeof(float2), s)) != cudaSuccess))
+            return bail(cuda_fail(e, "allocate FP8 sample"));
+    }
     cudaMemsetAsync(db->err, 0, sizeof(int32_t), s);
-    cudaMemsetAsync(flag, 0, sizeof(int32_t), s);
+    cudaMemsetAsync(flag, 0, 2 * sizeof(int32_t), s);
     const bool feats_dev = is_device_ptr(feats);
     if (need_perm) {
         if ((e = dalloc(&db->perm, (size_t)n)) != cudaSuccess) return bail(cuda_fail(e, "allocate perm"));
@@ -362,10 +381,14 @@ lhr_status lhr_build_db(const float* feats, const double* xy, const int32_t* sub
     cudaMemcpyAsync(db->chunk_off, db->chunk_off_h.data(), db->chunk_off_h.size() * sizeof(int32_t),
                     cudaMemcpyHostToDevice, s);
     if ((e = launch_build_derived(db, s)) != cudaSuccess) return bail(cuda_fail(e, "derived arrays"));
-    int32_t flag_h = 0;
-    cudaMemcpyAsync(&flag_h, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if ((e = launch_norms(db, reinterpret_cast<unsigned*>(flag + 1), s)) != cudaSuccess)
+        return bail(cuda_fail(e, "norms"));
+    int32_t flag_h2[2] = {0, 0};
+    cudaMemcpyAsync(flag_h2, flag, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(cuda_fail(e, "build"));
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(e, "build"));
+    const int32_t flag_h = flag_h2[0];
+    std::memcpy(&db->xnorm_max, &flag_h2[1], sizeof(float));
     if (flag_h & 1) return bail(fail(LHR_ERR_INVALID_ARG, "features contain a non-finite value"));
     if (flag_h & 2) return bail(fail(LHR_ERR_INVALID_ARG, "xy contains a non-finite value or a tile outside int32"));
     cudaFree(flag);

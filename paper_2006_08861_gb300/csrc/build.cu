@@ -86,6 +86,37 @@ __global__ void quantize_kernel(const float* X, int64_t n, int D, void* codes, f
     }
 }
 
+// One warp per row: FP32 squared norm, and the running maximum (as float
+// bits, order-preserving for non-negative values).
+__global__ void norms_kernel(const float* X, int64_t n, int D, float* norm, unsigned* max_bits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned mx = 0u;
+    for (int64_t r = wid; r < n; r += nw) {
+        const float* x = X + r * D;
+        float acc = 0.f;
+        for (int j = lane; j < D; j += 32) acc = fmaf(x[j], x[j], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (lane == 0) norm[r] = acc;
+        mx = max(mx, __float_as_uint(acc));
+    }
+    if (lane == 0) atomicMax(max_bits, mx);
+}
+
+// Rows 0, stride, 2 stride, ... of a code array (row_bytes % 16 == 0) and of
+// its (s, norm) pairs.
+__global__ void sample_rows_kernel(const uint4* codes, const float2* sn, int64_t ns, int stride, int row_u4,
+                                   uint4* codes_s, float2* sn_s) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns * row_u4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / row_u4, c = i % row_u4;
+        codes_s[i] = codes[r * stride * row_u4 + c];
+        if (c == 0) sn_s[r] = sn[r * stride];
+    }
+}
+
 int grid_for(int64_t work, int sms) {
     const int64_t b = (work + 255) / 256;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sms * 8));
@@ -109,6 +140,12 @@ cudaError_t launch_tiles(const double* xy, int64_t n, double t, int32_t* tile, i
     return cudaGetLastError();
 }
 
+cudaError_t launch_norms(const lhr_db* db, unsigned* max_bits, cudaStream_t stream) {
+    const int grid = (int)std::min<int64_t>((db->n + 7) / 8, (int64_t)db->sms * 16);
+    norms_kernel<<<grid, 256, 0, stream>>>(db->X, db->n, db->dim, db->xnorm, max_bits);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_build_derived(lhr_db* db, cudaStream_t stream) {
     cudaError_t e;
     if (db->Xc) {
@@ -123,6 +160,20 @@ cudaError_t launch_build_derived(lhr_db* db, cudaStream_t stream) {
     }
     if (db->X8) {
         quantize_kernel<true><<<qgrid, 256, 0, stream>>>(db->X, db->n, db->dim, db->X8, db->sn8);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (db->Xb_s) {
+        const int row_u4 = db->dim * 2 / 16;
+        sample_rows_kernel<<<grid_for(db->n_sample * row_u4, db->sms), 256, 0, stream>>>(
+            reinterpret_cast<const uint4*>(db->Xb), db->snb, db->n_sample, db->sample_stride, row_u4,
+            reinterpret_cast<uint4*>(db->Xb_s), db->snb_s);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (db->X8_s) {
+        const int row_u4 = db->dim / 16;
+        sample_rows_kernel<<<grid_for(db->n_sample * row_u4, db->sms), 256, 0, stream>>>(
+            reinterpret_cast<const uint4*>(db->X8), db->sn8, db->n_sample, db->sample_stride, row_u4,
+            reinterpret_cast<uint4*>(db->X8_s), db->sn8_s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

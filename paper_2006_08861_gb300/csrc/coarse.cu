@@ -4,19 +4,26 @@
 // this library's hierarchical form. The FFT-magnitude feature of §3 puts its
 // low frequencies first, which is what a prefix keeps.)
 //
-// Kernel 1 (coarse_kernel): one thread per row (grid-stride) computes the
-//   squared prefix distance to up to 8 frames with packed FP32 FMAs, writes it
-//   to scratch (frames x n floats, L2-resident at building scale) and counts
-//   the distance's top 11 value bits into a per-frame 2048-bin histogram
-//   (shared-memory bins, flushed once per CTA).
-// Kernel 2 (shortlist_kernel): one CTA per frame. The candidate key is
-//   (prefix distance bits << 32 | row); the S-th smallest key is located by a
-//   radix select that starts from kernel 1's histogram and refines by further
-//   11-bit digits only while the boundary bin holds more than kBinCap keys.
-//   One pass then collects every key below the boundary bin plus the boundary
-//   bin itself, which is sorted (bitonic, shared memory) to take exactly S.
-//   The S rows are re-scored on the full feature (warp per row) and each warp
-//   keeps a register top-k list; 32 lists merge into the frame's result.
+// The candidate key of a row is (prefix distance bits << 32 | row); the
+// shortlist is the S smallest keys, found by a radix select on 11-bit digits.
+//
+// K1 coarse_kernel: thread per row (grid-stride), squared prefix distance to
+//   up to 8 frames with packed FP32 FMAs, written to scratch (frames x n
+//   floats, L2-resident at building scale), and a per-frame 2048-bin
+//   histogram of the key's top digit (shared-memory bins, flushed once per
+//   CTA).
+// K2 collect_kernel: 16 CTAs per frame. Each finds, from the histogram, the
+//   bin holding the S-th key, then scans its slice of the frame's distances
+//   and appends (warp-aggregated atomics) every row below that bin to the
+//   frame's direct list and every key inside it to the frame's boundary list.
+//   If the boundary bin holds more keys than one CTA can sort (kBinCap), the
+//   frame is flagged and left to K3's refinement path.
+// K3 shortlist_kernel: one CTA per frame. Sorts the boundary keys (bitonic,
+//   shared memory) to take exactly S rows (or, for a flagged frame, refines
+//   the radix select by further 11-bit digits over the frame's distances and
+//   collects in place), re-scores the S rows on the full feature (warp per
+//   row, loads batched four rows deep) and keeps the top k in warp-register
+//   lists merged at the end.
 #include "common.cuh"
 #include "internal.h"
 
@@ -28,6 +35,12 @@ constexpr int kBins = 2048;      // 11-bit digits
 constexpr int kBinCap = 4096;    // boundary-bin keys sorted in shared memory
 constexpr int kSelThreads = 1024;
 constexpr int kMaxShortlist = 4096;
+constexpr int kParts = 16;       // collect CTAs per frame
+constexpr int kColThreads = 256;
+constexpr int kCtl = 8;          // control words per frame
+
+// Per-frame control words written by K2, read by K3.
+enum { kDirect = 0, kInBin = 1, kRefine = 2, kNeed = 3, kLo = 4 /* u64 at 4..5 */, kHi = 6 /* u64 at 6..7 */ };
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
@@ -46,7 +59,7 @@ __global__ void __launch_bounds__(256) coarse_kernel(const float* __restrict__ X
         qs[f][c] = (f < nf && c < d4) ? reinterpret_cast<const float4*>(Q + (size_t)(f0 + f) * qld)[c]
                                       : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int i = threadIdx.x; i < kFB * kBins; i += blockDim.x) (&h[0][0])[i] = 0u;
+    for (int i = threadIdx.x; i < nf * kBins; i += blockDim.x) (&h[0][0])[i] = 0u;
     __syncthreads();
     const float2 neg1 = f2(-1.f, -1.f);
     for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
@@ -80,15 +93,17 @@ __global__ void __launch_bounds__(256) coarse_kernel(const float* __restrict__ X
     }
 }
 
-// Block-wide exclusive scan helper: finds the bin holding the `need`-th
-// smallest key. Writes (bin, keys below it, keys in it) to out[0..2].
+// Finds the bin holding the `need`-th smallest key of a 2048-bin histogram in
+// shared memory, with a block of THREADS threads. Writes (bin, keys below it,
+// keys in it) to out[0..2]. `tmp` holds THREADS / 32 words.
+template <int THREADS>
 __device__ void find_bin(const unsigned* hsm, unsigned need, unsigned* out, unsigned* tmp) {
-    // 2048 bins over 1024 threads: two bins per thread.
-    const int t = threadIdx.x;
-    const unsigned a = hsm[2 * t], b = hsm[2 * t + 1];
-    unsigned s = a + b;
-    // inclusive scan of s over the block
-    const int lane = t & 31, w = t >> 5;
+    constexpr int kPer = kBins / THREADS;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    unsigned own = 0;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) own += hsm[t * kPer + i];
+    unsigned s = own;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned v = __shfl_up_sync(kFull, s, o);
@@ -97,24 +112,27 @@ __device__ void find_bin(const unsigned* hsm, unsigned need, unsigned* out, unsi
     if (lane == 31) tmp[w] = s;
     __syncthreads();
     if (w == 0) {
-        unsigned v = tmp[lane];
+        unsigned v = lane < THREADS / 32 ? tmp[lane] : 0u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned u = __shfl_up_sync(kFull, v, o);
             if (lane >= o) v += u;
         }
-        tmp[lane] = v;
+        if (lane < THREADS / 32) tmp[lane] = v;
     }
     __syncthreads();
-    const unsigned before = (w > 0 ? tmp[w - 1] : 0u) + s - (a + b);  // exclusive prefix of bin 2t
-    if (before < need && need <= before + a) {
-        out[0] = 2 * t;
-        out[1] = before;
-        out[2] = a;
-    } else if (before + a < need && need <= before + a + b) {
-        out[0] = 2 * t + 1;
-        out[1] = before + a;
-        out[2] = b;
+    unsigned before = (w > 0 ? tmp[w - 1] : 0u) + s - own;  // keys below this thread's first bin
+    if (before < need && need <= before + own) {
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const unsigned c = hsm[t * kPer + i];
+            if (before < need && need <= before + c) {
+                out[0] = t * kPer + i;
+                out[1] = before;
+                out[2] = c;
+            }
+            before += c;
+        }
     }
     __syncthreads();
 }
@@ -123,11 +141,82 @@ __device__ __forceinline__ u64 coarse_key(const float* dcf, int64_t row) {
     return ((u64)__float_as_uint(dcf[row]) << 32) | (u64)row;
 }
 
+// Appends `take` rows / keys of a warp at consecutive positions of a list.
+__device__ __forceinline__ void warp_append(bool take, unsigned* counter, unsigned cap, int* rows, u64* keys,
+                                            int64_t row, u64 key, int lane) {
+    const unsigned m = __ballot_sync(kFull, take);
+    if (!m) return;
+    unsigned base = 0;
+    const int leader = __ffs(m) - 1;
+    if (lane == leader) base = atomicAdd(counter, (unsigned)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    const unsigned pos = base + __popc(m & ((1u << lane) - 1u));
+    if (take && pos < cap) {
+        if (rows) rows[pos] = (int)row;
+        else keys[pos] = key;
+    }
+}
+
+__global__ void __launch_bounds__(kColThreads) collect_kernel(const float* __restrict__ dcall, int64_t n,
+                                                              const unsigned* __restrict__ hist, int S,
+                                                              unsigned* __restrict__ ctl_all,
+                                                              int* __restrict__ direct_all,
+                                                              u64* __restrict__ bin_all) {
+    __shared__ unsigned hsm[kBins];
+    __shared__ unsigned res[4];
+    __shared__ unsigned tmp[kColThreads / 32];
+    const int f = blockIdx.y, part = blockIdx.x;
+    const int t = threadIdx.x, lane = t & 31;
+    const float* dcf = dcall + (size_t)f * n;
+    unsigned* ctl = ctl_all + (size_t)f * kCtl;
+    int* direct = direct_all + (size_t)f * kMaxShortlist;
+    u64* bins = bin_all + (size_t)f * kBinCap;
+    const bool take_all = n <= S;
+    u64 lo = ~0ull, hi = ~0ull;
+    if (!take_all) {
+        for (int i = t; i < kBins; i += kColThreads) hsm[i] = hist[(size_t)f * kBins + i];
+        __syncthreads();
+        find_bin<kColThreads>(hsm, (unsigned)S, res, tmp);
+        if (res[2] > (unsigned)kBinCap) {
+            if (part == 0 && t == 0) ctl[kRefine] = 1u;
+            return;
+        }
+        lo = (u64)res[0] << 52;
+        hi = lo + (1ull << 52);
+        if (part == 0 && t == 0) {
+            ctl[kNeed] = (unsigned)S - res[1];
+            *reinterpret_cast<u64*>(&ctl[kLo]) = lo;
+            *reinterpret_cast<u64*>(&ctl[kHi]) = hi;
+        }
+    }
+    const int64_t per = (n + kParts - 1) / kParts;
+    const int64_t r0 = part * per, r1 = min(n, r0 + per);
+    // four rows per thread per pass keep several loads in flight
+    for (int64_t base = r0; base < r1; base += 4 * kColThreads) {
+        u64 key[4];
+        int64_t row[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            row[j] = base + j * kColThreads + t;
+            key[j] = row[j] < r1 ? coarse_key(dcf, row[j]) : kKeyEmpty;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool valid = row[j] < r1;
+            const bool d = valid && (take_all || key[j] < lo);
+            const bool b = valid && !d && key[j] < hi;
+            warp_append(d, &ctl[kDirect], kMaxShortlist, direct, nullptr, row[j], 0, lane);
+            warp_append(b, &ctl[kInBin], kBinCap, nullptr, bins, row[j], key[j], lane);
+        }
+    }
+}
+
 template <int CPL>
 __global__ void __launch_bounds__(kSelThreads, 1)
-    shortlist_kernel(const float* __restrict__ X, int D, int64_t n, const float* __restrict__ Q, int nq,
+    shortlist_kernel(const float* __restrict__ X, int D, int64_t n, const float* __restrict__ Q,
                      const float* __restrict__ dcall, const unsigned* __restrict__ hist, int S, int k,
-                     int64_t* __restrict__ idx, float* __restrict__ dist) {
+                     const unsigned* __restrict__ ctl_all, const int* __restrict__ direct_all,
+                     const u64* __restrict__ bin_all, int64_t* __restrict__ idx, float* __restrict__ dist) {
     extern __shared__ __align__(16) unsigned char smem[];
     u64* bin_keys = reinterpret_cast<u64*>(smem);                       // kBinCap
     int* short_rows = reinterpret_cast<int*>(bin_keys + kBinCap);       // kMaxShortlist
@@ -139,18 +228,30 @@ __global__ void __launch_bounds__(kSelThreads, 1)
     const int f = blockIdx.x;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const float* dcf = dcall + (size_t)f * n;
-    const int sel = (int)((int64_t)S < n ? (int64_t)S : n);
+    const unsigned* gctl = ctl_all + (size_t)f * kCtl;
+    const bool take_all = n <= S;
+    const bool refine = !take_all && gctl[kRefine] != 0u;
+    unsigned direct, need = 0, nb = 0;
 
-    u64 lo = 0, hi = 0;         // boundary bin [lo, hi) of keys
-    unsigned need = (unsigned)sel;
-    bool take_all = (n <= S);
-    if (!take_all) {
+    if (!refine) {
+        // K2 collected the shortlist's rows below the boundary bin and the bin's keys
+        direct = min(gctl[kDirect], (unsigned)kMaxShortlist);
+        for (unsigned i = t; i < direct; i += blockDim.x) short_rows[i] = direct_all[(size_t)f * kMaxShortlist + i];
+        if (!take_all) {
+            need = gctl[kNeed];
+            nb = min(gctl[kInBin], (unsigned)kBinCap);
+            for (unsigned i = t; i < nb; i += blockDim.x) bin_keys[i] = bin_all[(size_t)f * kBinCap + i];
+        }
+    } else {
+        // The boundary bin overflows: refine by further digits over the frame's keys.
+        const int sel = (int)((int64_t)S < n ? (int64_t)S : n);
+        need = (unsigned)sel;
         for (int i = t; i < kBins; i += blockDim.x) hsm[i] = hist[(size_t)f * kBins + i];
         __syncthreads();
-        find_bin(hsm, need, ctl, tmp);
+        find_bin<kSelThreads>(hsm, need, ctl, tmp);
         int shift = 52;
-        lo = (u64)ctl[0] << shift;
-        hi = lo + (1ull << shift);
+        u64 lo = (u64)ctl[0] << shift;
+        u64 hi = lo + (1ull << shift);
         need -= ctl[1];
         unsigned in_bin = ctl[2];
         while (in_bin > (unsigned)kBinCap && shift > 0) {
@@ -165,34 +266,34 @@ __global__ void __launch_bounds__(kSelThreads, 1)
                     atomicAdd(&hsm[(unsigned)((key >> nshift) & ((1ull << dbits) - 1))], 1u);
             }
             __syncthreads();
-            find_bin(hsm, need, ctl, tmp);
+            find_bin<kSelThreads>(hsm, need, ctl, tmp);
             lo += (u64)ctl[0] << nshift;
             hi = lo + (1ull << nshift);
             need -= ctl[1];
             in_bin = ctl[2];
             shift = nshift;
         }
-    }
-    // Collection pass.
-    if (t == 0) {
-        ctl[4] = 0u;  // rows taken directly
-        ctl[5] = 0u;  // keys in the boundary bin
-    }
-    __syncthreads();
-    for (int64_t r = t; r < n; r += blockDim.x) {
-        const u64 key = coarse_key(dcf, r);
-        if (take_all || key < lo) {
-            const unsigned pos = atomicAdd(&ctl[4], 1u);
-            short_rows[pos] = (int)r;
-        } else if (key < hi) {
-            const unsigned pos = atomicAdd(&ctl[5], 1u);
-            if (pos < (unsigned)kBinCap) bin_keys[pos] = key;
+        if (t == 0) {
+            ctl[4] = 0u;
+            ctl[5] = 0u;
         }
+        __syncthreads();
+        for (int64_t r = t; r < n; r += blockDim.x) {
+            const u64 key = coarse_key(dcf, r);
+            if (key < lo) {
+                const unsigned pos = atomicAdd(&ctl[4], 1u);
+                if (pos < (unsigned)kMaxShortlist) short_rows[pos] = (int)r;
+            } else if (key < hi) {
+                const unsigned pos = atomicAdd(&ctl[5], 1u);
+                if (pos < (unsigned)kBinCap) bin_keys[pos] = key;
+            }
+        }
+        __syncthreads();
+        direct = min(ctl[4], (unsigned)kMaxShortlist);
+        nb = min(ctl[5], (unsigned)kBinCap);
     }
     __syncthreads();
-    const unsigned direct = ctl[4];
     if (!take_all) {
-        const unsigned nb = min(ctl[5], (unsigned)kBinCap);
         unsigned p2 = 1;
         while (p2 < nb) p2 <<= 1;
         for (unsigned i = nb + t; i < p2; i += blockDim.x) bin_keys[i] = kKeyEmpty;
@@ -213,12 +314,14 @@ __global__ void __launch_bounds__(kSelThreads, 1)
                 __syncthreads();
             }
         }
-        for (unsigned i = t; i < need; i += blockDim.x) short_rows[direct + i] = (int)key_row(bin_keys[i]);
+        need = min(need, nb);
+        for (unsigned i = t; i < need && direct + i < (unsigned)kMaxShortlist; i += blockDim.x)
+            short_rows[direct + i] = (int)key_row(bin_keys[i]);
         __syncthreads();
     }
-    const int total = take_all ? (int)direct : (int)(direct + need);
+    const int total = (int)min(direct + need, (unsigned)kMaxShortlist);
 
-    // Re-rank on the full feature: warp per shortlisted row.
+    // Re-rank on the full feature: warp per shortlisted row, four rows in flight.
     const int D4 = D / 4;
     float4 qv[CPL];
 #pragma unroll
@@ -229,28 +332,47 @@ __global__ void __launch_bounds__(kSelThreads, 1)
     const float2 neg1 = f2(-1.f, -1.f);
     u64 L = kKeyEmpty;
     u64 thr = kKeyEmpty;
-    for (int i = warp; i < total; i += kSelThreads / 32) {
-        const int r = short_rows[i];
-        const float4* xr = reinterpret_cast<const float4*>(X + (size_t)r * D);
-        float2 acc = f2(0.f, 0.f);
+    constexpr int kWarps = kSelThreads / 32;
+    for (int i0 = warp; i0 < total; i0 += 4 * kWarps) {
+        int r[4];
+        float4 x[4][CPL];
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) {
-            const int c = lane + 32 * j;
-            if (c < D4) {
-                const float4 x = __ldg(xr + c);
-                float2 a = __ffma2_rn(f2(x.x, x.y), neg1, f2(qv[j].x, qv[j].y));
-                float2 b = __ffma2_rn(f2(x.z, x.w), neg1, f2(qv[j].z, qv[j].w));
-                acc = __ffma2_rn(a, a, acc);
-                acc = __ffma2_rn(b, b, acc);
+        for (int b = 0; b < 4; ++b) {
+            const int i = i0 + b * kWarps;
+            r[b] = i < total ? short_rows[i] : -1;
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                const int c = lane + 32 * j;
+                x[b][j] = (r[b] >= 0 && c < D4) ? __ldg(reinterpret_cast<const float4*>(X + (size_t)r[b] * D) + c)
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
-        float d = acc.x + acc.y;
+        float d[4];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
-        const u64 key = make_key(d, (uint32_t)r);
-        if (key < thr) {
-            list_insert(L, key, k, lane);
-            thr = __shfl_sync(kFull, L, k - 1);
+        for (int b = 0; b < 4; ++b) {
+            float2 acc = f2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                float2 a = __ffma2_rn(f2(x[b][j].x, x[b][j].y), neg1, f2(qv[j].x, qv[j].y));
+                float2 c2 = __ffma2_rn(f2(x[b][j].z, x[b][j].w), neg1, f2(qv[j].z, qv[j].w));
+                acc = __ffma2_rn(a, a, acc);
+                acc = __ffma2_rn(c2, c2, acc);
+            }
+            d[b] = acc.x + acc.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) d[b] += __shfl_xor_sync(kFull, d[b], o);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            if (r[b] < 0) continue;
+            const u64 key = make_key(d[b], (uint32_t)r[b]);
+            if (key < thr) {
+                list_insert(L, key, k, lane);
+                thr = __shfl_sync(kFull, L, k - 1);
+            }
         }
     }
     wl[warp * 32 + lane] = L;
@@ -278,28 +400,45 @@ size_t shortlist_smem() {
            (8 + 32) * sizeof(unsigned);
 }
 
+struct CoarseLayout {
+    size_t dc, hist, ctl, direct, bins, total;
+};
+
+CoarseLayout layout(const lhr_db* db, int nq) {
+    CoarseLayout L{};
+    L.dc = 0;
+    L.hist = align256((size_t)nq * db->n * sizeof(float));
+    L.ctl = L.hist + (size_t)nq * kBins * sizeof(unsigned);  // hist and ctl are cleared together
+    L.direct = align256(L.ctl + (size_t)nq * kCtl * sizeof(unsigned));
+    L.bins = align256(L.direct + (size_t)nq * kMaxShortlist * sizeof(int));
+    L.total = align256(L.bins + (size_t)nq * kBinCap * sizeof(u64));
+    return L;
+}
+
 }  // namespace
 
-size_t coarse_scratch_bytes(const lhr_db* db, int nq, int /*shortlist*/) {
-    return align256((size_t)nq * db->n * sizeof(float)) + align256((size_t)nq * kBins * sizeof(unsigned));
-}
+size_t coarse_scratch_bytes(const lhr_db* db, int nq, int /*shortlist*/) { return layout(db, nq).total; }
 
 cudaError_t launch_coarse(const lhr_db* db, const float* q, int nq, int shortlist, int k, int64_t* idx, float* dist,
                           void* scratch, cudaStream_t stream) {
-    float* dcbuf = reinterpret_cast<float*>(scratch);
-    unsigned* hist = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(scratch) +
-                                                 align256((size_t)nq * db->n * sizeof(float)));
-    cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)nq * kBins * sizeof(unsigned), stream);
+    const CoarseLayout Lo = layout(db, nq);
+    unsigned char* base = reinterpret_cast<unsigned char*>(scratch);
+    float* dcbuf = reinterpret_cast<float*>(base + Lo.dc);
+    unsigned* hist = reinterpret_cast<unsigned*>(base + Lo.hist);
+    unsigned* ctl = reinterpret_cast<unsigned*>(base + Lo.ctl);
+    int* direct = reinterpret_cast<int*>(base + Lo.direct);
+    u64* bins = reinterpret_cast<u64*>(base + Lo.bins);
+    cudaError_t e = cudaMemsetAsync(hist, 0, Lo.direct - Lo.hist, stream);
     if (e != cudaSuccess) return e;
     const int64_t nblk = (db->n + 255) / 256;
     dim3 g1((unsigned)std::min<int64_t>(nblk, (int64_t)db->sms * 2), (nq + kFB - 1) / kFB);
     const int dc4 = db->coarse_dim / 4;
-#define LHR_CK(C)                                                                                           \
-    do {                                                                                                    \
-        const size_t csm = sizeof(float4) * kFB * (C) + sizeof(unsigned) * kFB * kBins;                     \
-        e = cudaFuncSetAttribute(coarse_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);  \
-        if (e != cudaSuccess) return e;                                                                     \
-        ProfScope ps("coarse_kernel", stream);                                                              \
+#define LHR_CK(C)                                                                                                \
+    do {                                                                                                         \
+        const size_t csm = sizeof(float4) * kFB * (C) + sizeof(unsigned) * kFB * kBins;                          \
+        e = cudaFuncSetAttribute(coarse_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);       \
+        if (e != cudaSuccess) return e;                                                                          \
+        ProfScope ps("coarse_kernel", stream);                                                                   \
         coarse_kernel<C><<<g1, 256, csm, stream>>>(db->Xc, db->n, db->coarse_dim, q, db->dim, nq, dcbuf, hist); \
     } while (0)
     if (dc4 <= 8) LHR_CK(8);
@@ -307,8 +446,12 @@ cudaError_t launch_coarse(const lhr_db* db, const float* q, int nq, int shortlis
     else if (dc4 <= 32) LHR_CK(32);
     else return cudaErrorInvalidValue;
 #undef LHR_CK
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+        ProfScope ps("collect_kernel", stream);
+        collect_kernel<<<dim3(kParts, nq), kColThreads, 0, stream>>>(dcbuf, db->n, hist, shortlist, ctl, direct, bins);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     const size_t sm = shortlist_smem();
     const int d4 = db->dim / 4;
     const int cpl = d4 <= 32 ? 1 : (d4 <= 64 ? 2 : 4);
@@ -317,8 +460,8 @@ cudaError_t launch_coarse(const lhr_db* db, const float* q, int nq, int shortlis
         e = cudaFuncSetAttribute(shortlist_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
         if (e != cudaSuccess) return e;                                                                      \
         ProfScope ps("shortlist_kernel", stream);                                                            \
-        shortlist_kernel<C><<<nq, kSelThreads, sm, stream>>>(db->X, db->dim, db->n, q, nq, dcbuf, hist,     \
-                                                             shortlist, k, idx, dist);                       \
+        shortlist_kernel<C><<<nq, kSelThreads, sm, stream>>>(db->X, db->dim, db->n, q, dcbuf, hist,          \
+                                                             shortlist, k, ctl, direct, bins, idx, dist);    \
     } while (0)
     if (cpl == 1) LHR_SL(1);
     else if (cpl == 2) LHR_SL(2);

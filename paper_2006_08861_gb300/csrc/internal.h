@@ -12,6 +12,8 @@
 #include "../../include/lhr.h"
 
 constexpr int kSnPad = 256;
+constexpr int kSampleStride = 64;     // pilot sample: every 64th row
+constexpr int kSampleMinRows = 4096;  // sample only databases of at least 64 x 4096 rows
 
 struct lhr_db {
     int device = 0;
@@ -27,6 +29,8 @@ struct lhr_db {
     // one contiguous range. perm[i] is the caller's row of internal row i
     // (nullptr when the order is the caller's).
     float* X = nullptr;         // n x dim
+    float* xnorm = nullptr;     // n + kSnPad: FP32 ||x||^2 per row (internal order), zero padded
+    float xnorm_max = 0.f;      // max over rows of ||x||^2
     float* Xc = nullptr;        // n x coarse_dim (coarse prefix slab), or nullptr
     int32_t* perm = nullptr;    // n, or nullptr
     // Caller's order.
@@ -47,6 +51,13 @@ struct lhr_db {
     // kSnPad rows of zero padding so whole-tile bulk copies stay in bounds.
     void* Xb = nullptr;   float2* snb = nullptr;   // BF16
     void* X8 = nullptr;   float2* sn8 = nullptr;   // FP8 e4m3
+    // Every sample_stride-th row of each copy (rows 0, stride, 2 stride, ...),
+    // n_sample rows, with its (s, norm) pairs: the pilot pass that sets the
+    // low-precision path's per-query score threshold runs over these.
+    int sample_stride = 1;
+    int64_t n_sample = 0;
+    void* Xb_s = nullptr; float2* snb_s = nullptr;
+    void* X8_s = nullptr; float2* sn8_s = nullptr;
 
     int32_t* err = nullptr;  // device error word (lhr_db_error)
 };
@@ -120,5 +131,6 @@ cudaError_t launch_check_finite(const float* x, int64_t count, int32_t* flag, cu
 cudaError_t launch_gather_rows(const float* src, const int32_t* perm, int64_t n, int dim, float* dst,
                                cudaStream_t stream);
 cudaError_t launch_tiles(const double* xy, int64_t n, double t, int32_t* tile, int32_t* flag, cudaStream_t stream);
+cudaError_t launch_norms(const lhr_db* db, unsigned* max_bits, cudaStream_t stream);
 
 }  // namespace lhr

@@ -1,5 +1,5 @@
 // Low-precision form: tensor-core scores over a BF16 / FP8-e4m3 copy of the
-// database with per-row scales, a fused per-query top-W shortlist, and an
+// database with per-row scales, a per-query top-W shortlist by score, and an
 // FP32 re-rank of the shortlist on the FP32 rows (the paper scores FP
 // features directly, §3.1; this form trades a widened shortlist for
 // tensor-core throughput when many query frames are batched).
@@ -7,8 +7,10 @@
 // score(q, x_j) = n_j - 2 s_q s_j (q^ . x^_j)        (||q||^2 dropped: constant per query)
 //   q^, x^_j : quantised codes, s_q, s_j : per-vector scales,
 //   n_j = s_j^2 ||x^_j||^2 (built with the database).
+// Keys are (orderable score bits << 32 | row); the shortlist is the W
+// smallest keys, exactly.
 //
-// tc_topw_kernel, one CTA per (128-query block, database chunk), 6 warps:
+// tc_kernel, one CTA per (128-query block, database chunk), 6 warps:
 //   warp 0  producer: TMA (cp.async.bulk.tensor.2d, 128-byte swizzle) of the
 //           block's 128 query codes once, then the chunk's 128-row tiles, one
 //           128-byte K slice per stage, through a 6-stage mbarrier ring; plus
@@ -17,15 +19,26 @@
 //           N = 128 rows, K = 16 BF16 / 32 FP8 per instruction) into two
 //           128-column FP32 accumulators in TMEM, alternating per tile;
 //           tcgen05.commit frees smem stages and publishes accumulators.
-//   warps 2-5 epilogue: thread = query (TMEM lane); tcgen05.ld 32 columns at a
-//           time, score = fma(-2 s_q, s_j dot, n_j), compare with the thread's
-//           running W-th best and append survivors to a 32-entry shared-memory
-//           buffer, merged into the thread's sorted top-W list (local memory)
-//           only when full. Scores never leave the SM.
-// merge_rerank_kernel, one warp per query: the per-chunk top-W lists are cut
-//   at the smallest chunk's W-th key (a bound on the global W-th), sorted,
-//   the first W rows are re-scored with the exact FP32 direct form and the
-//   top k kept (warp-register list).
+//   warps 2-5 epilogue: thread = query (its TMEM lane); tcgen05.ld 32 columns
+//           at a time, score = fma(-2 s_q, s_j dot, n_j). What happens to a
+//           score depends on the pass:
+//     pilot  over every 64th database row (a copy built with the database):
+//            the thread keeps its query's 8 smallest sample keys in a static
+//            register network;
+//     main   over the database: the query's threshold key tau is the 8th
+//            smallest sample key (so at least 8 keys, about 8 x 64 in
+//            expectation, are <= tau); every key <= tau is appended to the
+//            query's candidate buffer (rare, one atomic each). Scores never
+//            leave the SM otherwise.
+//     full   (fallback, and the only pass for databases too small to sample):
+//            the thread keeps its query's exact top W of the chunk in local
+//            memory, filled through a 32-entry shared-memory survivor
+//            buffer. When run after a main pass it exits at once unless a
+//            query of its block collected fewer than W or more than kCap keys.
+// merge_rerank_kernel, one warp per query: the shortlist is the W smallest
+//   keys of the query's candidate buffer (or, after the full pass, of its
+//   per-chunk lists cut at the smallest chunk's W-th key); its rows are
+//   re-scored with the exact FP32 direct form and the top k kept.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -45,7 +58,6 @@ constexpr int kSliceTile = kTile * kSliceBytes;  // 16 KB per tile slice
 constexpr int kStages = 6;
 constexpr int kBuf = 32;          // survivor buffer entries per epilogue thread
 constexpr int kThreads = 192;
-constexpr int kMergeCap = 512;    // candidate keys sorted per query in the merge
 
 // ------------------------------------------------------------------ PTX
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, u64* bar) {
@@ -122,18 +134,44 @@ __device__ __forceinline__ u64 score_key(float t, uint32_t row) {
     return ((u64)u << 32) | row;
 }
 
+
+enum { kModePilot = 0, kModeMain = 1, kModeFull = 2 };
+constexpr int kPilotR = 8;        // sample keys kept per query by the pilot pass
+constexpr int kCap = 2048;        // candidate keys kept per query by the main pass
+constexpr int kMergeWarps = 4;
+
 struct TcParams {
     int64_t n;
-    int slices;       // D * elem / 128
-    int chunk_rows;   // multiple of kTile
+    int slices;          // D * elem / 128
+    int chunk_rows;      // multiple of kTile
     int nchunks;
-    const float2* sn; // per row (s_j, n_j), padded
-    const float* qm;  // per padded query: -2 s_q (0 for padding)
+    const float2* sn;    // per row (s_j, n_j), padded
+    const float* qm;     // per padded query: -2 s_q (0 for padding)
     int nq;
     int W;
-    u64* partial;     // [query][chunk][W]
+    u64* partial;        // full: [query][chunk][W]; pilot: [query][chunk][kPilotR]
+    const u64* pilot;    // main: the pilot lists [query][pchunks][kPilotR]
+    int pchunks;
+    u64* cand;           // main: [query][kCap]
+    unsigned* cnt;       // main: keys seen per query; full: nullptr = always run
     int* err;
 };
+
+__device__ __forceinline__ float key_score(u64 key) {
+    const uint32_t u = (uint32_t)(key >> 32);
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// Sorted register network of kPilotR keys (static indices only).
+__device__ __forceinline__ void net_insert(u64 (&net)[kPilotR], u64 key) {
+    if (key >= net[kPilotR - 1]) return;
+#pragma unroll
+    for (int i = kPilotR - 1; i > 0; --i) {
+        const u64 prev = net[i - 1];
+        net[i] = key < prev ? prev : (key < net[i] ? key : net[i]);
+    }
+    net[0] = key < net[0] ? key : net[0];
+}
 
 template <int WMAX>
 __device__ __noinline__ void flush_buffer(u64* list, const u64* buf, int stride, int nb, int W) {
@@ -163,19 +201,32 @@ __device__ __noinline__ void flush_buffer(u64* list, const u64* buf, int stride,
     for (int o = 0; o < W; ++o) list[o] = out[o];
 }
 
-template <bool kFp8, int WMAX>
+template <bool kFp8, int MODE, int WMAX>
 __global__ void __launch_bounds__(kThreads, 1)
-    tc_topw_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const TcParams p) {
+    tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
     extern __shared__ unsigned char smem_raw[];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int chunk = blockIdx.x, qblock = blockIdx.y;
+    if (MODE == kModeFull && p.cnt != nullptr) {
+        // fallback after a main pass: run only if a query of this block needs it
+        bool need = false;
+        if (threadIdx.x < kTile) {
+            const int64_t qi = (int64_t)qblock * kTile + threadIdx.x;
+            if (qi < p.nq) {
+                const unsigned c = p.cnt[qi];
+                need = c < (unsigned)p.W || c > (unsigned)kCap;
+            }
+        }
+        if (!__syncthreads_or(need)) return;
+    }
     // 1024-byte alignment for the 128-byte swizzle pattern
     unsigned char* smem =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = smem;                                   // slices x 16 KB
     unsigned char* sB = sA + (size_t)p.slices * kSliceTile;     // kStages x 16 KB
     float2* sSN = reinterpret_cast<float2*>(sB + (size_t)kStages * kSliceTile);  // 2 x 128
-    u64* sBuf = reinterpret_cast<u64*>(sSN + 2 * kTile);        // kBuf x 128 (slot-major)
-    u64* bars = sBuf + kBuf * kTile;
+    u64* sBuf = reinterpret_cast<u64*>(sSN + 2 * kTile);        // full pass: kBuf x 128 (slot-major)
+    u64* bars = MODE == kModeFull ? sBuf + kBuf * kTile : sBuf;
     u64* full = bars;
     u64* empty = full + kStages;
     u64* a_full = empty + kStages;
@@ -186,11 +237,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sn_empty + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int chunk = blockIdx.x, qblock = blockIdx.y;
     const int64_t row0 = (int64_t)chunk * p.chunk_rows;
     const int64_t row1 = min(p.n, row0 + p.chunk_rows);
-    const int ntiles = (int)((row1 - row0 + kTile - 1) / kTile);
+    const int ntiles = row1 > row0 ? (int)((row1 - row0 + kTile - 1) / kTile) : 0;
     constexpr int kElemPerSlice = kFp8 ? 128 : 64;
     constexpr int kMmaK = kFp8 ? 32 : 16;                       // elements per MMA
     constexpr int kMmaPerSlice = kElemPerSlice / kMmaK;         // 4
@@ -295,15 +344,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------ epilogue
         const int quad = warp & 3;                 // TMEM lane quadrant this warp may access
         const int qrow = quad * 32 + lane;         // query row within the block
-        const int et = (warp - 2) * 32 + lane;     // epilogue thread index (buffer column)
         const int64_t qi = (int64_t)qblock * kTile + qrow;
         const bool qvalid = qi < p.nq;
         const float m = qvalid ? p.qm[qi] : 0.f;
-        u64 list[WMAX];
-        for (int i = 0; i < WMAX; ++i) list[i] = kKeyEmpty;
+        // pilot: the sample keys; main: tau from the pilot lists; full: exact top W
+        u64 net[kPilotR];
+#pragma unroll
+        for (int i = 0; i < kPilotR; ++i) net[i] = kKeyEmpty;
+        u64 tau = kKeyEmpty;
+        float tau_score = __int_as_float(0x7f800000);
+        if (MODE == kModeMain && qvalid) {
+            const u64* pl = p.pilot + (size_t)qi * p.pchunks * kPilotR;
+            for (int i = 0; i < p.pchunks * kPilotR; ++i) net_insert(net, pl[i]);
+            tau = net[kPilotR - 1];
+            tau_score = tau == kKeyEmpty ? __int_as_float(0x7f800000) : key_score(tau);
+        }
+        u64 list[MODE == kModeFull ? WMAX : 1];
+        if (MODE == kModeFull)
+            for (int i = 0; i < WMAX; ++i) list[i] = kKeyEmpty;
         u64 thr = kKeyEmpty;
         int nb = 0;
-        u64* buf = sBuf + et;
+        u64* buf = sBuf + (warp - 2) * 32 + lane;
         for (int t = 0; t < ntiles; ++t) {
             const int a = t & 1;
             const uint32_t par = (uint32_t)((t >> 1) & 1);
@@ -328,13 +389,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int col = c0 + j;
                         const float2 sn = snt[col];
                         const float score = fmaf(m, sn.x * __uint_as_float(v[j]), sn.y);
-                        const u64 key = score_key(score, (uint32_t)(r + col));
-                        if (col < nr && key < thr) {
-                            buf[nb * kTile] = key;
-                            if (++nb == kBuf) {
-                                flush_buffer<WMAX>(list, buf, kTile, nb, p.W);
-                                nb = 0;
-                                thr = list[p.W - 1];
+                        if (MODE == kModePilot) {
+                            if (col < nr) net_insert(net, score_key(score, (uint32_t)(r + col)));
+                        } else if (MODE == kModeMain) {
+                            if (col < nr && score <= tau_score) {
+                                const u64 key = score_key(score, (uint32_t)(r + col));
+                                if (key <= tau) {
+                                    const unsigned pos = atomicAdd(&p.cnt[qi], 1u);
+                                    if (pos < (unsigned)kCap) p.cand[(size_t)qi * kCap + pos] = key;
+                                }
+                            }
+                        } else {
+                            const u64 key = score_key(score, (uint32_t)(r + col));
+                            if (col < nr && key < thr) {
+                                buf[nb * kTile] = key;
+                                if (++nb == kBuf) {
+                                    flush_buffer<WMAX>(list, buf, kTile, nb, p.W);
+                                    nb = 0;
+                                    thr = list[p.W - 1];
+                                }
                             }
                         }
                     }
@@ -347,10 +420,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_arrive(&sn_empty[a]);
             }
         }
-        if (nb) flush_buffer<WMAX>(list, buf, kTile, nb, p.W);
-        if (qvalid) {
-            u64* dst = p.partial + ((size_t)qi * p.nchunks + chunk) * p.W;
-            for (int i = 0; i < p.W; ++i) dst[i] = list[i];
+        if (MODE == kModePilot && qvalid) {
+            u64* dst = p.partial + ((size_t)qi * p.nchunks + chunk) * kPilotR;
+#pragma unroll
+            for (int i = 0; i < kPilotR; ++i) dst[i] = net[i];
+        }
+        if (MODE == kModeFull) {
+            if (nb) flush_buffer<WMAX>(list, buf, kTile, nb, p.W);
+            if (qvalid) {
+                u64* dst = p.partial + ((size_t)qi * p.nchunks + chunk) * p.W;
+                for (int i = 0; i < p.W; ++i) dst[i] = list[i];
+            }
         }
     }
     tc_fence_before();
@@ -426,85 +506,111 @@ __device__ int count_le(const u64* P, int total, u64 x, int lane) {
 }
 
 template <int CPL>
-__global__ void __launch_bounds__(256) merge_rerank_kernel(const u64* __restrict__ partial, int nchunks, int W,
-                                                           const float* __restrict__ X, int D,
-                                                           const float* __restrict__ Q, int nq, int k,
-                                                           int64_t* __restrict__ idx, float* __restrict__ dist) {
-    __shared__ u64 cand[8][kMergeCap];
+__global__ void __launch_bounds__(kMergeWarps * 32) merge_rerank_kernel(
+    const u64* __restrict__ partial, int nchunks, int W, const u64* __restrict__ cand,
+    const unsigned* __restrict__ cnt, const float* __restrict__ X, int D, const float* __restrict__ Q, int nq, int k,
+    int64_t* __restrict__ idx, float* __restrict__ dist) {
+    extern __shared__ u64 cand_sm[];  // kMergeWarps x kCap
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int qi = blockIdx.x * 8 + warp;
+    const int qi = blockIdx.x * kMergeWarps + warp;
     if (qi >= nq) return;
-    u64* cw = cand[warp];
-    const u64* P = partial + (size_t)qi * nchunks * W;
-    const int total = nchunks * W;
-    // every key of the global top W is <= the smallest chunk's W-th key
-    u64 bound = kKeyEmpty;
-    for (int c = lane; c < nchunks; c += 32) {
-        const u64 v = __ldcg(P + (size_t)c * W + W - 1);
-        bound = v < bound ? v : bound;
-    }
-    bound = warp_min_u64(bound);
-    int cnt = count_le(P, total, bound, lane);
-    if (cnt > kMergeCap) {
-        // many keys share the bound's neighbourhood: bisect for the W-th smallest key
-        u64 lo = 0, hi = bound;
-        while (lo < hi) {
-            const u64 mid = lo + (hi - lo) / 2;
-            if (count_le(P, total, mid, lane) >= W) hi = mid;
-            else lo = mid + 1;
-        }
-        bound = lo;
-        cnt = count_le(P, total, bound, lane);
-    }
+    u64* cw = cand_sm + (size_t)warp * kCap;
+    const unsigned c = cand != nullptr ? cnt[qi] : 0u;
     int n = 0;
-    for (int base = 0; base < total; base += 32) {
-        const int i = base + lane;
-        const u64 key = i < total ? __ldcg(P + i) : kKeyEmpty;
-        const bool take = key != kKeyEmpty && key <= bound;
-        const unsigned m = __ballot_sync(kFull, take);
-        const int pos = n + __popc(m & ((1u << lane) - 1u));
-        if (take && pos < kMergeCap) cw[pos] = key;
-        n += __popc(m);
+    if (cand != nullptr && c >= (unsigned)W && c <= (unsigned)kCap) {
+        // the main pass collected every key <= tau, and there are W..kCap of them
+        n = (int)c;
+        for (int i = lane; i < n; i += 32) cw[i] = __ldcg(cand + (size_t)qi * kCap + i);
+    } else {
+        // per-chunk top-W lists of the full pass; every key of the global top W
+        // is <= the smallest chunk's W-th key
+        const u64* P = partial + (size_t)qi * nchunks * W;
+        const int total = nchunks * W;
+        u64 bound = kKeyEmpty;
+        for (int ch = lane; ch < nchunks; ch += 32) {
+            const u64 v = __ldcg(P + (size_t)ch * W + W - 1);
+            bound = v < bound ? v : bound;
+        }
+        bound = warp_min_u64(bound);
+        int cntle = count_le(P, total, bound, lane);
+        if (cntle > kCap) {
+            // many keys near the bound: bisect for the W-th smallest key
+            u64 lo = 0, hi = bound;
+            while (lo < hi) {
+                const u64 mid = lo + (hi - lo) / 2;
+                if (count_le(P, total, mid, lane) >= W) hi = mid;
+                else lo = mid + 1;
+            }
+            bound = lo;
+        }
+        for (int base = 0; base < total; base += 32) {
+            const int i = base + lane;
+            const u64 key = i < total ? __ldcg(P + i) : kKeyEmpty;
+            const bool take = key != kKeyEmpty && key <= bound;
+            const unsigned m = __ballot_sync(kFull, take);
+            const int pos = n + __popc(m & ((1u << lane) - 1u));
+            if (take && pos < kCap) cw[pos] = key;
+            n += __popc(m);
+        }
+        n = min(n, kCap);
     }
-    n = min(n, kMergeCap);
     int p2 = 32;
     while (p2 < n) p2 <<= 1;
+    __syncwarp();
     for (int i = n + lane; i < p2; i += 32) cw[i] = kKeyEmpty;
     __syncwarp();
     warp_sort(cw, p2, lane);
     const int take = min(n, W);
-    // FP32 direct re-rank of the shortlist
+    // FP32 direct re-rank of the shortlist, four rows in flight
     const int D4 = D / 4;
     float4 qv[CPL];
 #pragma unroll
     for (int j = 0; j < CPL; ++j) {
-        const int c = lane + 32 * j;
-        qv[j] = c < D4 ? reinterpret_cast<const float4*>(Q + (size_t)qi * D)[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int cc = lane + 32 * j;
+        qv[j] = cc < D4 ? reinterpret_cast<const float4*>(Q + (size_t)qi * D)[cc] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const float2 neg1 = make_float2(-1.f, -1.f);
     u64 L = kKeyEmpty, thr = kKeyEmpty;
-    for (int i = 0; i < take; ++i) {
-        const uint32_t r = (uint32_t)cw[i];
-        const float4* xr = reinterpret_cast<const float4*>(X + (size_t)r * D);
-        float2 acc = make_float2(0.f, 0.f);
+    for (int i0 = 0; i0 < take; i0 += 4) {
+        uint32_t r[4];
+        float4 x[4][CPL];
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) {
-            const int c = lane + 32 * j;
-            if (c < D4) {
-                const float4 x = __ldg(xr + c);
-                float2 a = __ffma2_rn(make_float2(x.x, x.y), neg1, make_float2(qv[j].x, qv[j].y));
-                float2 b = __ffma2_rn(make_float2(x.z, x.w), neg1, make_float2(qv[j].z, qv[j].w));
-                acc = __ffma2_rn(a, a, acc);
-                acc = __ffma2_rn(b, b, acc);
+        for (int b = 0; b < 4; ++b) {
+            r[b] = i0 + b < take ? (uint32_t)cw[i0 + b] : 0xffffffffu;
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                const int cc = lane + 32 * j;
+                x[b][j] = (r[b] != 0xffffffffu && cc < D4)
+                              ? __ldg(reinterpret_cast<const float4*>(X + (size_t)r[b] * D) + cc)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
-        float d = acc.x + acc.y;
+        float d[4];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
-        const u64 key = make_key(d, r);
-        if (key < thr) {
-            list_insert(L, key, k, lane);
-            thr = __shfl_sync(kFull, L, k - 1);
+        for (int b = 0; b < 4; ++b) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                float2 a = __ffma2_rn(make_float2(x[b][j].x, x[b][j].y), neg1, make_float2(qv[j].x, qv[j].y));
+                float2 e = __ffma2_rn(make_float2(x[b][j].z, x[b][j].w), neg1, make_float2(qv[j].z, qv[j].w));
+                acc = __ffma2_rn(a, a, acc);
+                acc = __ffma2_rn(e, e, acc);
+            }
+            d[b] = acc.x + acc.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) d[b] += __shfl_xor_sync(kFull, d[b], o);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            if (r[b] == 0xffffffffu) continue;
+            const u64 key = make_key(d[b], r[b]);
+            if (key < thr) {
+                list_insert(L, key, k, lane);
+                thr = __shfl_sync(kFull, L, k - 1);
+            }
         }
     }
     if (lane < k) {
@@ -551,49 +657,79 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int D, bool fp8)
     return r == CUDA_SUCCESS;
 }
 
-struct LowpPlan {
-    int nq_pad, qblocks, chunk_rows, nchunks, wmax;
-    size_t codes_bytes, qm_bytes, partial_bytes, smem;
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Chunking {
+    int chunk_rows, nchunks;
 };
 
-size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+// About one CTA per SM over qblocks x chunks; chunks are whole tiles.
+Chunking chunking(int64_t rows, int qblocks, int sms) {
+    Chunking c{};
+    const int target = std::max(1, sms / qblocks);
+    int64_t cr = (rows + target - 1) / target;
+    cr = std::max<int64_t>(kTile, (cr + kTile - 1) / kTile * kTile);
+    c.chunk_rows = (int)cr;
+    c.nchunks = (int)((rows + cr - 1) / cr);
+    return c;
+}
+
+struct LowpPlan {
+    int nq_pad, qblocks, wmax;
+    bool sampled;
+    Chunking main, pilot;
+    size_t codes_bytes, qm_bytes, pilot_bytes, cnt_bytes, cand_bytes, partial_bytes;
+};
 
 LowpPlan plan(const lhr_db* db, int nq, bool fp8, int W) {
     LowpPlan pl{};
     pl.nq_pad = (nq + kTile - 1) / kTile * kTile;
     pl.qblocks = pl.nq_pad / kTile;
-    int target = std::max(1, db->sms / pl.qblocks);
-    int64_t cr = (db->n + target - 1) / target;
-    cr = (cr + kTile - 1) / kTile * kTile;
-    pl.chunk_rows = (int)cr;
-    pl.nchunks = (int)((db->n + cr - 1) / cr);
     pl.wmax = W <= 32 ? 32 : (W <= 64 ? 64 : 128);
+    pl.sampled = (fp8 ? db->X8_s : db->Xb_s) != nullptr;
+    pl.main = chunking(db->n, pl.qblocks, db->sms);
+    pl.pilot = chunking(std::max<int64_t>(db->n_sample, 1), pl.qblocks, db->sms);
     const int elem = fp8 ? 1 : 2;
     pl.codes_bytes = a256((size_t)pl.nq_pad * db->dim * elem);
     pl.qm_bytes = a256((size_t)pl.nq_pad * sizeof(float));
-    pl.partial_bytes = a256((size_t)nq * pl.nchunks * W * sizeof(u64));
-    const int slices = db->dim * elem / kSliceBytes;
-    pl.smem = 1024 + (size_t)slices * kSliceTile + (size_t)kStages * kSliceTile + 2 * kTile * sizeof(float2) +
-              (size_t)kBuf * kTile * sizeof(u64) + (2 * kStages + 9) * sizeof(u64) + 16;
+    pl.pilot_bytes = pl.sampled ? a256((size_t)nq * pl.pilot.nchunks * kPilotR * sizeof(u64)) : 0;
+    pl.cnt_bytes = pl.sampled ? a256((size_t)nq * sizeof(unsigned)) : 0;
+    pl.cand_bytes = pl.sampled ? a256((size_t)nq * kCap * sizeof(u64)) : 0;
+    pl.partial_bytes = a256((size_t)nq * pl.main.nchunks * W * sizeof(u64));
     return pl;
 }
 
-template <bool kFp8, int WMAX>
-cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& tp, const LowpPlan& pl,
-                      cudaStream_t stream) {
-    auto kern = tc_topw_kernel<kFp8, WMAX>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+size_t tc_smem(int slices, int mode) {
+    return 1024 + (size_t)slices * kSliceTile + (size_t)kStages * kSliceTile + 2 * kTile * sizeof(float2) +
+           (mode == kModeFull ? (size_t)kBuf * kTile * sizeof(u64) : 0) + (2 * kStages + 9) * sizeof(u64) + 16;
+}
+
+template <bool kFp8, int MODE, int WMAX>
+cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& tp, int qblocks,
+                      cudaStream_t stream, const char* name) {
+    auto kern = tc_kernel<kFp8, MODE, WMAX>;
+    const size_t sm = tc_smem(tp.slices, MODE);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    ProfScope ps(kFp8 ? "tc_topw_kernel_fp8" : "tc_topw_kernel_bf16", stream);
-    kern<<<dim3(pl.nchunks, pl.qblocks), kThreads, pl.smem, stream>>>(ma, mb, tp);
+    ProfScope ps(name, stream);
+    kern<<<dim3(tp.nchunks, qblocks), kThreads, sm, stream>>>(ma, mb, tp);
     return cudaGetLastError();
+}
+
+template <bool kFp8>
+cudaError_t launch_full(int wmax, const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& tp, int qblocks,
+                        cudaStream_t stream) {
+    const char* name = kFp8 ? "tc_full_kernel_fp8" : "tc_full_kernel_bf16";
+    if (wmax == 32) return launch_tc<kFp8, kModeFull, 32>(ma, mb, tp, qblocks, stream, name);
+    if (wmax == 64) return launch_tc<kFp8, kModeFull, 64>(ma, mb, tp, qblocks, stream, name);
+    return launch_tc<kFp8, kModeFull, 128>(ma, mb, tp, qblocks, stream, name);
 }
 
 }  // namespace
 
 size_t lowp_scratch_bytes(const lhr_db* db, int nq, bool fp8, int W) {
     const LowpPlan pl = plan(db, nq, fp8, W);
-    return pl.codes_bytes + pl.qm_bytes + pl.partial_bytes;
+    return pl.codes_bytes + pl.qm_bytes + pl.pilot_bytes + pl.cnt_bytes + pl.cand_bytes + pl.partial_bytes;
 }
 
 cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int W, int k, int64_t* idx, float* dist,
@@ -601,8 +737,17 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
     const LowpPlan pl = plan(db, nq, fp8, W);
     unsigned char* base = reinterpret_cast<unsigned char*>(scratch);
     void* codes = base;
-    float* qm = reinterpret_cast<float*>(base + pl.codes_bytes);
-    u64* partial = reinterpret_cast<u64*>(base + pl.codes_bytes + pl.qm_bytes);
+    base += pl.codes_bytes;
+    float* qm = reinterpret_cast<float*>(base);
+    base += pl.qm_bytes;
+    u64* pilot = reinterpret_cast<u64*>(base);
+    base += pl.pilot_bytes;
+    unsigned* cnt = reinterpret_cast<unsigned*>(base);
+    base += pl.cnt_bytes;
+    u64* cand = reinterpret_cast<u64*>(base);
+    base += pl.cand_bytes;
+    u64* partial = reinterpret_cast<u64*>(base);
+    cudaError_t e;
     {
         ProfScope ps("quantize_queries_kernel", stream);
         const int blocks = (pl.nq_pad * 32 + 255) / 256;
@@ -610,44 +755,72 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
             quantize_queries_kernel<true><<<blocks, 256, 0, stream>>>(q, nq, pl.nq_pad, db->dim, codes, qm);
         else
             quantize_queries_kernel<false><<<blocks, 256, 0, stream>>>(q, nq, pl.nq_pad, db->dim, codes, qm);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    CUtensorMap ma, mb;
+    CUtensorMap ma, mb, ms;
     if (!make_map(&ma, codes, pl.nq_pad, db->dim, fp8) || !make_map(&mb, fp8 ? db->X8 : db->Xb, db->n, db->dim, fp8))
         return cudaErrorInvalidValue;
     TcParams tp{};
-    tp.n = db->n;
     tp.slices = db->dim * (fp8 ? 1 : 2) / kSliceBytes;
-    tp.chunk_rows = pl.chunk_rows;
-    tp.nchunks = pl.nchunks;
-    tp.sn = fp8 ? db->sn8 : db->snb;
     tp.qm = qm;
     tp.nq = nq;
     tp.W = W;
-    tp.partial = partial;
     tp.err = db->err;
-    cudaError_t e;
-    if (fp8) {
-        e = pl.wmax == 32 ? launch_tc<true, 32>(ma, mb, tp, pl, stream)
-                          : (pl.wmax == 64 ? launch_tc<true, 64>(ma, mb, tp, pl, stream)
-                                           : launch_tc<true, 128>(ma, mb, tp, pl, stream));
-    } else {
-        e = pl.wmax == 32 ? launch_tc<false, 32>(ma, mb, tp, pl, stream)
-                          : (pl.wmax == 64 ? launch_tc<false, 64>(ma, mb, tp, pl, stream)
-                                           : launch_tc<false, 128>(ma, mb, tp, pl, stream));
+    if (pl.sampled) {
+        if (!make_map(&ms, fp8 ? db->X8_s : db->Xb_s, db->n_sample, db->dim, fp8)) return cudaErrorInvalidValue;
+        // pilot over the sample
+        TcParams pp = tp;
+        pp.n = db->n_sample;
+        pp.chunk_rows = pl.pilot.chunk_rows;
+        pp.nchunks = pl.pilot.nchunks;
+        pp.sn = fp8 ? db->sn8_s : db->snb_s;
+        pp.partial = pilot;
+        e = fp8 ? launch_tc<true, kModePilot, 32>(ma, ms, pp, pl.qblocks, stream, "tc_pilot_kernel_fp8")
+                : launch_tc<false, kModePilot, 32>(ma, ms, pp, pl.qblocks, stream, "tc_pilot_kernel_bf16");
+        if (e != cudaSuccess) return e;
+        // main pass: every key <= tau into the candidate buffers
+        if ((e = cudaMemsetAsync(cnt, 0, (size_t)nq * sizeof(unsigned), stream)) != cudaSuccess) return e;
+        TcParams mp = tp;
+        mp.n = db->n;
+        mp.chunk_rows = pl.main.chunk_rows;
+        mp.nchunks = pl.main.nchunks;
+        mp.sn = fp8 ? db->sn8 : db->snb;
+        mp.pilot = pilot;
+        mp.pchunks = pl.pilot.nchunks;
+        mp.cand = cand;
+        mp.cnt = cnt;
+        e = fp8 ? launch_tc<true, kModeMain, 32>(ma, mb, mp, pl.qblocks, stream, "tc_main_kernel_fp8")
+                : launch_tc<false, kModeMain, 32>(ma, mb, mp, pl.qblocks, stream, "tc_main_kernel_bf16");
+        if (e != cudaSuccess) return e;
     }
+    // full pass: always without a sample, otherwise only where a main pass fell short
+    TcParams fp = tp;
+    fp.n = db->n;
+    fp.chunk_rows = pl.main.chunk_rows;
+    fp.nchunks = pl.main.nchunks;
+    fp.sn = fp8 ? db->sn8 : db->snb;
+    fp.partial = partial;
+    fp.cnt = pl.sampled ? cnt : nullptr;
+    e = fp8 ? launch_full<true>(pl.wmax, ma, mb, fp, pl.qblocks, stream)
+            : launch_full<false>(pl.wmax, ma, mb, fp, pl.qblocks, stream);
     if (e != cudaSuccess) return e;
     const int d4 = db->dim / 4;
     const int cpl = d4 <= 32 ? 1 : (d4 <= 64 ? 2 : 4);
-    ProfScope ps("merge_rerank_kernel", stream);
-    const int blocks = (nq + 7) / 8;
-    if (cpl == 1)
-        merge_rerank_kernel<1><<<blocks, 256, 0, stream>>>(partial, pl.nchunks, W, db->X, db->dim, q, nq, k, idx, dist);
-    else if (cpl == 2)
-        merge_rerank_kernel<2><<<blocks, 256, 0, stream>>>(partial, pl.nchunks, W, db->X, db->dim, q, nq, k, idx, dist);
-    else
-        merge_rerank_kernel<4><<<blocks, 256, 0, stream>>>(partial, pl.nchunks, W, db->X, db->dim, q, nq, k, idx, dist);
+    const size_t msm = (size_t)kMergeWarps * kCap * sizeof(u64);
+    const u64* candp = pl.sampled ? cand : nullptr;
+    const int blocks = (nq + kMergeWarps - 1) / kMergeWarps;
+#define LHR_MR(C)                                                                                              \
+    do {                                                                                                       \
+        e = cudaFuncSetAttribute(merge_rerank_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm); \
+        if (e != cudaSuccess) return e;                                                                        \
+        ProfScope ps("merge_rerank_kernel", stream);                                                           \
+        merge_rerank_kernel<C><<<blocks, kMergeWarps * 32, msm, stream>>>(partial, pl.main.nchunks, W, candp, cnt, \
+                                                                            db->X, db->dim, q, nq, k, idx, dist); \
+    } while (0)
+    if (cpl == 1) LHR_MR(1);
+    else if (cpl == 2) LHR_MR(2);
+    else LHR_MR(4);
+#undef LHR_MR
     return cudaGetLastError();
 }
 

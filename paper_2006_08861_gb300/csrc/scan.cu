@@ -2,25 +2,39 @@
 // Algorithm 1: calculateDistance for every (query frame, database frame) pair,
 // then selectTopCandidates; §4: Euclidean distance, top N).
 //
-// Design (GB300): the database is memory-bound work for a handful of query
-// frames, so every byte of it is read once per launch.
-//   * One CTA per (row chunk, query block). A row chunk is a contiguous range
-//     of one subspace; the chunk table is built with the database.
+// Design (GB300): for a handful of query frames the scan is bound by HBM, so
+// every database byte is read once per launch and the arithmetic per byte is
+// kept small.
+//   * One CTA per (row chunk, block of QB query frames). A row chunk is a
+//     contiguous range of one subspace; the chunk table is built with the
+//     database.
 //   * A producer thread streams the chunk through shared memory with 1-D bulk
-//     copies (cp.async.bulk, 16 rows per stage) into an mbarrier ring; each
-//     consumer warp owns the stages s with s % warps == warp, so its parity
-//     waits always see consecutive phases.
-//   * Lanes split the feature dimensions (float4 chunks, conflict-free), the
-//     block's QB query frames sit in registers, and (q - x)^2 runs as packed
-//     FP32 pairs (FFMA2). A 5-step butterfly transpose-reduce leaves lane l
-//     with the full distance of (row l / QB, query l % QB): 31 shuffles for 32
-//     distances.
-//   * Each warp keeps, per query, a sorted top-k list in registers (lane i
-//     holds the i-th key); a ballot against the list's k-th key rejects almost
-//     every distance with one compare. The distance matrix never leaves the SM.
+//     copies (cp.async.bulk, 8 rows per stage) into an mbarrier ring; consumer
+//     warp w owns the stages s with s % warps == w, so its parity waits always
+//     see consecutive phases.
+//   * Filter: lanes split the feature dimensions (float4 chunks,
+//     conflict-free), the QB frames sit in registers, and each lane forms
+//     partial dot products q.x with packed FP32 FMAs (one instruction per two
+//     elements). A 5-step butterfly transpose-reduce leaves lane l with the
+//     dot product of (row l / QB, frame l % QB), and
+//     d~ = ||x||^2 + ||q||^2 - 2 q.x
+//     (row norms built with the database). d~ differs from the exact value by
+//     at most (gamma_D + 3u)(||x|| + ||q||)^2 (dot-product error bound, u =
+//     2^-24), and so does the FP32 direct form; a row can only enter the list
+//     if d~ <= threshold + 2 (gamma_D + 3u)(max||x|| + ||q||)^2.
+//   * Rows that pass (rare once the lists fill) get their exact direct-form
+//     distance sum_j (q_j - x_j)^2, recomputed by the warp from shared memory,
+//     and are inserted into the warp's per-frame top-k list (shared memory,
+//     lane i holds the i-th key). Keys are (distance bits << 32 | row): ties go
+//     to the lower row. A per-frame threshold shared by the CTA's warps (the
+//     smallest k-th distance of any warp) prunes further: an element above
+//     another warp's k-th cannot be in the CTA's top k.
 //   * Warp lists merge into a per-CTA list written to scratch; the last CTA of
-//     a query block (atomic ticket) merges every chunk of each subspace and
-//     writes the final lists. One launch per call.
+//     a query block (atomic ticket) merges every chunk of each subspace, keys
+//     above the smallest per-chunk k-th key being skipped, and writes the
+//     final lists. One launch per call; the distance matrix never leaves the SM.
+#include <math.h>
+
 #include <mutex>
 #include <string>
 
@@ -30,11 +44,13 @@
 namespace lhr {
 namespace {
 
-constexpr int kRowsPerStage = 16;
+constexpr int kRPS = 8;            // rows per stage
+constexpr int kMaxWarps = 12;      // consumer warps per CTA
 constexpr int kMaxSmem = 227 * 1024;
 
 struct ScanParams {
     const float* X;
+    const float* xnorm;
     int D;
     const int4* chunks;
     int nchunks;
@@ -45,6 +61,8 @@ struct ScanParams {
     int nq;
     int k;
     int stages;
+    float xmax;          // sqrt(max ||x||^2)
+    float margin_scale;  // 2 (gamma_D + 3u)
     u64* partial;        // [qblock][QB][nchunks][k]
     unsigned* counters;  // [qblock]
     int64_t* idx;        // [nq][n_sub][k]
@@ -60,28 +78,33 @@ struct ScanConfig {
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 template <int QB, int CPL>
-__global__ void __launch_bounds__(288, 1) scan_topk_kernel(const ScanParams p) {
+__global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(const ScanParams p) {
     constexpr int RW = 32 / QB;  // rows per reduction round
+    constexpr int kRounds = kRPS / RW;
+    static_assert(kRPS % RW == 0, "stage rows must hold whole rounds");
     extern __shared__ __align__(128) unsigned char smem[];
     const int warps = blockDim.x / 32 - 1;  // consumer warps; the last warp produces
     const int warp = threadIdx.x / 32;
     const int lane = threadIdx.x % 32;
-    const int D4 = p.D / 4;
+    const int D = p.D;
+    const int D4 = D / 4;
     const int NS = p.stages;
-    const size_t stage_floats = (size_t)kRowsPerStage * p.D;
+    const size_t stage_floats = (size_t)kRPS * D;
 
     float* stage_buf = reinterpret_cast<float*>(smem);
-    u64* full = reinterpret_cast<u64*>(smem + NS * stage_floats * sizeof(float));
+    float* qs = stage_buf + NS * stage_floats;                            // QB x D
+    u64* full = reinterpret_cast<u64*>(qs + (size_t)QB * D);
     u64* empty = full + NS;
-    u64* lists = empty + NS;  // [warps][QB][32]
-    int* flags = reinterpret_cast<int*>(lists + (size_t)warps * QB * 32);
+    u64* lists = empty + NS;                                              // [warps][QB][32]
+    unsigned* thr_sh = reinterpret_cast<unsigned*>(lists + (size_t)warps * QB * 32);  // QB float bits
+    int* flags = reinterpret_cast<int*>(thr_sh + QB);
     volatile int* abort_flag = flags;
 
     const int chunk = blockIdx.x;
     const int qblock = blockIdx.y;
     const int4 ch = p.chunks[chunk];
     const int row0 = ch.x, row1 = ch.y;
-    const int iters = (row1 - row0 + kRowsPerStage - 1) / kRowsPerStage;
+    const int iters = (row1 - row0 + kRPS - 1) / kRPS;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -92,6 +115,14 @@ __global__ void __launch_bounds__(288, 1) scan_topk_kernel(const ScanParams p) {
         flags[1] = 0;
         fence_mbar_init();
     }
+    for (int i = threadIdx.x; i < QB * D4; i += blockDim.x) {
+        const int q = i / D4, c = i % D4;
+        const int qi = qblock * QB + q;
+        reinterpret_cast<float4*>(qs)[i] =
+            qi < p.nq ? reinterpret_cast<const float4*>(p.Q)[(size_t)qi * D4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int i = threadIdx.x; i < warps * QB * 32; i += blockDim.x) lists[i] = kKeyEmpty;
+    if (threadIdx.x < QB) thr_sh[threadIdx.x] = 0x7f800000u;  // +inf
     __syncthreads();
 
     if (warp == warps) {
@@ -106,11 +137,11 @@ __global__ void __launch_bounds__(288, 1) scan_topk_kernel(const ScanParams p) {
                     record_error(p.err, kErrTimeout);
                     break;
                 }
-                const int r = row0 + it * kRowsPerStage;
-                const int nr = min(kRowsPerStage, row1 - r);
-                const uint32_t bytes = (uint32_t)nr * (uint32_t)p.D * 4u;
+                const int r = row0 + it * kRPS;
+                const int nr = min(kRPS, row1 - r);
+                const uint32_t bytes = (uint32_t)nr * (uint32_t)D * 4u;
                 mbar_arrive_expect_tx(&full[s], bytes);
-                bulk_g2s(stage_buf + s * stage_floats, p.X + (size_t)r * p.D, bytes, &full[s]);
+                bulk_g2s(stage_buf + s * stage_floats, p.X + (size_t)r * D, bytes, &full[s]);
                 ++issued;
             }
             if (*abort_flag) {
@@ -122,27 +153,45 @@ __global__ void __launch_bounds__(288, 1) scan_topk_kernel(const ScanParams p) {
     } else {
         // ------------------------------------------------ consumers
         float4 qreg[QB][CPL];
+        float qpart[QB];
 #pragma unroll
         for (int q = 0; q < QB; ++q) {
-            const int qi = qblock * QB + q;
+            float a = 0.f;
 #pragma unroll
             for (int j = 0; j < CPL; ++j) {
                 const int c = lane + 32 * j;
-                qreg[q][j] = (qi < p.nq && c < D4)
-                                 ? reinterpret_cast<const float4*>(p.Q)[(size_t)qi * D4 + c]
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+                qreg[q][j] = c < D4 ? reinterpret_cast<const float4*>(qs + (size_t)q * D)[c]
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+                a = fmaf(qreg[q][j].x, qreg[q][j].x, a);
+                a = fmaf(qreg[q][j].y, qreg[q][j].y, a);
+                a = fmaf(qreg[q][j].z, qreg[q][j].z, a);
+                a = fmaf(qreg[q][j].w, qreg[q][j].w, a);
             }
+            qpart[q] = a;
         }
-        u64 L[QB];
+        // ||q||^2 of this lane's frame (lane % QB), and its filter margin
+        float qn = 0.f;
 #pragma unroll
-        for (int q = 0; q < QB; ++q) L[q] = kKeyEmpty;
-        u64 thr = kKeyEmpty;  // k-th key of the list of query (lane % QB)
-        const bool q_valid = (qblock * QB + (lane % QB)) < p.nq;
-        const float2 neg1 = f2(-1.f, -1.f);
+        for (int q = 0; q < QB; ++q) {
+            float a = qpart[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
+            if ((lane % QB) == q) qn = a;
+        }
+        const int myq = lane % QB;
+        const bool q_valid = (qblock * QB + myq) < p.nq;
+        const float rad = p.xmax + sqrtf(qn);
+        const float margin = p.margin_scale * rad * rad;
+        float thr_own = __int_as_float(0x7f800000);  // k-th distance of this warp's list for frame myq
+        u64* wlist = lists + (size_t)warp * QB * 32;
+        const volatile unsigned* thr_v = thr_sh;     // other warps lower it with atomicMin
 
         for (int it = warp; it < iters; it += warps) {
             const int s = it % NS;
             const uint32_t ph = (uint32_t)(it / NS) & 1u;
+            const int rbase = row0 + it * kRPS;
+            const int nr = min(kRPS, row1 - rbase);
+            const float xn_l = lane < nr ? __ldg(p.xnorm + rbase + lane) : 0.f;
             if (!mbar_wait(&full[s], ph, abort_flag)) {
                 if (lane == 0) {
                     *abort_flag = 1;
@@ -150,11 +199,11 @@ __global__ void __launch_bounds__(288, 1) scan_topk_kernel(const ScanParams p) {
                 }
                 break;
             }
-            const float4* sb = reinterpret_cast<const float4*>(stage_buf + s * stage_floats);
-            const int rbase = row0 + it * kRowsPerStage;
-            const int nr = min(kRowsPerStage, row1 - rbase);
+            const float* sbf = stage_buf + s * stage_floats;
+            const float4* sb = reinterpret_cast<const float4*>(sbf);
 #pragma unroll 1
-            for (int rb = 0; rb < kRowsPerStage; rb += RW) {
+            for (int rr = 0; rr < kRounds; ++rr) {
+                const int rb = rr * RW;
                 float part[32];
 #pragma unroll
                 for (int r = 0; r < RW; ++r) {
@@ -169,10 +218,8 @@ __global__ void __launch_bounds__(288, 1) scan_topk_kernel(const ScanParams p) {
                         float2 acc = f2(0.f, 0.f);
 #pragma unroll
                         for (int j = 0; j < CPL; ++j) {
-                            float2 d0 = __ffma2_rn(f2(x[j].x, x[j].y), neg1, f2(qreg[q][j].x, qreg[q][j].y));
-                            float2 d1 = __ffma2_rn(f2(x[j].z, x[j].w), neg1, f2(qreg[q][j].z, qreg[q][j].w));
-                            acc = __ffma2_rn(d0, d0, acc);
-                            acc = __ffma2_rn(d1, d1, acc);
+                            acc = __ffma2_rn(f2(x[j].x, x[j].y), f2(qreg[q][j].x, qreg[q][j].y), acc);
+                            acc = __ffma2_rn(f2(x[j].z, x[j].w), f2(qreg[q][j].z, qreg[q][j].w), acc);
                         }
                         part[r * QB + q] = acc.x + acc.y;
                     }
@@ -189,29 +236,52 @@ __global__ void __launch_bounds__(288, 1) scan_topk_kernel(const ScanParams p) {
                     }
                 }
                 const int rl = rb + lane / QB;
-                const u64 key = (q_valid && rl < nr) ? make_key(part[0], (uint32_t)(rbase + rl)) : kKeyEmpty;
-                unsigned m = __ballot_sync(kFull, key < thr);
+                const float xn = __shfl_sync(kFull, xn_l, rl);
+                const float approx = fmaf(-2.f, part[0], xn + qn);
+                const float thr = fminf(thr_own, __uint_as_float(thr_v[myq]));
+                const bool pass = q_valid && rl < nr && approx <= thr + margin;
+                unsigned m = __ballot_sync(kFull, pass);
                 while (m) {
                     const int j = __ffs(m) - 1;
                     m &= m - 1;
-                    const u64 kj = __shfl_sync(kFull, key, j);
-                    const int qj = j % QB;
-                    u64 t = kKeyEmpty;
+                    const int rj = rb + j / QB, qj = j % QB;
+                    // exact direct-form distance of (row rj, frame qj)
+                    const float4* xr = reinterpret_cast<const float4*>(sbf + (size_t)rj * D);
+                    const float4* qr = reinterpret_cast<const float4*>(qs + (size_t)qj * D);
+                    float2 acc = f2(0.f, 0.f);
 #pragma unroll
-                    for (int q = 0; q < QB; ++q) {
-                        if (q == qj) {
-                            list_insert(L[q], kj, p.k, lane);
-                            t = __shfl_sync(kFull, L[q], p.k - 1);
+                    for (int jj = 0; jj < CPL; ++jj) {
+                        const int c = lane + 32 * jj;
+                        if (c < D4) {
+                            const float4 x = xr[c], qv = qr[c];
+                            const float2 d0 = __ffma2_rn(f2(x.x, x.y), f2(-1.f, -1.f), f2(qv.x, qv.y));
+                            const float2 d1 = __ffma2_rn(f2(x.z, x.w), f2(-1.f, -1.f), f2(qv.z, qv.w));
+                            acc = __ffma2_rn(d0, d0, acc);
+                            acc = __ffma2_rn(d1, d1, acc);
                         }
                     }
-                    if ((lane % QB) == qj) thr = t;
+                    float de = acc.x + acc.y;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) de += __shfl_xor_sync(kFull, de, o);
+                    if (de > __uint_as_float(thr_v[qj])) continue;  // another warp already holds k better
+                    const u64 key = make_key(de, (uint32_t)(rbase + rj));
+                    u64 L = wlist[qj * 32 + lane];
+                    const u64 kth = __shfl_sync(kFull, L, p.k - 1);
+                    if (key >= kth) continue;
+                    list_insert(L, key, p.k, lane);
+                    wlist[qj * 32 + lane] = L;
+                    const u64 nk = __shfl_sync(kFull, L, p.k - 1);
+                    if (nk != kKeyEmpty) {
+                        const float nd = key_dist(nk);
+                        if (myq == qj) thr_own = nd;
+                        if (lane == 0) atomicMin(&thr_sh[qj], __float_as_uint(nd));
+                    }
+                    __syncwarp();
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
         }
-#pragma unroll
-        for (int q = 0; q < QB; ++q) lists[((size_t)warp * QB + q) * 32 + lane] = L[q];
     }
     __syncthreads();
 
@@ -233,26 +303,75 @@ __global__ void __launch_bounds__(288, 1) scan_topk_kernel(const ScanParams p) {
     __threadfence();
 
     // ---------------------------------------------------- last CTA: final lists
-    for (int pair = warp; pair < QB * p.n_sub; pair += nwarps) {
-        const int q = pair / p.n_sub;
-        const int sub = pair % p.n_sub;
+    // G warps share each (frame, subspace) pair: each merges a share of the
+    // pair's chunk lists, then the pair's first warp merges the G results.
+    const int pairs = QB * p.n_sub;
+    const int G = max(1, nwarps / pairs);
+    const int per_round = nwarps / G;
+    u64* mlist = lists;  // free now: [nwarps][32]
+    for (int pbase = 0; pbase < pairs; pbase += per_round) {
+        const int pair = pbase + warp / G;
+        const int g = warp % G;
+        const bool active = warp / G < per_round && pair < pairs;
+        const int q = active ? pair / p.n_sub : 0;
+        const int sub = active ? pair % p.n_sub : 0;
         const int qi = qblock * QB + q;
-        if (qi >= p.nq) continue;
-        const int c0 = p.chunk_off[sub], c1 = p.chunk_off[sub + 1];
         u64 M = kKeyEmpty;
-        list_merge_keys<true>(M, p.partial + (((size_t)qblock * QB + q) * p.nchunks + c0) * p.k, (c1 - c0) * p.k,
-                              p.k, lane);
-        if (lane < p.k) {
-            const size_t o = ((size_t)qi * p.n_sub + sub) * p.k + lane;
-            if (M == kKeyEmpty) {
-                p.idx[o] = -1;
-                p.dist[o] = __int_as_float(0x7f800000);
-            } else {
-                const uint32_t r = key_row(M);
-                p.idx[o] = p.perm ? (int64_t)p.perm[r] : (int64_t)r;
-                p.dist[o] = key_dist(M);
+        if (active && qi < p.nq) {
+            const int c0 = p.chunk_off[sub], c1 = p.chunk_off[sub + 1];
+            const u64* P = p.partial + (((size_t)qblock * QB + q) * p.nchunks + c0) * p.k;
+            // every key of the subspace's top k is <= the smallest per-chunk k-th key
+            u64 bound = kKeyEmpty;
+            for (int c = lane; c < c1 - c0; c += 32) {
+                const u64 v = __ldcg(P + (size_t)c * p.k + p.k - 1);
+                bound = v < bound ? v : bound;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const u64 v = __shfl_xor_sync(kFull, bound, o);
+                bound = v < bound ? v : bound;
+            }
+            const int nch = c1 - c0;
+            const int ca = (int)((int64_t)nch * g / G), cb = (int)((int64_t)nch * (g + 1) / G);
+            const u64* Pg = P + (size_t)ca * p.k;
+            const int total = (cb - ca) * p.k;
+            u64 thr = kKeyEmpty;
+            for (int base = 0; base < total; base += 128) {
+                u64 key[4];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int i = base + b * 32 + lane;
+                    key[b] = i < total ? __ldcg(Pg + i) : kKeyEmpty;
+                }
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    unsigned m = __ballot_sync(kFull, key[b] <= bound && key[b] < thr);
+                    while (m) {
+                        const int j = __ffs(m) - 1;
+                        m &= m - 1;
+                        list_insert(M, __shfl_sync(kFull, key[b], j), p.k, lane);
+                    }
+                    thr = __shfl_sync(kFull, M, p.k - 1);
+                }
             }
         }
+        mlist[warp * 32 + lane] = M;
+        __syncthreads();
+        if (active && g == 0 && qi < p.nq) {
+            for (int h = 1; h < G; ++h) list_merge_keys<false>(M, &mlist[(warp + h) * 32], p.k, p.k, lane);
+            if (lane < p.k) {
+                const size_t o = ((size_t)qi * p.n_sub + sub) * p.k + lane;
+                if (M == kKeyEmpty) {
+                    p.idx[o] = -1;
+                    p.dist[o] = __int_as_float(0x7f800000);
+                } else {
+                    const uint32_t r = key_row(M);
+                    p.idx[o] = p.perm ? (int64_t)p.perm[r] : (int64_t)r;
+                    p.dist[o] = key_dist(M);
+                }
+            }
+        }
+        __syncthreads();
     }
     if (threadIdx.x == 0) p.counters[qblock] = 0u;
 }
@@ -262,27 +381,27 @@ ScanConfig choose_config(const lhr_db* db, int nq) {
     const int d4 = db->dim / 4;
     c.cpl = d4 <= 32 ? 1 : (d4 <= 64 ? 2 : 4);
     const int qb_max = 16 / c.cpl;
-    int qb = 2;
+    int qb = 4;
     while (qb < nq && qb < qb_max) qb *= 2;
     c.qb = qb;
-    const size_t stage_bytes = (size_t)kRowsPerStage * db->dim * sizeof(float);
-    const int warps_pref = 8;
-    // shared memory: stages + 2 barriers per stage + lists + flags
-    for (int w = warps_pref; w >= 1; --w) {
+    const size_t stage_bytes = (size_t)kRPS * db->dim * sizeof(float);
+    const size_t qs_bytes = (size_t)qb * db->dim * sizeof(float);
+    for (int w = kMaxWarps; w >= 1; --w) {
         const size_t lists = (size_t)w * qb * 32 * sizeof(u64);
-        const size_t budget = kMaxSmem - 1024 - lists;
-        int ns = (int)(budget / (stage_bytes + 16));
-        ns = (ns / w) * w;
-        if (ns >= 2 * w) {
-            c.warps = w;
-            c.stages = ns;
-            c.smem = ns * stage_bytes + 2 * ns * sizeof(u64) + lists + 16;
-            return c;
+        for (int per = 3; per >= 2; --per) {
+            const int ns = per * w;
+            const size_t smem = ns * stage_bytes + qs_bytes + 2 * ns * sizeof(u64) + lists + qb * sizeof(unsigned) + 16;
+            if (smem <= (size_t)kMaxSmem - 1024) {
+                c.warps = w;
+                c.stages = ns;
+                c.smem = smem;
+                return c;
+            }
         }
     }
     c.warps = 1;
     c.stages = 2;
-    c.smem = 2 * stage_bytes + 4 * sizeof(u64) + (size_t)qb * 32 * sizeof(u64) + 16;
+    c.smem = 2 * stage_bytes + qs_bytes + 4 * sizeof(u64) + (size_t)qb * 32 * sizeof(u64) + qb * sizeof(unsigned) + 16;
     return c;
 }
 
@@ -313,6 +432,7 @@ cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t
     const int nqb = (nq + c.qb - 1) / c.qb;
     ScanParams p{};
     p.X = db->X;
+    p.xnorm = db->xnorm;
     p.D = db->dim;
     p.chunks = db->chunks;
     p.nchunks = db->nchunks;
@@ -323,6 +443,11 @@ cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t
     p.nq = nq;
     p.k = k;
     p.stages = c.stages;
+    // 2 (gamma_D + 3u) with u = 2^-24 and gamma_D = D u / (1 - D u), slightly rounded up
+    const double u = 1.0 / 16777216.0;
+    const double gamma = db->dim * u / (1.0 - db->dim * u);
+    p.margin_scale = (float)(2.0 * (gamma + 3.0 * u) * 1.0001);
+    p.xmax = (float)(sqrt((double)db->xnorm_max) * 1.0001);
     p.partial = reinterpret_cast<u64*>(scratch);
     const size_t part_bytes = align256((size_t)nqb * c.qb * db->nchunks * k * sizeof(u64));
     p.counters = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(scratch) + part_bytes);
@@ -332,14 +457,11 @@ cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t
     cudaError_t e = cudaMemsetAsync(p.counters, 0, nqb * sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
     switch (c.cpl * 100 + c.qb) {
-        case 102: return launch_t<2, 1>(c, p, nqb, stream);
         case 104: return launch_t<4, 1>(c, p, nqb, stream);
         case 108: return launch_t<8, 1>(c, p, nqb, stream);
         case 116: return launch_t<16, 1>(c, p, nqb, stream);
-        case 202: return launch_t<2, 2>(c, p, nqb, stream);
         case 204: return launch_t<4, 2>(c, p, nqb, stream);
         case 208: return launch_t<8, 2>(c, p, nqb, stream);
-        case 402: return launch_t<2, 4>(c, p, nqb, stream);
         case 404: return launch_t<4, 4>(c, p, nqb, stream);
         default: return cudaErrorInvalidConfiguration;
     }

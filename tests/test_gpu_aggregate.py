@@ -63,7 +63,8 @@ def test_random_windows_against_oracle(lhr, mode):
     db = _db_for_xy(lhr, xy)
     cands, dists = [], []
     for w in range(40):
-        c = rng.integers(0, n, size=int(rng.integers(1, 900)))
+        # sizes on both sides of 1024 (the kernel's warp and block paths)
+        c = rng.integers(0, n, size=int(rng.integers(1, 3000)))
         if w % 3 == 0:
             c[: len(c) // 2] = rng.integers(0, 50, size=len(c) // 2)
         if w % 7 == 0:

@@ -62,6 +62,37 @@ def test_against_oracle(lhr, fmt_name, n, dim, nq, W, k):
     assert checked >= int(0.9 * nq)
 
 
+@pytest.mark.parametrize("fmt_name", ["bf16", "fp8"])
+def test_sampled_threshold_path_against_oracle(lhr, fmt_name):
+    # 300,000 rows: large enough for the pilot sample (every 64th row), so the
+    # shortlist comes from the thresholded main pass. Query 0 is copied into
+    # most rows off the sample grid: its candidate count overflows the buffer
+    # and the exact per-chunk fallback must give the same answer.
+    fmt, bit = FMT[fmt_name]
+    rng = np.random.default_rng(31)
+    n, dim, nq, W, k = 300_000, 128, 130, 64, 10
+    X = rng.standard_normal((n, dim)).astype(np.float32)
+    Q = (X[rng.integers(0, n, nq)] + 0.3 * rng.standard_normal((nq, dim))).astype(np.float32)
+    dup = np.arange(100, 200_000)
+    dup = dup[dup % 64 != 0]
+    X[dup] = X[5]
+    Q[0] = X[5]
+    db = lhr.lhr_build_db(X, np.zeros((n, 2)), lowp=bit)
+    idx, dist = lhr.lhr_query(db, torch.from_numpy(Q).cuda(), k, score=fmt_name, rerank_width=W)
+    torch.cuda.synchronize()
+    assert lhr.lhr_db_error(db) == 0
+    gi, gd = idx.cpu().numpy()[:, 0], dist.cpu().numpy()[:, 0]
+    s_rows, codes = olowp.quantize_rows(X, fmt)
+    sample = np.random.default_rng(32).choice(np.arange(1, nq), size=24, replace=False)
+    for qi in [0] + sample.tolist():
+        if qi and not _shortlist_separated(Q[qi], X, fmt, W, s_rows, codes):
+            continue
+        o_idx, o_dist, _ = olowp.lowp_topk(Q[qi:qi + 1], X, fmt, W, k + 1, codes=codes, s_rows=s_rows)
+        check_list(Q[qi], X, gi[qi], gd[qi], o_idx[0], o_dist[0], k, where=f"{fmt_name} q{qi}")
+    # query 0: exact copies at distance 0, lowest rows first
+    assert gi[0, 0] == 5 and np.all(gd[0] == 0.0)
+
+
 def test_width_equal_to_database_is_exhaustive(lhr):
     rng = np.random.default_rng(3)
     X = rng.standard_normal((100, 128)).astype(np.float32)

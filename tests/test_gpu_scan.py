@@ -73,6 +73,17 @@ def test_shapes(lhr, n, dim, nq, k):
     _compare(X, Q, k, gi, gd)
 
 
+@pytest.mark.parametrize("offset", [100.0, -3000.0])
+def test_large_common_offset(lhr, offset):
+    # ||x||^2 + ||q||^2 - 2 q.x cancels badly when every vector sits far from
+    # the origin; the scan's filter must still never drop a true neighbour.
+    rng = np.random.default_rng(9)
+    X = (offset + rng.standard_normal((6000, 64))).astype(np.float32)
+    Q = (X[rng.integers(0, 6000, 6)] + 0.1 * rng.standard_normal((6, 64))).astype(np.float32)
+    _, gi, gd = _run(lhr, X, Q, 16)
+    _compare(X, Q, 16, gi, gd)
+
+
 def test_exact_ties_break_by_lower_row(lhr):
     # Integer-valued rows with many duplicates: FP32 distances are exact, so
     # the order must equal the oracle's (distance, row) order bit for bit.
