@@ -41,9 +41,9 @@ __device__ __forceinline__ void write_invalid(const AggArgs& a, int w) {
 }
 
 // Algorithm 2 for one window of at most kWarpCand candidate slots, by a single
-// warp: the same steps, tie rules and integer tests as the block path below,
-// with warp shuffles in place of block barriers.
-__device__ void aggregate_warp(const AggParams& p, int w, long long b0, long long total, u64* keys, int* cand_rows,
+// warp: the same steps, tie rules and integer tests as the block path of
+// aggregate.cu, with warp shuffles in place of block barriers.
+__device__ inline void aggregate_warp(const AggParams& p, int w, long long b0, long long total, u64* keys, int* cand_rows,
                                float* cand_d, int* cnt) {
     const AggArgs& a = p.a;
     const int lane = threadIdx.x & 31;

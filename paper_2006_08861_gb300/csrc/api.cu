@@ -173,6 +173,11 @@ static lhr_status run_retrieval(const lhr_db* db, const float* q, int nq, const 
         if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
         e = launch_lowp(db, q, nq, fp8, p->rerank_width, p->k, idx, dist, scr.ptr, s);
         if (e != cudaSuccess) return cuda_fail(e, "low-precision launch");
+    } else if (p->shortlist > 0 && hier_fused_eligible(db, nq, p->shortlist)) {
+        e = scr.alloc(hier_scratch_bytes(db, nq), s);
+        if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+        e = launch_hier_fused(db, q, nq, p->shortlist, p->k, idx, dist, nullptr, scr.ptr, s);
+        if (e != cudaSuccess) return cuda_fail(e, "fused coarse-to-fine launch");
     } else if (p->shortlist > 0) {
         e = scr.alloc(coarse_scratch_bytes(db, nq, p->shortlist), s);
         if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
@@ -443,6 +448,24 @@ lhr_status lhr_query_window(const lhr_db* db, const float* frames, const int32_t
     if ((st = check_agg_params(a)) != LHR_OK) return st;
     DeviceGuard g(db->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    if (p->score == LHR_F32 && p->shortlist > 0 && nw <= W && hier_fused_eligible(db, W, p->shortlist)) {
+        // the whole request -- retrieval and Algorithm 2 -- in one cooperative launch
+        AggArgs ag = make_agg(db, a);
+        ag.idx = idx;
+        ag.dist = dist;
+        ag.offsets = offsets;
+        ag.per_frame = p->k;
+        ag.limit = (long long)W * p->k;
+        ag.nw = nw;
+        ag.xy_out = xy;
+        ag.status = status;
+        Scratch scr;
+        cudaError_t e = scr.alloc(hier_scratch_bytes(db, W), s);
+        if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+        e = launch_hier_fused(db, frames, W, p->shortlist, p->k, idx, dist, &ag, scr.ptr, s);
+        if (e != cudaSuccess) return cuda_fail(e, "fused coarse-to-fine launch");
+        return LHR_OK;
+    }
     if ((st = run_retrieval(db, frames, W, p, idx, dist, s)) != LHR_OK) return st;
     AggArgs ag = make_agg(db, a);
     ag.idx = idx;

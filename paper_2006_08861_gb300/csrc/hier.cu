@@ -1,0 +1,535 @@
+// Fused coarse-to-fine retrieval and Algorithm 2 for a small request: up to
+// 8 query frames (one window of M frames, §3.1) in a single cooperative
+// launch of one CTA per SM. The steps are those of coarse.cu and aggregate.cu
+// (same keys, same tie rules, same tests); only the scheduling differs: a
+// building-scale request is a few microseconds of work, so instead of four
+// kernels with mostly idle SMs the whole GPU walks through five phases
+// separated by grid barriers:
+//   A  every CTA scores its slice of rows on the coarse prefix for every frame
+//      (packed FP32 FMAs), writes the distances to scratch and adds the
+//      key's top 11-bit digit to per-frame histograms;
+//   B  every CTA locates, per frame, the histogram bin holding the S-th key
+//      and appends its rows below that bin (direct list) and inside it
+//      (boundary list) with warp-aggregated atomics;
+//   C  all warps of the grid re-score every collected row on the full
+//      feature, one row per warp;
+//   D  CTA f cuts frame f's boundary list at its need-th coarse key (exactly
+//      S rows in all) and keeps the top k of the shortlist's full keys; a
+//      frame whose boundary bin overflowed is refined and ranked by CTA f
+//      alone, over the frame's distances;
+//   E  CTA w runs Algorithm 2 on window w's candidates (one warp).
+// The grid barrier is a global counter and generation word; waits give up
+// after kWaitLimitNs and record LHR_ERR_TIMEOUT.
+#include "aggregate.cuh"
+#include "common.cuh"
+#include "internal.h"
+#include "select.cuh"
+
+namespace lhr {
+namespace {
+
+using namespace sel;
+
+constexpr int kHT = 512;  // threads per CTA
+constexpr int kHW = kHT / 32;
+constexpr int kHBinCap = 4096;
+constexpr int kHMaxShort = 4096;
+constexpr int kHRegion = 64 * 1024;  // shared region reused by every phase
+constexpr int kHCtl = 8;             // control words per frame
+enum { cDirect = 0, cInBin = 1, cRefine = 2, cNeed = 3 };
+
+struct HierParams {
+    const float* Xc;
+    int dc;
+    const float* X;
+    int D;
+    int64_t n;
+    const float* Q;
+    int nf;
+    int S, k;
+    float* dcbuf;     // nf x n coarse distances
+    unsigned* hist;   // nf x kBins (zeroed)
+    unsigned* ctl;    // nf x kHCtl (zeroed)
+    unsigned* bar;    // grid barrier: count, generation (zeroed)
+    int* direct;      // nf x kHMaxShort rows below the boundary bin
+    u64* bins;        // nf x kHBinCap coarse keys in the boundary bin
+    u64* fkd;         // nf x kHMaxShort full keys of the direct rows
+    u64* fkb;         // nf x kHBinCap full keys of the boundary rows
+    int64_t* idx;     // nf x k
+    float* dist;
+    agg::AggParams ap;  // windows over the frames (per_frame = k), ap.a.nw of them; nw = 0: none
+    int* err;
+};
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Bounded grid-wide barrier (all CTAs are co-resident: cooperative launch).
+__device__ bool grid_sync(unsigned* bar, volatile int* abort_sm, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            const u64 t0 = globaltimer();
+            while (*gen == g) {
+                if (globaltimer() - t0 > kWaitLimitNs) {
+                    *abort_sm = 1;
+                    record_error(err, kErrTimeout);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *abort_sm == 0;
+}
+
+// Full-feature squared distance of row r to frame q, by one warp.
+template <int CPL>
+__device__ __forceinline__ float warp_dist(const float* X, int D, const float* q, uint32_t r, int lane) {
+    const int D4 = D / 4;
+    const float4* xr = reinterpret_cast<const float4*>(X + (size_t)r * D);
+    const float4* qr = reinterpret_cast<const float4*>(q);
+    float2 acc = f2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+        const int c = lane + 32 * j;
+        if (c < D4) {
+            const float4 x = __ldg(xr + c), qv = __ldg(qr + c);
+            const float2 a = __ffma2_rn(f2(x.x, x.y), f2(-1.f, -1.f), f2(qv.x, qv.y));
+            const float2 b = __ffma2_rn(f2(x.z, x.w), f2(-1.f, -1.f), f2(qv.z, qv.w));
+            acc = __ffma2_rn(a, a, acc);
+            acc = __ffma2_rn(b, b, acc);
+        }
+    }
+    float d = acc.x + acc.y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+    return d;
+}
+
+// Block bitonic sort of a[0, p2) ascending (p2 a power of two).
+__device__ void block_sort(u64* a, unsigned p2) {
+    for (unsigned size = 2; size <= p2; size <<= 1) {
+        for (unsigned stride = size >> 1; stride > 0; stride >>= 1) {
+            for (unsigned i = threadIdx.x; i < p2 / 2; i += blockDim.x) {
+                const unsigned lo = 2 * i - (i & (stride - 1));
+                const unsigned hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const u64 x = a[lo], y = a[hi];
+                if ((x > y) == up) {
+                    a[lo] = y;
+                    a[hi] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Warp lists in wl[kHW][32] -> frame f's final top k (warp 0 writes).
+__device__ void finish_frame(const HierParams& p, int f, u64 L, u64* wl) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    wl[warp * 32 + lane] = L;
+    __syncthreads();
+    if (warp == 0) {
+        u64 M = kKeyEmpty;
+        list_merge_keys<false>(M, wl, kHW * 32, p.k, lane);
+        if (lane < p.k) {
+            const size_t o = (size_t)f * p.k + lane;
+            if (M == kKeyEmpty) {
+                p.idx[o] = -1;
+                p.dist[o] = __int_as_float(0x7f800000);
+            } else {
+                p.idx[o] = (int64_t)key_row(M);
+                p.dist[o] = key_dist(M);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Frame f whose boundary bin overflowed: refine the radix select over the
+// frame's coarse distances, collect the S rows, rank them (this CTA alone).
+template <int CPL>
+__device__ void refine_frame(const HierParams& p, int f, unsigned char* region, u64* wl, unsigned* res,
+                             unsigned* tmp) {
+    const int t = threadIdx.x, warp = t / 32, lane = t % 32;
+    unsigned* hsm = reinterpret_cast<unsigned*>(region);               // kBins
+    u64* bin_keys = reinterpret_cast<u64*>(hsm + kBins);                // kHBinCap
+    int* short_rows = reinterpret_cast<int*>(bin_keys + kHBinCap);      // kHMaxShort
+    const float* dcf = p.dcbuf + (size_t)f * p.n;
+    unsigned need = (unsigned)p.S;
+    for (int i = t; i < kBins; i += kHT) hsm[i] = __ldcg(p.hist + (size_t)f * kBins + i);
+    __syncthreads();
+    find_bin<kHT>(hsm, need, res, tmp);
+    int shift = 52;
+    u64 lo = (u64)res[0] << shift, hi = lo + (1ull << shift);
+    need -= res[1];
+    unsigned in_bin = res[2];
+    while (in_bin > (unsigned)kHBinCap && shift > 0) {
+        const int nshift = shift >= 11 ? shift - 11 : 0;
+        const int dbits = shift - nshift;
+        __syncthreads();
+        for (int i = t; i < kBins; i += kHT) hsm[i] = 0u;
+        __syncthreads();
+        for (int64_t r = t; r < p.n; r += kHT) {
+            const u64 key = coarse_key(dcf, r);
+            if (key >= lo && key < hi) atomicAdd(&hsm[(unsigned)((key >> nshift) & ((1ull << dbits) - 1))], 1u);
+        }
+        __syncthreads();
+        find_bin<kHT>(hsm, need, res, tmp);
+        lo += (u64)res[0] << nshift;
+        hi = lo + (1ull << nshift);
+        need -= res[1];
+        in_bin = res[2];
+        shift = nshift;
+    }
+    __syncthreads();
+    if (t == 0) {
+        res[0] = 0u;
+        res[1] = 0u;
+    }
+    __syncthreads();
+    for (int64_t r = t; r < p.n; r += kHT) {
+        const u64 key = coarse_key(dcf, r);
+        if (key < lo) {
+            const unsigned pos = atomicAdd(&res[0], 1u);
+            if (pos < (unsigned)kHMaxShort) short_rows[pos] = (int)r;
+        } else if (key < hi) {
+            const unsigned pos = atomicAdd(&res[1], 1u);
+            if (pos < (unsigned)kHBinCap) bin_keys[pos] = key;
+        }
+    }
+    __syncthreads();
+    const unsigned direct = min(res[0], (unsigned)kHMaxShort);
+    const unsigned nb = min(res[1], (unsigned)kHBinCap);
+    unsigned p2 = 1;
+    while (p2 < nb) p2 <<= 1;
+    for (unsigned i = nb + t; i < p2; i += kHT) bin_keys[i] = kKeyEmpty;
+    __syncthreads();
+    block_sort(bin_keys, p2);
+    need = min(need, nb);
+    for (unsigned i = t; i < need && direct + i < (unsigned)kHMaxShort; i += kHT)
+        short_rows[direct + i] = (int)key_row(bin_keys[i]);
+    __syncthreads();
+    const int total = (int)min(direct + need, (unsigned)kHMaxShort);
+    const float* q = p.Q + (size_t)f * p.D;
+    u64 L = kKeyEmpty, thr = kKeyEmpty;
+    for (int i = warp; i < total; i += kHW) {
+        const uint32_t r = (uint32_t)short_rows[i];
+        const u64 key = make_key(warp_dist<CPL>(p.X, p.D, q, r, lane), r);
+        if (key < thr) {
+            list_insert(L, key, p.k, lane);
+            thr = __shfl_sync(kFull, L, p.k - 1);
+        }
+    }
+    finish_frame(p, f, L, wl);
+}
+
+template <int DC4, int CPL>
+__global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char* region = smem;                                           // kHRegion
+    float4* qsc = reinterpret_cast<float4*>(smem + kHRegion);               // 8 frames x DC4
+    u64* wl = reinterpret_cast<u64*>(qsc + 8 * DC4);                        // kHW x 32
+    unsigned* fr = reinterpret_cast<unsigned*>(wl + kHW * 32);              // per frame: lo(2) hi(2) flags
+    unsigned* res = fr + 8 * 8;                                             // 4
+    unsigned* tmp = res + 4;                                                // kHW
+    volatile int* abort_sm = reinterpret_cast<volatile int*>(tmp + kHW);
+
+    const int t = threadIdx.x, warp = t / 32, lane = t % 32;
+    const int nf = p.nf;
+    const int64_t per = (p.n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = min(p.n, (int64_t)blockIdx.x * per), r1 = min(p.n, r0 + per);
+    if (t == 0) *abort_sm = 0;
+
+    // ------------------------------------------------ A: coarse distances + histograms
+    unsigned* hsm = reinterpret_cast<unsigned*>(region);  // nf x kBins
+    for (int i = t; i < nf * kBins; i += kHT) hsm[i] = 0u;
+    const int dc4 = p.dc / 4;
+    for (int i = t; i < 8 * DC4; i += kHT) {
+        const int f = i / DC4, c = i % DC4;
+        qsc[i] = (f < nf && c < dc4) ? reinterpret_cast<const float4*>(p.Q + (size_t)f * p.D)[c]
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    for (int64_t row = r0 + t; row < r1; row += kHT) {
+        float4 x[DC4];
+        const float4* xr = reinterpret_cast<const float4*>(p.Xc + row * p.dc);
+#pragma unroll
+        for (int c = 0; c < DC4; ++c) x[c] = c < dc4 ? __ldg(xr + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int f = 0; f < nf; ++f) {
+            float2 acc = f2(0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < DC4; ++c) {
+                const float4 qv = qsc[f * DC4 + c];
+                const float2 a = __ffma2_rn(f2(x[c].x, x[c].y), f2(-1.f, -1.f), f2(qv.x, qv.y));
+                const float2 b = __ffma2_rn(f2(x[c].z, x[c].w), f2(-1.f, -1.f), f2(qv.z, qv.w));
+                acc = __ffma2_rn(a, a, acc);
+                acc = __ffma2_rn(b, b, acc);
+            }
+            const float d = acc.x + acc.y;
+            p.dcbuf[(size_t)f * p.n + row] = d;
+            atomicAdd(&hsm[f * kBins + (__float_as_uint(d) >> 20)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = t; i < nf * kBins; i += kHT) {
+        const unsigned v = hsm[i];
+        if (v) atomicAdd(&p.hist[i], v);
+    }
+    if (!grid_sync(p.bar, abort_sm, p.err)) return;
+
+    // ------------------------------------------------ B: boundary bin per frame, collect
+    const bool take_all = p.n <= p.S;
+    for (int f = 0; f < nf; ++f) {
+        if (take_all) {
+            if (t == 0) {
+                *reinterpret_cast<u64*>(&fr[f * 8 + 0]) = ~0ull;
+                *reinterpret_cast<u64*>(&fr[f * 8 + 2]) = ~0ull;
+                fr[f * 8 + 4] = 0u;
+            }
+            continue;
+        }
+        for (int i = t; i < kBins; i += kHT) hsm[i] = __ldcg(p.hist + (size_t)f * kBins + i);
+        __syncthreads();
+        find_bin<kHT>(hsm, (unsigned)p.S, res, tmp);
+        if (t == 0) {
+            const u64 lo = (u64)res[0] << 52;
+            *reinterpret_cast<u64*>(&fr[f * 8 + 0]) = lo;
+            *reinterpret_cast<u64*>(&fr[f * 8 + 2]) = lo + (1ull << 52);
+            fr[f * 8 + 4] = res[2] > (unsigned)kHBinCap ? 1u : 0u;
+            if (blockIdx.x == 0) {
+                p.ctl[f * kHCtl + cRefine] = fr[f * 8 + 4];
+                p.ctl[f * kHCtl + cNeed] = (unsigned)p.S - res[1];
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int64_t base = r0; base < r1; base += kHT) {
+        const int64_t row = base + t;
+        const bool valid = row < r1;
+        for (int f = 0; f < nf; ++f) {
+            if (fr[f * 8 + 4]) continue;  // refined in phase D
+            const u64 lo = *reinterpret_cast<const u64*>(&fr[f * 8 + 0]);
+            const u64 hi = *reinterpret_cast<const u64*>(&fr[f * 8 + 2]);
+            const u64 key = valid ? coarse_key(p.dcbuf + (size_t)f * p.n, row) : kKeyEmpty;
+            const bool d = valid && (take_all || key < lo);
+            const bool b = valid && !d && key < hi;
+            warp_append(d, &p.ctl[f * kHCtl + cDirect], kHMaxShort, p.direct + (size_t)f * kHMaxShort, nullptr, row,
+                        0, lane);
+            warp_append(b, &p.ctl[f * kHCtl + cInBin], kHBinCap, nullptr, p.bins + (size_t)f * kHBinCap, row, key,
+                        lane);
+        }
+    }
+    if (!grid_sync(p.bar, abort_sm, p.err)) return;
+
+    // ------------------------------------------------ C: full distances of every collected row
+    unsigned* cnts = reinterpret_cast<unsigned*>(region);  // per frame: direct, in-bin (0 if refined)
+    if (t < nf) {
+        const bool rf = __ldcg(&p.ctl[t * kHCtl + cRefine]) != 0u;
+        cnts[2 * t] = rf ? 0u : min(__ldcg(&p.ctl[t * kHCtl + cDirect]), (unsigned)kHMaxShort);
+        cnts[2 * t + 1] = rf ? 0u : min(__ldcg(&p.ctl[t * kHCtl + cInBin]), (unsigned)kHBinCap);
+    }
+    __syncthreads();
+    {
+        unsigned total = 0;
+        for (int f = 0; f < nf; ++f) total += cnts[2 * f] + cnts[2 * f + 1];
+        const unsigned gw = blockIdx.x * kHW + warp, GW = gridDim.x * kHW;
+        for (unsigned item = gw; item < total; item += GW) {
+            unsigned j = item;
+            int f = 0;
+            while (j >= cnts[2 * f] + cnts[2 * f + 1]) {
+                j -= cnts[2 * f] + cnts[2 * f + 1];
+                ++f;
+            }
+            const bool is_direct = j < cnts[2 * f];
+            const uint32_t row = is_direct ? (uint32_t)__ldcg(p.direct + (size_t)f * kHMaxShort + j)
+                                           : key_row(__ldcg(p.bins + (size_t)f * kHBinCap + (j - cnts[2 * f])));
+            const float d = warp_dist<CPL>(p.X, p.D, p.Q + (size_t)f * p.D, row, lane);
+            if (lane == 0) {
+                if (is_direct) p.fkd[(size_t)f * kHMaxShort + j] = make_key(d, row);
+                else p.fkb[(size_t)f * kHBinCap + (j - cnts[2 * f])] = make_key(d, row);
+            }
+        }
+    }
+    if (!grid_sync(p.bar, abort_sm, p.err)) return;
+
+    // ------------------------------------------------ D: per frame, exact S-cut and top k
+    if ((int)blockIdx.x < nf) {
+        const int f = blockIdx.x;
+        if (__ldcg(&p.ctl[f * kHCtl + cRefine]) != 0u) {
+            refine_frame<CPL>(p, f, region, wl, res, tmp);
+        } else {
+            const unsigned cd = min(__ldcg(&p.ctl[f * kHCtl + cDirect]), (unsigned)kHMaxShort);
+            const unsigned nb = min(__ldcg(&p.ctl[f * kHCtl + cInBin]), (unsigned)kHBinCap);
+            const unsigned need = take_all ? 0u : min(__ldcg(&p.ctl[f * kHCtl + cNeed]), nb);
+            u64* sk = reinterpret_cast<u64*>(region);  // kHBinCap
+            unsigned p2 = 1;
+            while (p2 < nb) p2 <<= 1;
+            for (unsigned i = t; i < p2; i += kHT) sk[i] = i < nb ? __ldcg(p.bins + (size_t)f * kHBinCap + i) : kKeyEmpty;
+            __syncthreads();
+            block_sort(sk, p2);
+            const u64 cstar = need > 0 ? sk[need - 1] : 0ull;  // last boundary key inside the shortlist
+            u64 L = kKeyEmpty, thr = kKeyEmpty;
+            for (unsigned base = 0; base < cd + nb; base += kHT) {
+                const unsigned i = base + t;
+                u64 key = kKeyEmpty;
+                if (i < cd) {
+                    key = __ldcg(p.fkd + (size_t)f * kHMaxShort + i);
+                } else if (i < cd + nb && need > 0) {
+                    const unsigned j = i - cd;
+                    if (__ldcg(p.bins + (size_t)f * kHBinCap + j) <= cstar) key = __ldcg(p.fkb + (size_t)f * kHBinCap + j);
+                }
+                unsigned m = __ballot_sync(kFull, key < thr);
+                while (m) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1;
+                    list_insert(L, __shfl_sync(kFull, key, j), p.k, lane);
+                }
+                thr = __shfl_sync(kFull, L, p.k - 1);
+            }
+            finish_frame(p, f, L, wl);
+        }
+    }
+    if (p.ap.a.nw == 0) return;
+    if (!grid_sync(p.bar, abort_sm, p.err)) return;
+
+    // ------------------------------------------------ E: Algorithm 2 per window
+    if ((int)blockIdx.x < p.ap.a.nw && warp == 0) {
+        const AggArgs& a = p.ap.a;
+        const int w = blockIdx.x;
+        const long long b0 = (long long)a.offsets[w] * a.per_frame, b1 = (long long)a.offsets[w + 1] * a.per_frame;
+        const long long total = b1 - b0;
+        if (total <= 0 || total > agg::kWarpCand || b0 < 0 || b1 > a.limit) {
+            if (lane == 0) agg::write_invalid(a, w);
+        } else {
+            u64* keys = reinterpret_cast<u64*>(region);                      // kWarpCand
+            int* rows = reinterpret_cast<int*>(keys + agg::kWarpCand);       // kWarpCand
+            float* dd = reinterpret_cast<float*>(rows + agg::kWarpCand);     // kWarpCand
+            int* cnt = reinterpret_cast<int*>(dd + agg::kWarpCand);          // kWarpCand + 1
+            agg::aggregate_warp(p.ap, w, b0, total, keys, rows, dd, cnt);
+        }
+    }
+}
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct HierLayout {
+    size_t dcbuf, hist, ctl, bar, zero_end, direct, bins, fkd, fkb, total;
+};
+
+HierLayout hlayout(const lhr_db* db, int nf) {
+    HierLayout L{};
+    L.dcbuf = 0;
+    L.hist = a256((size_t)nf * db->n * sizeof(float));
+    L.ctl = L.hist + (size_t)nf * kBins * sizeof(unsigned);
+    L.bar = L.ctl + (size_t)nf * kHCtl * sizeof(unsigned);
+    L.zero_end = L.bar + 2 * sizeof(unsigned);
+    L.direct = a256(L.zero_end);
+    L.bins = a256(L.direct + (size_t)nf * kHMaxShort * sizeof(int));
+    L.fkd = a256(L.bins + (size_t)nf * kHBinCap * sizeof(u64));
+    L.fkb = a256(L.fkd + (size_t)nf * kHMaxShort * sizeof(u64));
+    L.total = a256(L.fkb + (size_t)nf * kHBinCap * sizeof(u64));
+    return L;
+}
+
+size_t hier_smem(int dc4) {
+    return kHRegion + (size_t)8 * dc4 * sizeof(float4) + kHW * 32 * sizeof(u64) +
+           (8 * 8 + 4 + kHW + 4) * sizeof(unsigned);
+}
+
+template <int DC4, int CPL>
+cudaError_t launch_h(const HierParams& hp, int grid, cudaStream_t stream) {
+    auto kern = hier_fused_kernel<DC4, CPL>;
+    const size_t sm = hier_smem(DC4);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kHT);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ProfScope ps("hier_fused_kernel", stream);
+    return cudaLaunchKernelEx(&cfg, kern, hp);
+}
+
+}  // namespace
+
+bool hier_fused_eligible(const lhr_db* db, int nq, int shortlist) {
+    return nq >= 1 && nq <= 8 && db->Xc != nullptr && db->n_sub == 1 && shortlist <= kHMaxShort &&
+           db->coarse_dim <= 128;
+}
+
+size_t hier_scratch_bytes(const lhr_db* db, int nq) { return hlayout(db, nq).total; }
+
+cudaError_t launch_hier_fused(const lhr_db* db, const float* q, int nq, int shortlist, int k, int64_t* idx,
+                              float* dist, const AggArgs* agg_args, void* scratch, cudaStream_t stream) {
+    const HierLayout L = hlayout(db, nq);
+    unsigned char* base = reinterpret_cast<unsigned char*>(scratch);
+    cudaError_t e = cudaMemsetAsync(base + L.hist, 0, L.zero_end - L.hist, stream);
+    if (e != cudaSuccess) return e;
+    HierParams hp{};
+    hp.Xc = db->Xc;
+    hp.dc = db->coarse_dim;
+    hp.X = db->X;
+    hp.D = db->dim;
+    hp.n = db->n;
+    hp.Q = q;
+    hp.nf = nq;
+    hp.S = shortlist;
+    hp.k = k;
+    hp.dcbuf = reinterpret_cast<float*>(base + L.dcbuf);
+    hp.hist = reinterpret_cast<unsigned*>(base + L.hist);
+    hp.ctl = reinterpret_cast<unsigned*>(base + L.ctl);
+    hp.bar = reinterpret_cast<unsigned*>(base + L.bar);
+    hp.direct = reinterpret_cast<int*>(base + L.direct);
+    hp.bins = reinterpret_cast<u64*>(base + L.bins);
+    hp.fkd = reinterpret_cast<u64*>(base + L.fkd);
+    hp.fkb = reinterpret_cast<u64*>(base + L.fkb);
+    hp.idx = idx;
+    hp.dist = dist;
+    hp.err = db->err;
+    if (agg_args) {
+        hp.ap.a = *agg_args;
+        hp.ap.tile = db->tile;
+        hp.ap.xy = db->xy;
+        hp.ap.n = db->n;
+        hp.ap.rlim = (long long)floor(sqrt((double)agg_args->r2max)) + 1;
+        hp.ap.err = db->err;
+    } else {
+        hp.ap.a.nw = 0;
+    }
+    const int dc4 = db->coarse_dim / 4;
+    const int d4 = db->dim / 4;
+    const int cpl = d4 <= 32 ? 1 : (d4 <= 64 ? 2 : 4);
+    const int grid = db->sms;
+    if (dc4 <= 8) {
+        if (cpl == 1) return launch_h<8, 1>(hp, grid, stream);
+        if (cpl == 2) return launch_h<8, 2>(hp, grid, stream);
+        return launch_h<8, 4>(hp, grid, stream);
+    }
+    if (dc4 <= 16) {
+        if (cpl == 1) return launch_h<16, 1>(hp, grid, stream);
+        if (cpl == 2) return launch_h<16, 2>(hp, grid, stream);
+        return launch_h<16, 4>(hp, grid, stream);
+    }
+    if (cpl == 1) return launch_h<32, 1>(hp, grid, stream);
+    if (cpl == 2) return launch_h<32, 2>(hp, grid, stream);
+    return launch_h<32, 4>(hp, grid, stream);
+}
+
+}  // namespace lhr

@@ -92,6 +92,15 @@ size_t scan_scratch_bytes(const lhr_db* db, int nq, int k);
 cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t* idx, float* dist,
                         void* scratch, cudaStream_t stream);
 
+struct AggArgs;
+
+// Fused coarse-to-fine (+ optional Algorithm 2) for requests of at most 8
+// frames: one cooperative launch (hier.cu).
+bool hier_fused_eligible(const lhr_db* db, int nq, int shortlist);
+size_t hier_scratch_bytes(const lhr_db* db, int nq);
+cudaError_t launch_hier_fused(const lhr_db* db, const float* q, int nq, int shortlist, int k, int64_t* idx,
+                              float* dist, const AggArgs* agg_args, void* scratch, cudaStream_t stream);
+
 // Low-precision tensor-core scores + FP32 re-rank (lowp.cu).
 size_t lowp_scratch_bytes(const lhr_db* db, int nq, bool fp8, int W);
 cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int W, int k, int64_t* idx, float* dist,

@@ -201,6 +201,15 @@ __device__ __noinline__ void flush_buffer(u64* list, const u64* buf, int stride,
     for (int o = 0; o < W; ++o) list[o] = out[o];
 }
 
+// Main pass: moves a thread's buffered keys (shared memory, stride kTile) to its
+// query's candidate buffer with one atomic. Returns the new buffer fill (0).
+__device__ __noinline__ int append_candidates(const TcParams& p, int64_t qi, const u64* buf, int nb) {
+    const unsigned pos = atomicAdd(&p.cnt[qi], (unsigned)nb);
+    for (int i = 0; i < nb; ++i)
+        if (pos + i < (unsigned)kCap) p.cand[(size_t)qi * kCap + pos + i] = buf[i * kTile];
+    return 0;
+}
+
 template <bool kFp8, int MODE, int WMAX>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
@@ -225,8 +234,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char* sA = smem;                                   // slices x 16 KB
     unsigned char* sB = sA + (size_t)p.slices * kSliceTile;     // kStages x 16 KB
     float2* sSN = reinterpret_cast<float2*>(sB + (size_t)kStages * kSliceTile);  // 2 x 128
-    u64* sBuf = reinterpret_cast<u64*>(sSN + 2 * kTile);        // full pass: kBuf x 128 (slot-major)
-    u64* bars = MODE == kModeFull ? sBuf + kBuf * kTile : sBuf;
+    u64* sBuf = reinterpret_cast<u64*>(sSN + 2 * kTile);        // main / full pass: kBuf x 128 (slot-major)
+    u64* bars = MODE != kModePilot ? sBuf + kBuf * kTile : sBuf;
     u64* full = bars;
     u64* empty = full + kStages;
     u64* a_full = empty + kStages;
@@ -354,8 +363,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         u64 tau = kKeyEmpty;
         float tau_score = __int_as_float(0x7f800000);
         if (MODE == kModeMain && qvalid) {
+            // tau = the kPilotR-th smallest pilot key; one pilot chunk's list per
+            // pass, its loads issued together
             const u64* pl = p.pilot + (size_t)qi * p.pchunks * kPilotR;
-            for (int i = 0; i < p.pchunks * kPilotR; ++i) net_insert(net, pl[i]);
+            for (int c = 0; c < p.pchunks; ++c) {
+                u64 kk[kPilotR];
+#pragma unroll
+                for (int i = 0; i < kPilotR; ++i) kk[i] = __ldcg(pl + (size_t)c * kPilotR + i);
+#pragma unroll
+                for (int i = 0; i < kPilotR; ++i) net_insert(net, kk[i]);
+            }
             tau = net[kPilotR - 1];
             tau_score = tau == kKeyEmpty ? __int_as_float(0x7f800000) : key_score(tau);
         }
@@ -383,7 +400,38 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int c0 = 0; c0 < kTile; c0 += 32) {
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kTile + c0), v);
-                if (qvalid) {
+                if (MODE == kModeMain && qvalid) {
+                    // branch-free scoring of 32 columns (packed pairs) into a
+                    // survivor mask; survivors are rare and handled after
+                    float sc[32];
+                    unsigned mask = 0u;
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2) {
+                        const float4 s4 = *reinterpret_cast<const float4*>(snt + c0 + j);  // s_j n_j s_j+1 n_j+1
+                        const float2 prod = __fmul2_rn(make_float2(s4.x, s4.z),
+                                                       make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])));
+                        const float2 s2 = __ffma2_rn(make_float2(m, m), prod, make_float2(s4.y, s4.w));
+                        sc[j] = s2.x;
+                        sc[j + 1] = s2.y;
+                        mask |= (s2.x <= tau_score ? 1u : 0u) << j;
+                        mask |= (s2.y <= tau_score ? 1u : 0u) << (j + 1);
+                    }
+                    const int valid = nr - c0;
+                    if (valid < 32) mask &= valid > 0 ? ((1u << valid) - 1u) : 0u;
+                    if (mask) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if ((mask >> j) & 1u) {
+                                const u64 key = score_key(sc[j], (uint32_t)(r + c0 + j));
+                                if (key <= tau) {
+                                    buf[nb * kTile] = key;
+                                    if (++nb == kBuf) nb = append_candidates(p, qi, buf, nb);
+                                }
+                            }
+                        }
+                    }
+                }
+                if (MODE != kModeMain && qvalid) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int col = c0 + j;
@@ -391,14 +439,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const float score = fmaf(m, sn.x * __uint_as_float(v[j]), sn.y);
                         if (MODE == kModePilot) {
                             if (col < nr) net_insert(net, score_key(score, (uint32_t)(r + col)));
-                        } else if (MODE == kModeMain) {
-                            if (col < nr && score <= tau_score) {
-                                const u64 key = score_key(score, (uint32_t)(r + col));
-                                if (key <= tau) {
-                                    const unsigned pos = atomicAdd(&p.cnt[qi], 1u);
-                                    if (pos < (unsigned)kCap) p.cand[(size_t)qi * kCap + pos] = key;
-                                }
-                            }
                         } else {
                             const u64 key = score_key(score, (uint32_t)(r + col));
                             if (col < nr && key < thr) {
@@ -425,6 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int i = 0; i < kPilotR; ++i) dst[i] = net[i];
         }
+        if (MODE == kModeMain && nb) append_candidates(p, qi, buf, nb);
         if (MODE == kModeFull) {
             if (nb) flush_buffer<WMAX>(list, buf, kTile, nb, p.W);
             if (qvalid) {
@@ -701,7 +742,7 @@ LowpPlan plan(const lhr_db* db, int nq, bool fp8, int W) {
 
 size_t tc_smem(int slices, int mode) {
     return 1024 + (size_t)slices * kSliceTile + (size_t)kStages * kSliceTile + 2 * kTile * sizeof(float2) +
-           (mode == kModeFull ? (size_t)kBuf * kTile * sizeof(u64) : 0) + (2 * kStages + 9) * sizeof(u64) + 16;
+           (mode != kModePilot ? (size_t)kBuf * kTile * sizeof(u64) : 0) + (2 * kStages + 9) * sizeof(u64) + 16;
 }
 
 template <bool kFp8, int MODE, int WMAX>

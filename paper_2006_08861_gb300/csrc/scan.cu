@@ -65,6 +65,7 @@ struct ScanParams {
     float margin_scale;  // 2 (gamma_D + 3u)
     u64* partial;        // [qblock][QB][nchunks][k]
     unsigned* counters;  // [qblock]
+    unsigned* gthr;      // [qblock * QB][n_sub]: grid-wide k-th distance bound (float bits)
     int64_t* idx;        // [nq][n_sub][k]
     float* dist;
     int* err;
@@ -185,13 +186,27 @@ __global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(cons
         float thr_own = __int_as_float(0x7f800000);  // k-th distance of this warp's list for frame myq
         u64* wlist = lists + (size_t)warp * QB * 32;
         const volatile unsigned* thr_v = thr_sh;     // other warps lower it with atomicMin
+        // grid-wide per-frame bound: the smallest k-th distance any warp of any
+        // CTA of this subspace holds (float bits; 0xffffffff = none yet)
+        unsigned* gthr = p.gthr + ((size_t)qblock * QB) * p.n_sub + ch.z;
+        // row norms of this warp's next stage, loaded one stage ahead
+        float xn_next = 0.f;
+        if (warp < iters) {
+            const int r = row0 + warp * kRPS;
+            xn_next = lane < min(kRPS, row1 - r) ? __ldg(p.xnorm + r + lane) : 0.f;
+        }
 
         for (int it = warp; it < iters; it += warps) {
             const int s = it % NS;
             const uint32_t ph = (uint32_t)(it / NS) & 1u;
             const int rbase = row0 + it * kRPS;
             const int nr = min(kRPS, row1 - rbase);
-            const float xn_l = lane < nr ? __ldg(p.xnorm + rbase + lane) : 0.f;
+            const float xn_l = xn_next;
+            if (it + warps < iters) {
+                const int r = row0 + (it + warps) * kRPS;
+                xn_next = lane < min(kRPS, row1 - r) ? __ldg(p.xnorm + r + lane) : 0.f;
+            }
+            const unsigned gbound = lane < QB ? __ldcg(gthr + (size_t)lane * p.n_sub) : 0xffffffffu;
             if (!mbar_wait(&full[s], ph, abort_flag)) {
                 if (lane == 0) {
                     *abort_flag = 1;
@@ -278,6 +293,14 @@ __global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(cons
                     }
                     __syncwarp();
                 }
+            }
+            // exchange bounds with the rest of the grid (gbound was loaded at the
+            // stage's start): publish ours only when it is better, so the few
+            // global words see rare atomics
+            if (lane < QB) {
+                const unsigned mine = thr_v[lane];
+                if (mine < gbound) atomicMin(gthr + (size_t)lane * p.n_sub, mine);
+                else if (gbound < mine) atomicMin(&thr_sh[lane], gbound);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
@@ -423,7 +446,8 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t scan_scratch_bytes(const lhr_db* db, int nq, int k) {
     const ScanConfig c = choose_config(db, nq);
     const size_t nqb = (nq + c.qb - 1) / c.qb;
-    return align256(nqb * c.qb * (size_t)db->nchunks * k * sizeof(u64)) + align256(nqb * sizeof(unsigned));
+    return align256(nqb * c.qb * (size_t)db->nchunks * k * sizeof(u64)) + align256(nqb * sizeof(unsigned)) +
+           align256(nqb * c.qb * (size_t)db->n_sub * sizeof(unsigned));
 }
 
 cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t* idx, float* dist, void* scratch,
@@ -451,10 +475,14 @@ cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t
     p.partial = reinterpret_cast<u64*>(scratch);
     const size_t part_bytes = align256((size_t)nqb * c.qb * db->nchunks * k * sizeof(u64));
     p.counters = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(scratch) + part_bytes);
+    p.gthr = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(scratch) + part_bytes +
+                                         align256(nqb * sizeof(unsigned)));
     p.idx = idx;
     p.dist = dist;
     p.err = db->err;
     cudaError_t e = cudaMemsetAsync(p.counters, 0, nqb * sizeof(unsigned), stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(p.gthr, 0xff, (size_t)nqb * c.qb * db->n_sub * sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
     switch (c.cpl * 100 + c.qb) {
         case 104: return launch_t<4, 1>(c, p, nqb, stream);

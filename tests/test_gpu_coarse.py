@@ -81,6 +81,34 @@ def test_boundary_bin_overflow_refines_to_rows(lhr):
         assert np.all(gi[qi] < S)
 
 
+def test_fused_small_requests(lhr):
+    # Requests of at most 8 frames take the single-launch fused path: one
+    # window of m = 5 frames per call (the building-scale benchmark's call),
+    # and one call carrying two windows of 3 and 4 frames.
+    cfg = synth.CONFIGS["hierarchical"]
+    db = synth.make_database(cfg["n"], cfg["dim"], seed=1001)
+    h = lhr.lhr_build_db(db.feats, db.xy, coarse_dim=cfg["coarse_dim"])
+    wins = synth.make_windows(db, 4, cfg["m"], seed=2101)
+    two = synth.make_windows(db, 2, (3, 4), seed=2102)
+    calls = [(wins.frames[wins.offsets[w]:wins.offsets[w + 1]], np.array([0, 5], np.int32)) for w in range(4)]
+    calls.append((two.frames, two.offsets))
+    for frames, offs in calls:
+        idx, dist, xy, st = lhr.lhr_query_window(h, torch.from_numpy(np.ascontiguousarray(frames)).cuda(),
+                                                 torch.from_numpy(offs).cuda(), cfg["k"],
+                                                 shortlist=cfg["shortlist"], mode="tile")
+        torch.cuda.synchronize()
+        gi, gd = idx.cpu().numpy()[:, 0], dist.cpu().numpy()[:, 0]
+        o_idx, o_dist, _ = oret.hierarchical_topk(frames, db.feats, cfg["coarse_dim"], cfg["shortlist"],
+                                                  cfg["k"] + 1)
+        for f in range(frames.shape[0]):
+            if _shortlist_separated(frames[f], db.feats, cfg["coarse_dim"], cfg["shortlist"]):
+                check_list(frames[f], db.feats, gi[f], gd[f], o_idx[f], o_dist[f], cfg["k"], where=f"f{f}")
+        o_xy, o_st = oagg.aggregate_windows(oret.window_candidates(gi, offs), db.xy, mode="tile")
+        assert np.array_equal(st.cpu().numpy(), o_st)
+        assert np.max(np.abs(xy.cpu().numpy() - o_xy)) <= XY_ATOL
+    assert lhr.lhr_db_error(h) == 0
+
+
 def test_hierarchical_configuration_windows(lhr):
     # Building scale: N = 100,000, D = 256, coarse prefix 32, shortlist 512,
     # k = 20, windows of m = 5 frames 0.3 m apart, aggregated in 2-D.
