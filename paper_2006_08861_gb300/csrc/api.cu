@@ -128,7 +128,8 @@ static bool is_device_ptr(const void* p) {
 static void free_db(lhr_db* db) {
     if (!db) return;
     void* bufs[] = {db->X, db->xnorm, db->Xc, db->perm, db->xy, db->tile, db->chunks, db->chunk_off,
-                    db->Xb, db->snb, db->X8, db->sn8, db->Xb_s, db->snb_s, db->X8_s, db->sn8_s, db->err};
+                    db->Xb, db->snb, db->X8, db->sn8, db->Xb_s, db->snb_s, db->X8_s, db->sn8_s,
+                    db->Xp, db->sub_p, db->err};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete db;
@@ -184,9 +185,9 @@ static lhr_status run_retrieval(const lhr_db* db, const float* q, int nq, const 
         e = launch_coarse(db, q, nq, p->shortlist, p->k, idx, dist, scr.ptr, s);
         if (e != cudaSuccess) return cuda_fail(e, "coarse-to-fine launch");
     } else {
-        e = scr.alloc(scan_scratch_bytes(db, nq, p->k), s);
+        e = scr.alloc(scan_scratch_bytes(db, nq, p->k, true), s);
         if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
-        e = launch_scan(db, q, nq, p->k, idx, dist, scr.ptr, s);
+        e = launch_scan(db, q, nq, p->k, idx, dist, scr.ptr, true, s);
         if (e != cudaSuccess) return cuda_fail(e, "scan launch");
     }
     return LHR_OK;
@@ -385,9 +386,29 @@ lhr_status lhr_build_db(const float* feats, const double* xy, const int32_t* sub
     cudaMemcpyAsync(db->chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(db->chunk_off, db->chunk_off_h.data(), db->chunk_off_h.size() * sizeof(int32_t),
                     cudaMemcpyHostToDevice, s);
+    if (n >= kPilotMinRows) {
+        // Pilot sample of the exhaustive scan: internal rows j * 64, each with
+        // the subspace of its row (subspaces are contiguous in internal order).
+        db->n_pilot = (n + kSampleStride - 1) / kSampleStride;
+        std::vector<int32_t> sub_p(db->n_pilot);
+        int64_t r0 = 0;
+        for (int s2 = 0; s2 < db->n_sub; ++s2) {
+            const int64_t r1 = r0 + db->sub_rows_h[s2];
+            for (int64_t j = (r0 + kSampleStride - 1) / kSampleStride; j * kSampleStride < r1; ++j) sub_p[j] = s2;
+            r0 = r1;
+        }
+        if ((e = dalloc(&db->Xp, (size_t)db->n_pilot * D)) != cudaSuccess ||
+            (e = dalloc(&db->sub_p, (size_t)db->n_pilot)) != cudaSuccess)
+            return bail(cuda_fail(e, "allocate pilot sample"));
+        e = cudaMemcpyAsync(db->sub_p, sub_p.data(), sub_p.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        // sub_p is read by the copy: finish it before the vector goes out of scope
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "pilot sample"));
+    }
     if ((e = launch_build_derived(db, s)) != cudaSuccess) return bail(cuda_fail(e, "derived arrays"));
     if ((e = launch_norms(db, reinterpret_cast<unsigned*>(flag + 1), s)) != cudaSuccess)
         return bail(cuda_fail(e, "norms"));
+    if ((e = launch_pilot_sample(db, s)) != cudaSuccess) return bail(cuda_fail(e, "pilot sample"));
     int32_t flag_h2[2] = {0, 0};
     cudaMemcpyAsync(flag_h2, flag, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(cuda_fail(e, "build"));

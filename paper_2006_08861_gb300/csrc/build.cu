@@ -117,6 +117,15 @@ __global__ void sample_rows_kernel(const uint4* codes, const float2* sn, int64_t
     }
 }
 
+// FP32 rows 0, stride, 2 stride, ...
+__global__ void pilot_rows_kernel(const float4* X, int64_t ns, int stride, int row_f4, float4* Xp) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns * row_f4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / row_f4, c = i % row_f4;
+        Xp[i] = X[r * stride * row_f4 + c];
+    }
+}
+
 int grid_for(int64_t work, int sms) {
     const int64_t b = (work + 255) / 256;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sms * 8));
@@ -143,6 +152,14 @@ cudaError_t launch_tiles(const double* xy, int64_t n, double t, int32_t* tile, i
 cudaError_t launch_norms(const lhr_db* db, unsigned* max_bits, cudaStream_t stream) {
     const int grid = (int)std::min<int64_t>((db->n + 7) / 8, (int64_t)db->sms * 16);
     norms_kernel<<<grid, 256, 0, stream>>>(db->X, db->n, db->dim, db->xnorm, max_bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pilot_sample(const lhr_db* db, cudaStream_t stream) {
+    if (!db->Xp) return cudaSuccess;
+    const int row_f4 = db->dim / 4;
+    pilot_rows_kernel<<<grid_for(db->n_pilot * row_f4, db->sms), 256, 0, stream>>>(
+        reinterpret_cast<const float4*>(db->X), db->n_pilot, kSampleStride, row_f4, reinterpret_cast<float4*>(db->Xp));
     return cudaGetLastError();
 }
 

@@ -114,25 +114,6 @@ __device__ __forceinline__ float warp_dist(const float* X, int D, const float* q
     return d;
 }
 
-// Block bitonic sort of a[0, p2) ascending (p2 a power of two).
-__device__ void block_sort(u64* a, unsigned p2) {
-    for (unsigned size = 2; size <= p2; size <<= 1) {
-        for (unsigned stride = size >> 1; stride > 0; stride >>= 1) {
-            for (unsigned i = threadIdx.x; i < p2 / 2; i += blockDim.x) {
-                const unsigned lo = 2 * i - (i & (stride - 1));
-                const unsigned hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const u64 x = a[lo], y = a[hi];
-                if ((x > y) == up) {
-                    a[lo] = y;
-                    a[hi] = x;
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
 // Warp lists in wl[kHW][32] -> frame f's final top k (warp 0 writes).
 __device__ void finish_frame(const HierParams& p, int f, u64 L, u64* wl) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -210,15 +191,20 @@ __device__ void refine_frame(const HierParams& p, int f, unsigned char* region, 
     __syncthreads();
     const unsigned direct = min(res[0], (unsigned)kHMaxShort);
     const unsigned nb = min(res[1], (unsigned)kHBinCap);
-    unsigned p2 = 1;
-    while (p2 < nb) p2 <<= 1;
-    for (unsigned i = nb + t; i < p2; i += kHT) bin_keys[i] = kKeyEmpty;
-    __syncthreads();
-    block_sort(bin_keys, p2);
     need = min(need, nb);
-    for (unsigned i = t; i < need && direct + i < (unsigned)kHMaxShort; i += kHT)
-        short_rows[direct + i] = (int)key_row(bin_keys[i]);
-    __syncthreads();
+    if (need > 0) {
+        const u64 cstar = block_kth_key<kHT>(bin_keys, nb, need, lo, shift, hsm, res, tmp);
+        if (t == 0) res[0] = direct;
+        __syncthreads();
+        for (unsigned i = t; i < nb; i += kHT) {
+            const u64 key = bin_keys[i];
+            if (key <= cstar) {
+                const unsigned pos = atomicAdd(&res[0], 1u);
+                if (pos < (unsigned)kHMaxShort) short_rows[pos] = (int)key_row(key);
+            }
+        }
+        __syncthreads();
+    }
     const int total = (int)min(direct + need, (unsigned)kHMaxShort);
     const float* q = p.Q + (size_t)f * p.D;
     u64 L = kKeyEmpty, thr = kKeyEmpty;
@@ -289,45 +275,84 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
 
     // ------------------------------------------------ B: boundary bin per frame, collect
     const bool take_all = p.n <= p.S;
-    for (int f = 0; f < nf; ++f) {
+    if (warp < nf) {
+        const int f = warp;
         if (take_all) {
-            if (t == 0) {
+            if (lane == 0) {
                 *reinterpret_cast<u64*>(&fr[f * 8 + 0]) = ~0ull;
                 *reinterpret_cast<u64*>(&fr[f * 8 + 2]) = ~0ull;
                 fr[f * 8 + 4] = 0u;
             }
-            continue;
-        }
-        for (int i = t; i < kBins; i += kHT) hsm[i] = __ldcg(p.hist + (size_t)f * kBins + i);
-        __syncthreads();
-        find_bin<kHT>(hsm, (unsigned)p.S, res, tmp);
-        if (t == 0) {
-            const u64 lo = (u64)res[0] << 52;
-            *reinterpret_cast<u64*>(&fr[f * 8 + 0]) = lo;
-            *reinterpret_cast<u64*>(&fr[f * 8 + 2]) = lo + (1ull << 52);
-            fr[f * 8 + 4] = res[2] > (unsigned)kHBinCap ? 1u : 0u;
-            if (blockIdx.x == 0) {
-                p.ctl[f * kHCtl + cRefine] = fr[f * 8 + 4];
-                p.ctl[f * kHCtl + cNeed] = (unsigned)p.S - res[1];
+        } else {
+            const uint3 b = warp_find_bin(p.hist + (size_t)f * kBins, (unsigned)p.S, lane);
+            if (lane == 0) {
+                const u64 lo = (u64)b.x << 52;
+                *reinterpret_cast<u64*>(&fr[f * 8 + 0]) = lo;
+                *reinterpret_cast<u64*>(&fr[f * 8 + 2]) = lo + (1ull << 52);
+                fr[f * 8 + 4] = b.z > (unsigned)kHBinCap ? 1u : 0u;
+                if (blockIdx.x == 0) {
+                    p.ctl[f * kHCtl + cRefine] = fr[f * 8 + 4];
+                    p.ctl[f * kHCtl + cNeed] = (unsigned)p.S - b.y;
+                }
             }
         }
-        __syncthreads();
     }
     __syncthreads();
-    for (int64_t base = r0; base < r1; base += kHT) {
-        const int64_t row = base + t;
-        const bool valid = row < r1;
-        for (int f = 0; f < nf; ++f) {
-            if (fr[f * 8 + 4]) continue;  // refined in phase D
-            const u64 lo = *reinterpret_cast<const u64*>(&fr[f * 8 + 0]);
-            const u64 hi = *reinterpret_cast<const u64*>(&fr[f * 8 + 2]);
-            const u64 key = valid ? coarse_key(p.dcbuf + (size_t)f * p.n, row) : kKeyEmpty;
-            const bool d = valid && (take_all || key < lo);
-            const bool b = valid && !d && key < hi;
-            warp_append(d, &p.ctl[f * kHCtl + cDirect], kHMaxShort, p.direct + (size_t)f * kHMaxShort, nullptr, row,
-                        0, lane);
-            warp_append(b, &p.ctl[f * kHCtl + cInBin], kHBinCap, nullptr, p.bins + (size_t)f * kHBinCap, row, key,
-                        lane);
+    {
+        // Appends are counted per warp, summed per CTA, and placed with one
+        // global atomic per (frame, list) and chunk of kHT rows.
+        unsigned* wcnt = reinterpret_cast<unsigned*>(region);  // [2 nf][kHW] counts, then bases
+        const unsigned below = (1u << lane) - 1u;
+        for (int64_t base = r0; base < r1; base += kHT) {
+            const int64_t row = base + t;
+            const bool valid = row < r1;
+            unsigned rank[16];
+            u64 key[8];
+#pragma unroll
+            for (int f = 0; f < 8; ++f) {
+                bool d = false, b = false;
+                key[f] = kKeyEmpty;
+                if (f < nf && !fr[f * 8 + 4]) {
+                    const u64 lo = *reinterpret_cast<const u64*>(&fr[f * 8 + 0]);
+                    const u64 hi = *reinterpret_cast<const u64*>(&fr[f * 8 + 2]);
+                    key[f] = valid ? coarse_key(p.dcbuf + (size_t)f * p.n, row) : kKeyEmpty;
+                    d = valid && (take_all || key[f] < lo);
+                    b = valid && !d && key[f] < hi;
+                }
+                const unsigned md = __ballot_sync(kFull, d), mb = __ballot_sync(kFull, b);
+                rank[2 * f] = d ? __popc(md & below) : ~0u;
+                rank[2 * f + 1] = b ? __popc(mb & below) : ~0u;
+                if (lane == 0 && f < nf) {
+                    wcnt[(2 * f) * kHW + warp] = __popc(md);
+                    wcnt[(2 * f + 1) * kHW + warp] = __popc(mb);
+                }
+            }
+            __syncthreads();
+            if (t < 2 * nf) {
+                unsigned tot = 0;
+                for (int w = 0; w < kHW; ++w) tot += wcnt[t * kHW + w];
+                unsigned at = tot ? atomicAdd(&p.ctl[(t / 2) * kHCtl + ((t & 1) ? cInBin : cDirect)], tot) : 0u;
+                for (int w = 0; w < kHW; ++w) {
+                    const unsigned c = wcnt[t * kHW + w];
+                    wcnt[t * kHW + w] = at;
+                    at += c;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int f = 0; f < 8; ++f) {
+                if (f < nf) {
+                    if (rank[2 * f] != ~0u) {
+                        const unsigned pos = wcnt[(2 * f) * kHW + warp] + rank[2 * f];
+                        if (pos < (unsigned)kHMaxShort) p.direct[(size_t)f * kHMaxShort + pos] = (int)row;
+                    }
+                    if (rank[2 * f + 1] != ~0u) {
+                        const unsigned pos = wcnt[(2 * f + 1) * kHW + warp] + rank[2 * f + 1];
+                        if (pos < (unsigned)kHBinCap) p.bins[(size_t)f * kHBinCap + pos] = key[f];
+                    }
+                }
+            }
+            __syncthreads();
         }
     }
     if (!grid_sync(p.bar, abort_sm, p.err)) return;
@@ -372,13 +397,14 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
             const unsigned cd = min(__ldcg(&p.ctl[f * kHCtl + cDirect]), (unsigned)kHMaxShort);
             const unsigned nb = min(__ldcg(&p.ctl[f * kHCtl + cInBin]), (unsigned)kHBinCap);
             const unsigned need = take_all ? 0u : min(__ldcg(&p.ctl[f * kHCtl + cNeed]), nb);
-            u64* sk = reinterpret_cast<u64*>(region);  // kHBinCap
-            unsigned p2 = 1;
-            while (p2 < nb) p2 <<= 1;
-            for (unsigned i = t; i < p2; i += kHT) sk[i] = i < nb ? __ldcg(p.bins + (size_t)f * kHBinCap + i) : kKeyEmpty;
+            u64* sk = reinterpret_cast<u64*>(region);                   // kHBinCap
+            unsigned* hs = reinterpret_cast<unsigned*>(sk + kHBinCap);  // kBins
+            for (unsigned i = t; i < nb; i += kHT) sk[i] = __ldcg(p.bins + (size_t)f * kHBinCap + i);
             __syncthreads();
-            block_sort(sk, p2);
-            const u64 cstar = need > 0 ? sk[need - 1] : 0ull;  // last boundary key inside the shortlist
+            // last boundary key inside the shortlist
+            const u64 cstar =
+                need > 0 ? block_kth_key<kHT>(sk, nb, need, *reinterpret_cast<const u64*>(&fr[f * 8 + 0]), 52, hs, res, tmp)
+                         : 0ull;
             u64 L = kKeyEmpty, thr = kKeyEmpty;
             for (unsigned base = 0; base < cd + nb; base += kHT) {
                 const unsigned i = base + t;

@@ -14,6 +14,7 @@
 constexpr int kSnPad = 256;
 constexpr int kSampleStride = 64;     // pilot sample: every 64th row
 constexpr int kSampleMinRows = 4096;  // sample only databases of at least 64 x 4096 rows
+constexpr int64_t kPilotMinRows = 65536;  // exhaustive-scan pilot sample for databases of at least this many rows
 
 struct lhr_db {
     int device = 0;
@@ -59,6 +60,15 @@ struct lhr_db {
     void* Xb_s = nullptr; float2* snb_s = nullptr;
     void* X8_s = nullptr; float2* sn8_s = nullptr;
 
+    // FP32 pilot sample of the exhaustive scan: internal rows 0, 64, 128, ...
+    // (n_pilot rows) and the subspace of each. A frame's k-th distance over the
+    // sample bounds its k-th over the whole database from above, so the full
+    // scan starts with (a bound close to) it instead of +inf. Absent below
+    // kPilotMinRows.
+    int64_t n_pilot = 0;
+    float* Xp = nullptr;
+    int32_t* sub_p = nullptr;  // n_pilot: subspace of each sample row
+
     int32_t* err = nullptr;  // device error word (lhr_db_error)
 };
 
@@ -88,9 +98,11 @@ struct ProfScope {
 };
 
 // Exhaustive FP32 scan + fused top-k (scan.cu).
-size_t scan_scratch_bytes(const lhr_db* db, int nq, int k);
+// `pilot`: seed the scan's thresholds from the pilot sample when the database
+// has one (same results, fewer exact recomputes; more scratch).
+size_t scan_scratch_bytes(const lhr_db* db, int nq, int k, bool pilot);
 cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t* idx, float* dist,
-                        void* scratch, cudaStream_t stream);
+                        void* scratch, bool pilot, cudaStream_t stream);
 
 struct AggArgs;
 
@@ -141,5 +153,6 @@ cudaError_t launch_gather_rows(const float* src, const int32_t* perm, int64_t n,
                                cudaStream_t stream);
 cudaError_t launch_tiles(const double* xy, int64_t n, double t, int32_t* tile, int32_t* flag, cudaStream_t stream);
 cudaError_t launch_norms(const lhr_db* db, unsigned* max_bits, cudaStream_t stream);
+cudaError_t launch_pilot_sample(const lhr_db* db, cudaStream_t stream);
 
 }  // namespace lhr

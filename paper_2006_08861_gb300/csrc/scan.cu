@@ -9,7 +9,7 @@
 //     contiguous range of one subspace; the chunk table is built with the
 //     database.
 //   * A producer thread streams the chunk through shared memory with 1-D bulk
-//     copies (cp.async.bulk, 8 rows per stage) into an mbarrier ring; consumer
+//     copies (cp.async.bulk, 16 rows per stage) into an mbarrier ring; consumer
 //     warp w owns the stages s with s % warps == w, so its parity waits always
 //     see consecutive phases.
 //   * Filter: lanes split the feature dimensions (float4 chunks,
@@ -35,16 +35,18 @@
 //     final lists. One launch per call; the distance matrix never leaves the SM.
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 
 #include "common.cuh"
 #include "internal.h"
+#include "select.cuh"
 
 namespace lhr {
 namespace {
 
-constexpr int kRPS = 8;            // rows per stage
+constexpr int kRPS = 16;           // rows per stage
 constexpr int kMaxWarps = 12;      // consumer warps per CTA
 constexpr int kMaxSmem = 227 * 1024;
 
@@ -61,6 +63,7 @@ struct ScanParams {
     int nq;
     int k;
     int stages;
+    const unsigned* bmin;  // nullable: [nq][n_sub][kPilotBuckets] pilot bucket minima (float bits; ~0u = empty)
     float xmax;          // sqrt(max ||x||^2)
     float margin_scale;  // 2 (gamma_D + 3u)
     u64* partial;        // [qblock][QB][nchunks][k]
@@ -77,6 +80,42 @@ struct ScanConfig {
 };
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+constexpr int kPilotBuckets = 128;
+
+// Pilot bound of frame qi in subspace `sub`, by one warp. The pilot sample's
+// rows were dealt into 128 buckets (row j -> j mod 128) and each bucket keeps
+// its minimum distance; the k-th smallest non-empty bucket minimum (ties by
+// bucket) is reached by k distinct database rows, so it bounds the frame's
+// k-th distance from above, and it seldom exceeds the sample's own k-th (the
+// best rows rarely share a bucket). Any k consecutive rows fill k buckets.
+// The bound is widened by 2^-12 relative against a difference in the last
+// bits between the two kernels' distances, and lowers *thr (float bits).
+__device__ void pilot_bound(const ScanParams& p, int qi, int sub, int lane, unsigned* thr) {
+    const unsigned* bm = p.bmin + ((size_t)qi * p.n_sub + sub) * kPilotBuckets;
+    unsigned v[4], rank[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __ldcg(bm + lane + 32 * i);
+    for (int src = 0; src < 32; ++src) {
+#pragma unroll
+        for (int i2 = 0; i2 < 4; ++i2) {
+            const unsigned u = __shfl_sync(kFull, v[i2], src);
+            const int ub = src + 32 * i2;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) rank[i] += (u < v[i] || (u == v[i] && ub < lane + 32 * i)) ? 1u : 0u;
+        }
+    }
+    unsigned b = 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if (v[i] < 0x7f800000u && rank[i] == (unsigned)p.k - 1u) b = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = min(b, __shfl_xor_sync(kFull, b, o));
+    if (lane == 0 && b < 0x7f800000u) {
+        const float w = __uint_as_float(b) * (1.0f + 1.0f / 4096.0f);
+        atomicMin(thr, __float_as_uint(w));
+    }
+}
 
 template <int QB, int CPL>
 __global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(const ScanParams p) {
@@ -179,6 +218,8 @@ __global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(cons
             for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
             if ((lane % QB) == q) qn = a;
         }
+        if (p.bmin != nullptr)
+            for (int f = warp; f < QB && qblock * QB + f < p.nq; f += warps) pilot_bound(p, qblock * QB + f, ch.z, lane, &thr_sh[f]);
         const int myq = lane % QB;
         const bool q_valid = (qblock * QB + myq) < p.nq;
         const float rad = p.xmax + sqrtf(qn);
@@ -328,7 +369,7 @@ __global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(cons
     // ---------------------------------------------------- last CTA: final lists
     // G warps share each (frame, subspace) pair: each merges a share of the
     // pair's chunk lists, then the pair's first warp merges the G results.
-    const int pairs = QB * p.n_sub;
+    const int pairs = min(QB, p.nq - qblock * QB) * p.n_sub;  // (frame, subspace) pairs of real frames
     const int G = max(1, nwarps / pairs);
     const int per_round = nwarps / G;
     u64* mlist = lists;  // free now: [nwarps][32]
@@ -399,6 +440,10 @@ __global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(cons
     if (threadIdx.x == 0) p.counters[qblock] = 0u;
 }
 
+// Launch shape. With few frames per block (QB <= 4) the warps are
+// latency-bound, so each keeps two stages in flight, even at half the warps;
+// otherwise (or when that leaves fewer than 6 warps) the most warps that fit
+// win, down to one stage each.
 ScanConfig choose_config(const lhr_db* db, int nq) {
     ScanConfig c{};
     const int d4 = db->dim / 4;
@@ -409,32 +454,94 @@ ScanConfig choose_config(const lhr_db* db, int nq) {
     c.qb = qb;
     const size_t stage_bytes = (size_t)kRPS * db->dim * sizeof(float);
     const size_t qs_bytes = (size_t)qb * db->dim * sizeof(float);
-    for (int w = kMaxWarps; w >= 1; --w) {
-        const size_t lists = (size_t)w * qb * 32 * sizeof(u64);
-        for (int per = 3; per >= 2; --per) {
-            const int ns = per * w;
-            const size_t smem = ns * stage_bytes + qs_bytes + 2 * ns * sizeof(u64) + lists + qb * sizeof(unsigned) + 16;
-            if (smem <= (size_t)kMaxSmem - 1024) {
-                c.warps = w;
-                c.stages = ns;
-                c.smem = smem;
-                return c;
-            }
-        }
+    auto smem_for = [&](int w, int per) {
+        const int ns = per * w;
+        return ns * stage_bytes + qs_bytes + 2 * ns * sizeof(u64) + (size_t)w * qb * 32 * sizeof(u64) +
+               qb * sizeof(unsigned) + 16;
+    };
+    const size_t cap = (size_t)kMaxSmem - 1024;
+    for (int pass = qb <= 4 ? 0 : 1; pass < 2; ++pass) {
+        const int w_min = pass == 0 ? 6 : 1, per_min = pass == 0 ? 2 : 1;
+        for (int w = kMaxWarps; w >= w_min; --w)
+            for (int per = 3; per >= per_min; --per)
+                if (smem_for(w, per) <= cap) {
+                    c.warps = w;
+                    c.stages = per * w;
+                    c.smem = smem_for(w, per);
+                    return c;
+                }
     }
     c.warps = 1;
-    c.stages = 2;
-    c.smem = 2 * stage_bytes + qs_bytes + 4 * sizeof(u64) + (size_t)qb * 32 * sizeof(u64) + qb * sizeof(unsigned) + 16;
+    c.stages = 1;
+    c.smem = smem_for(1, 1);
     return c;
 }
 
+// ------------------------------------------------------------------ pilot
+// Distances of every pilot-sample row to every frame (one warp per row, up to
+// 8 frames per reduction round; the same direct-form FP32 arithmetic as the
+// scan's exact step), folded into the bucket minima read by pilot_bound:
+// bmin[(f * n_sub + sub_p[j]) * 128 + j % 128] (float bits, preset to ~0u).
+template <int CPL>
+__global__ void __launch_bounds__(256) pilot_kernel(const float* Xp, const int32_t* sub_p, int64_t np, int D,
+                                                    const float* Q, int nq, int n_sub, unsigned* bmin) {
+    const int lane = threadIdx.x % 32;
+    const int D4 = D / 4;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
+    for (int64_t r = gw; r < np; r += nw) {
+        float4 x[CPL];
+        const float4* xr = reinterpret_cast<const float4*>(Xp + r * D);
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            const int c = lane + 32 * j;
+            x[j] = c < D4 ? __ldg(xr + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const int sub = __ldg(sub_p + r);
+        for (int f0 = 0; f0 < nq; f0 += 8) {
+            float de[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                float2 acc = f2(0.f, 0.f);
+                if (f0 + i < nq) {
+                    const float4* qr = reinterpret_cast<const float4*>(Q + (size_t)(f0 + i) * D);
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j) {
+                        const int c = lane + 32 * j;
+                        if (c < D4) {
+                            const float4 qv = __ldg(qr + c);
+                            const float2 d0 = __ffma2_rn(f2(x[j].x, x[j].y), f2(-1.f, -1.f), f2(qv.x, qv.y));
+                            const float2 d1 = __ffma2_rn(f2(x[j].z, x[j].w), f2(-1.f, -1.f), f2(qv.z, qv.w));
+                            acc = __ffma2_rn(d0, d0, acc);
+                            acc = __ffma2_rn(d1, d1, acc);
+                        }
+                    }
+                }
+                de[i] = acc.x + acc.y;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) de[i] += __shfl_xor_sync(kFull, de[i], o);
+            }
+            if (lane < 8 && f0 + lane < nq) {
+                float v = de[0];
+#pragma unroll
+                for (int i = 1; i < 8; ++i) v = lane == i ? de[i] : v;
+                atomicMin(bmin + ((size_t)(f0 + lane) * n_sub + sub) * kPilotBuckets + (r % kPilotBuckets),
+                          __float_as_uint(v));
+            }
+        }
+    }
+}
+
 template <int QB, int CPL>
-cudaError_t launch_t(const ScanConfig& c, const ScanParams& p, int nqb, cudaStream_t stream) {
+cudaError_t launch_t(const ScanConfig& c, const ScanParams& p, int nqb, const char* label, cudaStream_t stream) {
     auto kern = scan_topk_kernel<QB, CPL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
     if (e != cudaSuccess) return e;
     dim3 grid(p.nchunks, nqb);
-    ProfScope ps("scan_topk_kernel", stream);
+    ProfScope ps(label, stream);
     kern<<<grid, (c.warps + 1) * 32, c.smem, stream>>>(p);
     return cudaGetLastError();
 }
@@ -443,37 +550,74 @@ cudaError_t launch_t(const ScanConfig& c, const ScanParams& p, int nqb, cudaStre
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-size_t scan_scratch_bytes(const lhr_db* db, int nq, int k) {
-    const ScanConfig c = choose_config(db, nq);
+namespace {
+
+// The rows one scan pass streams: the database, or its pilot sample.
+struct ScanSrc {
+    const float* X;
+    const float* xnorm;
+    const int4* chunks;
+    int nchunks;
+    const int32_t* chunk_off;
+    const int32_t* perm;  // nullable
+};
+
+size_t pass_bytes(const ScanConfig& c, int nchunks, int n_sub, int nq, int k) {
     const size_t nqb = (nq + c.qb - 1) / c.qb;
-    return align256(nqb * c.qb * (size_t)db->nchunks * k * sizeof(u64)) + align256(nqb * sizeof(unsigned)) +
-           align256(nqb * c.qb * (size_t)db->n_sub * sizeof(unsigned));
+    return align256(nqb * c.qb * (size_t)nchunks * k * sizeof(u64)) + align256(nqb * sizeof(unsigned)) +
+           align256(nqb * c.qb * (size_t)n_sub * sizeof(unsigned));
 }
 
-cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t* idx, float* dist, void* scratch,
-                        cudaStream_t stream) {
+constexpr int kPilotMaxFrames = 256;  // larger requests scan without the pilot
+
+bool use_pilot(const lhr_db* db, int nq) { return db->Xp != nullptr && nq <= kPilotMaxFrames; }
+
+size_t pilot_bytes(const lhr_db* db, int nq) { return align256((size_t)nq * db->n_sub * kPilotBuckets * sizeof(unsigned)); }
+
+cudaError_t launch_pilot(const lhr_db* db, const float* q, int nq, void* scratch, unsigned** bmin_out,
+                         cudaStream_t stream) {
+    unsigned* bmin = reinterpret_cast<unsigned*>(scratch);
+    cudaError_t e = cudaMemsetAsync(bmin, 0xff, (size_t)nq * db->n_sub * kPilotBuckets * sizeof(unsigned), stream);
+    if (e != cudaSuccess) return e;
+    const int d4 = db->dim / 4;
+    const int cpl = d4 <= 32 ? 1 : (d4 <= 64 ? 2 : 4);
+    const int grid = (int)std::min<int64_t>((db->n_pilot + 7) / 8, (int64_t)db->sms * 32);
+    {
+        ProfScope ps("scan_pilot", stream);
+        if (cpl == 1) pilot_kernel<1><<<grid, 256, 0, stream>>>(db->Xp, db->sub_p, db->n_pilot, db->dim, q, nq, db->n_sub, bmin);
+        else if (cpl == 2) pilot_kernel<2><<<grid, 256, 0, stream>>>(db->Xp, db->sub_p, db->n_pilot, db->dim, q, nq, db->n_sub, bmin);
+        else pilot_kernel<4><<<grid, 256, 0, stream>>>(db->Xp, db->sub_p, db->n_pilot, db->dim, q, nq, db->n_sub, bmin);
+    }
+    *bmin_out = bmin;
+    return cudaGetLastError();
+}
+
+cudaError_t scan_pass(const lhr_db* db, const ScanSrc& src, const char* label, const float* q, int nq, int k,
+                      const unsigned* bmin, int64_t* idx, float* dist, void* scratch, cudaStream_t stream) {
     const ScanConfig c = choose_config(db, nq);
     const int nqb = (nq + c.qb - 1) / c.qb;
     ScanParams p{};
-    p.X = db->X;
-    p.xnorm = db->xnorm;
+    p.X = src.X;
+    p.xnorm = src.xnorm;
     p.D = db->dim;
-    p.chunks = db->chunks;
-    p.nchunks = db->nchunks;
-    p.chunk_off = db->chunk_off;
+    p.chunks = src.chunks;
+    p.nchunks = src.nchunks;
+    p.chunk_off = src.chunk_off;
     p.n_sub = db->n_sub;
-    p.perm = db->perm;
+    p.perm = src.perm;
     p.Q = q;
     p.nq = nq;
     p.k = k;
     p.stages = c.stages;
+    p.bmin = bmin;
     // 2 (gamma_D + 3u) with u = 2^-24 and gamma_D = D u / (1 - D u), slightly rounded up
     const double u = 1.0 / 16777216.0;
     const double gamma = db->dim * u / (1.0 - db->dim * u);
     p.margin_scale = (float)(2.0 * (gamma + 3.0 * u) * 1.0001);
+    // max ||x|| over the whole database bounds the sample's too
     p.xmax = (float)(sqrt((double)db->xnorm_max) * 1.0001);
     p.partial = reinterpret_cast<u64*>(scratch);
-    const size_t part_bytes = align256((size_t)nqb * c.qb * db->nchunks * k * sizeof(u64));
+    const size_t part_bytes = align256((size_t)nqb * c.qb * src.nchunks * k * sizeof(u64));
     p.counters = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(scratch) + part_bytes);
     p.gthr = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(scratch) + part_bytes +
                                          align256(nqb * sizeof(unsigned)));
@@ -485,14 +629,40 @@ cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t
     e = cudaMemsetAsync(p.gthr, 0xff, (size_t)nqb * c.qb * db->n_sub * sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
     switch (c.cpl * 100 + c.qb) {
-        case 104: return launch_t<4, 1>(c, p, nqb, stream);
-        case 108: return launch_t<8, 1>(c, p, nqb, stream);
-        case 116: return launch_t<16, 1>(c, p, nqb, stream);
-        case 204: return launch_t<4, 2>(c, p, nqb, stream);
-        case 208: return launch_t<8, 2>(c, p, nqb, stream);
-        case 404: return launch_t<4, 4>(c, p, nqb, stream);
+        case 104: return launch_t<4, 1>(c, p, nqb, label, stream);
+        case 108: return launch_t<8, 1>(c, p, nqb, label, stream);
+        case 116: return launch_t<16, 1>(c, p, nqb, label, stream);
+        case 204: return launch_t<4, 2>(c, p, nqb, label, stream);
+        case 208: return launch_t<8, 2>(c, p, nqb, label, stream);
+        case 404: return launch_t<4, 4>(c, p, nqb, label, stream);
         default: return cudaErrorInvalidConfiguration;
     }
+}
+
+}  // namespace
+
+size_t scan_scratch_bytes(const lhr_db* db, int nq, int k, bool pilot) {
+    const ScanConfig c = choose_config(db, nq);
+    const size_t main = pass_bytes(c, db->nchunks, db->n_sub, nq, k);
+    return pilot && use_pilot(db, nq) ? main + pilot_bytes(db, nq) : main;
+}
+
+// With a pilot sample (every 64th row): a bound on each frame's k-th distance
+// per subspace, taken from the sample (pilot_bound), seeds the full scan's
+// thresholds, so only rows that can still reach a top k are ever recomputed
+// and inserted. Every key of the final top k is <= that bound: the k sample
+// rows reaching it are database rows the full scan meets again.
+cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t* idx, float* dist, void* scratch,
+                        bool pilot, cudaStream_t stream) {
+    const ScanSrc full{db->X, db->xnorm, db->chunks, db->nchunks, db->chunk_off, db->perm};
+    unsigned* bmin = nullptr;
+    if (pilot && use_pilot(db, nq)) {
+        const ScanConfig c = choose_config(db, nq);
+        unsigned char* ps = reinterpret_cast<unsigned char*>(scratch) + pass_bytes(c, db->nchunks, db->n_sub, nq, k);
+        cudaError_t e = launch_pilot(db, q, nq, ps, &bmin, stream);
+        if (e != cudaSuccess) return e;
+    }
+    return scan_pass(db, full, "scan_topk_kernel", q, nq, k, bmin, idx, dist, scratch, stream);
 }
 
 }  // namespace lhr
@@ -539,7 +709,7 @@ extern "C" lhr_status lhr_query_static(const lhr_db* db, const float* q, int32_t
     if (reinterpret_cast<uintptr_t>(q) % 16) return fail(LHR_ERR_INVALID_ARG, "q must be 16-byte aligned");
     if (nq < 1) return fail(LHR_ERR_INVALID_ARG, "nq must be >= 1");
     if (k < 1 || k > 32) return fail(LHR_ERR_INVALID_ARG, "k must be in [1, 32]");
-    const size_t need = scan_scratch_bytes(db, nq, k);
+    const size_t need = scan_scratch_bytes(db, nq, k, false);
     if (need > kStaticScratchBytes)
         return fail(LHR_ERR_INVALID_ARG, "lhr_query_static: this request needs " + std::to_string(need) +
                                              " bytes of scratch, more than the fixed " +
@@ -552,7 +722,7 @@ extern "C" lhr_status lhr_query_static(const lhr_db* db, const float* q, int32_t
     void* scratch = nullptr;
     cudaError_t e = static_scratch_address(db->device, &scratch);
     if (e == cudaSuccess)
-        e = launch_scan(db, q, nq, k, idx, dist, scratch, reinterpret_cast<cudaStream_t>(cuda_stream));
+        e = launch_scan(db, q, nq, k, idx, dist, scratch, false, reinterpret_cast<cudaStream_t>(cuda_stream));
     if (prev != db->device) cudaSetDevice(prev);
     if (e != cudaSuccess) return cuda_fail(e, "lhr_query_static");
     return LHR_OK;

@@ -54,6 +54,88 @@ __device__ void find_bin(const unsigned* hsm, unsigned need, unsigned* out, unsi
     __syncthreads();
 }
 
+// The same search over a histogram in global memory, by one warp: lane l
+// holds bins [64 l, 64 l + 64) in registers (16 loads in flight per lane).
+// Returns (bin, keys below it, keys in it) on every lane; zeros when the
+// histogram holds fewer than `need` keys.
+__device__ __forceinline__ uint3 warp_find_bin(const unsigned* hist, unsigned need, int lane) {
+    static_assert(kBins == 64 * 32, "one lane per 64 bins");
+    const uint4* h4 = reinterpret_cast<const uint4*>(hist) + lane * 16;
+    uint4 v[16];
+    unsigned own = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        v[i] = __ldcg(h4 + i);
+        own += v[i].x + v[i].y + v[i].z + v[i].w;
+    }
+    unsigned s = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_up_sync(kFull, s, o);
+        if (lane >= o) s += u;
+    }
+    unsigned before = s - own;
+    const bool mine = before < need && need <= s;
+    uint3 out = make_uint3(0u, 0u, 0u);
+    if (mine) {
+#pragma unroll
+        for (int i = 0; i < 64; ++i) {
+            const uint4 q = v[i / 4];
+            const unsigned c = (i % 4) == 0 ? q.x : ((i % 4) == 1 ? q.y : ((i % 4) == 2 ? q.z : q.w));
+            if (before < need && need <= before + c) out = make_uint3((unsigned)(lane * 64 + i), before, c);
+            before += c;
+        }
+    }
+    const unsigned m = __ballot_sync(kFull, mine);
+    const int src = m ? __ffs(m) - 1 : 0;
+    out.x = __shfl_sync(kFull, out.x, src);
+    out.y = __shfl_sync(kFull, out.y, src);
+    out.z = __shfl_sync(kFull, out.z, src);
+    return out;
+}
+
+// The need-th smallest (1-based) of the nb distinct keys keys[0, nb) in shared
+// memory, all of which lie in [lo, lo + 2^shift): radix refinement on 11-bit
+// digits, one histogram pass per digit, until one key is left in the range.
+// `hsm` holds kBins words, `res` 4 and `tmp` THREADS / 32; every thread of the
+// block calls it and gets the key.
+template <int THREADS>
+__device__ u64 block_kth_key(const u64* keys, unsigned nb, unsigned need, u64 lo, int shift, unsigned* hsm,
+                             unsigned* res, unsigned* tmp) {
+    const int t = threadIdx.x;
+    for (;;) {
+        const int nshift = shift > 11 ? shift - 11 : 0;
+        const u64 hi = shift >= 64 ? ~0ull : lo + (1ull << shift) - 1ull;  // inclusive
+        const unsigned mask = (1u << (shift - nshift)) - 1u;
+        for (int i = t; i < kBins; i += THREADS) hsm[i] = 0u;
+        __syncthreads();
+        for (unsigned i = t; i < nb; i += THREADS) {
+            const u64 key = keys[i];
+            if (key >= lo && key <= hi) atomicAdd(&hsm[(unsigned)(key >> nshift) & mask], 1u);
+        }
+        __syncthreads();
+        find_bin<THREADS>(hsm, need, res, tmp);
+        lo += (u64)res[0] << nshift;
+        need -= res[1];
+        const unsigned in_bin = res[2];
+        shift = nshift;
+        if (shift == 0) return lo;
+        if (in_bin == 1u) break;
+    }
+    // one key left in [lo, lo + 2^shift)
+    const u64 hi = lo + (1ull << shift) - 1ull;
+    u64* found = reinterpret_cast<u64*>(hsm);
+    __syncthreads();
+    for (unsigned i = t; i < nb; i += THREADS) {
+        const u64 key = keys[i];
+        if (key >= lo && key <= hi) *found = key;
+    }
+    __syncthreads();
+    const u64 key = *found;
+    __syncthreads();
+    return key;
+}
+
 __device__ __forceinline__ u64 coarse_key(const float* dcf, int64_t row) {
     return ((u64)__float_as_uint(dcf[row]) << 32) | (u64)row;
 }

@@ -175,3 +175,55 @@ def test_two_million_rows_sampled(lhr):
     # most queries find their own row first (aliased copies sometimes win)
     assert np.mean(gi[:, 0, 0] == rows) >= 0.75
     h.close()
+
+
+# ------------------------------------------------------------------ pilot sample
+# Databases of >= 65,536 rows carry a pilot sample (every 64th row); its k-th
+# distances seed the scan's thresholds. Results must not change.
+def test_pilot_seeded_scan_matches_oracle(lhr):
+    rng = np.random.default_rng(41)
+    n, dim, nq, k = 70_001, 64, 9, 32
+    X = rng.standard_normal((n, dim)).astype(np.float32)
+    Q = (X[rng.integers(0, n, nq)] + 0.3 * rng.standard_normal((nq, dim))).astype(np.float32)
+    _, gi, gd = _run(lhr, X, Q, k)
+    _compare(X, Q, k, gi, gd)
+
+
+def test_pilot_with_subspaces_small_and_empty(lhr):
+    # subspace 1 holds fewer than k sample rows (its pilot bound is +inf),
+    # subspace 2 is empty, ids are shuffled
+    rng = np.random.default_rng(42)
+    n, dim, k = 90_000, 32, 20
+    X = rng.standard_normal((n, dim)).astype(np.float32)
+    sub = rng.choice([0, 1, 3], size=n, p=[0.6, 0.01, 0.39]).astype(np.int32)
+    Q = (X[rng.integers(0, n, 6)] + 0.2 * rng.standard_normal((6, dim))).astype(np.float32)
+    db, gi, gd = _run(lhr, X, Q, k, subspace=sub)
+    assert db.n_subspaces == 4 and np.all(gi[:, 2] == -1)
+    _compare(X, Q, k, gi, gd, subspace=sub, n_sub=4)
+
+
+def test_pilot_exact_ties(lhr):
+    # integer rows with many exact duplicates: the pilot bound lands on tied
+    # distances; order must still equal the oracle's bit for bit
+    rng = np.random.default_rng(43)
+    base = rng.integers(-2, 3, size=(60, 16)).astype(np.float32)
+    X = base[rng.integers(0, 60, size=80_000)]
+    Q = rng.integers(-2, 3, size=(5, 16)).astype(np.float32)
+    _, gi, gd = _run(lhr, X, Q, 30)
+    o_idx, o_dist = oret.exhaustive_topk(Q, X, 30)
+    assert np.array_equal(gi, o_idx)
+    assert np.array_equal(gd.astype(np.float64), o_dist)
+
+
+def test_pilot_and_plain_scan_agree(lhr):
+    # lhr_query seeds from the pilot; lhr_query_static never does
+    rng = np.random.default_rng(44)
+    X = rng.standard_normal((100_000, 128)).astype(np.float32)
+    db = lhr.lhr_build_db(X, np.zeros((100_000, 2)))
+    q = torch.from_numpy((X[:7] + 0.1 * rng.standard_normal((7, 128))).astype(np.float32)).cuda()
+    i1, d1 = lhr.lhr_query(db, q, 24)
+    out_i = torch.empty((7, 1, 24), dtype=torch.int64, device="cuda")
+    out_d = torch.empty((7, 1, 24), dtype=torch.float32, device="cuda")
+    lhr.lhr_query_static(db, q, 24, (out_i, out_d))
+    torch.cuda.synchronize()
+    assert torch.equal(i1, out_i) and torch.equal(d1, out_d)
