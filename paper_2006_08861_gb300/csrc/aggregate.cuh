@@ -52,7 +52,7 @@ __device__ inline void aggregate_warp(const AggParams& p, int w, long long b0, l
     int C = 0;
     for (long long base = 0; base < total; base += 32) {
         const long long i = base + lane;
-        const int64_t r = i < total ? a.idx[b0 + i] : -1;
+        const int64_t r = i < total ? __ldcg(a.idx + b0 + i) : -1;  // may come from another CTA of the launch
         const bool bad = r >= p.n;
         if (bad) record_error(p.err, kErrInvalidArg);
         const bool take = r >= 0 && !bad;
@@ -60,7 +60,7 @@ __device__ inline void aggregate_warp(const AggParams& p, int w, long long b0, l
         const int pos = C + __popc(m & below);
         if (take) {
             cand_rows[pos] = (int)r;
-            cand_d[pos] = a.dist != nullptr ? a.dist[b0 + i] : 0.f;
+            cand_d[pos] = a.dist != nullptr ? __ldcg(a.dist + b0 + i) : 0.f;
             keys[pos] = tile_key(p.tile[2 * r], p.tile[2 * r + 1]);
         }
         C += __popc(m);

@@ -3,23 +3,25 @@
 // launch of one CTA per SM. The steps are those of coarse.cu and aggregate.cu
 // (same keys, same tie rules, same tests); only the scheduling differs: a
 // building-scale request is a few microseconds of work, so instead of four
-// kernels with mostly idle SMs the whole GPU walks through five phases
-// separated by grid barriers:
+// kernels with mostly idle SMs the whole GPU walks through four phases:
 //   A  every CTA scores its slice of rows on the coarse prefix for every frame
-//      (packed FP32 FMAs), writes the distances to scratch and adds the
-//      key's top 11-bit digit to per-frame histograms;
-//   B  every CTA locates, per frame, the histogram bin holding the S-th key
-//      and appends its rows below that bin (direct list) and inside it
-//      (boundary list) with warp-aggregated atomics;
-//   C  all warps of the grid re-score every collected row on the full
-//      feature, one row per warp;
-//   D  CTA f cuts frame f's boundary list at its need-th coarse key (exactly
-//      S rows in all) and keeps the top k of the shortlist's full keys; a
+//      (packed FP32 FMAs), writes the distances to scratch and counts them in
+//      per-frame histograms of a 1/32-octave digit of the distance;
+//   -- grid barrier
+//   B  every CTA locates, per frame, the bin holding the S-th key (one warp per
+//      frame), takes its rows below that bin (direct) and inside it
+//      (boundary), re-scores each on the full feature (one warp per row) and
+//      appends the keys with one global atomic per (frame, list) and chunk;
+//   -- grid barrier
+//   C  CTA f cuts frame f's boundary list at its need-th coarse key (radix
+//      select: exactly S rows in all) and selects the top k of the
+//      shortlist's full keys (radix select, then one warp sorts the k); a
 //      frame whose boundary bin overflowed is refined and ranked by CTA f
-//      alone, over the frame's distances;
-//   E  CTA w runs Algorithm 2 on window w's candidates (one warp).
-// The grid barrier is a global counter and generation word; waits give up
-// after kWaitLimitNs and record LHR_ERR_TIMEOUT.
+//      alone, over the frame's distances; CTAs with no frame leave;
+//   -- a done counter (only the window CTAs wait for it)
+//   D  CTA w runs Algorithm 2 on window w's candidates (one warp).
+// The grid barrier is a global counter and generation word; every wait gives
+// up after kWaitLimitNs and records LHR_ERR_TIMEOUT.
 #include "aggregate.cuh"
 #include "common.cuh"
 #include "internal.h"
@@ -34,9 +36,23 @@ constexpr int kHT = 512;  // threads per CTA
 constexpr int kHW = kHT / 32;
 constexpr int kHBinCap = 4096;
 constexpr int kHMaxShort = 4096;
-constexpr int kHRegion = 64 * 1024;  // shared region reused by every phase
+constexpr int kHRegion = 80 * 1024;  // shared region reused by every phase
 constexpr int kHCtl = 8;             // control words per frame
 enum { cDirect = 0, cInBin = 1, cRefine = 2, cNeed = 3 };
+
+// Coarse digit of a distance d >= 0: 8 exponent bits and the top 5 mantissa
+// bits, i.e. 1/32-octave bins, over 2^-32 .. 2^32; smaller and larger values
+// share the end bins. It is a monotone function of the key's top bits
+// (key >> 50), so each bin is one key range (bin_range).
+constexpr unsigned kDigitBase = (127u - 32u) << 5;
+__device__ __forceinline__ unsigned coarse_digit(float d) {
+    const unsigned v = __float_as_uint(d) >> 18;
+    return v <= kDigitBase ? 0u : min(v - kDigitBase, (unsigned)kBins - 1u);
+}
+__device__ __forceinline__ void bin_range(unsigned b, u64& lo, u64& hi) {  // keys of bin b: [lo, hi]
+    lo = b == 0 ? 0ull : (u64)(kDigitBase + b) << 50;
+    hi = b == (unsigned)kBins - 1u ? ~0ull : ((u64)(kDigitBase + b + 1u) << 50) - 1ull;
+}
 
 struct HierParams {
     const float* Xc;
@@ -50,11 +66,10 @@ struct HierParams {
     float* dcbuf;     // nf x n coarse distances
     unsigned* hist;   // nf x kBins (zeroed)
     unsigned* ctl;    // nf x kHCtl (zeroed)
-    unsigned* bar;    // grid barrier: count, generation (zeroed)
-    int* direct;      // nf x kHMaxShort rows below the boundary bin
-    u64* bins;        // nf x kHBinCap coarse keys in the boundary bin
+    unsigned* bar;    // grid barrier count, generation; frames done (zeroed)
+    u64* bins;        // nf x kHBinCap coarse keys of the boundary rows
+    u64* fkb;         // nf x kHBinCap their full keys (same slots)
     u64* fkd;         // nf x kHMaxShort full keys of the direct rows
-    u64* fkb;         // nf x kHBinCap full keys of the boundary rows
     int64_t* idx;     // nf x k
     float* dist;
     agg::AggParams ap;  // windows over the frames (per_frame = k), ap.a.nw of them; nw = 0: none
@@ -114,63 +129,93 @@ __device__ __forceinline__ float warp_dist(const float* X, int D, const float* q
     return d;
 }
 
-// Warp lists in wl[kHW][32] -> frame f's final top k (warp 0 writes).
-__device__ void finish_frame(const HierParams& p, int f, u64 L, u64* wl) {
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    wl[warp * 32 + lane] = L;
+// Writes frame f's final top k: the keys of fk[0, total) that are <= kth
+// (at most 32 of them, distinct) are gathered, sorted by warp 0 and written.
+__device__ void write_topk(const HierParams& p, int f, const u64* fk, unsigned total, u64 kth, u64* outk,
+                           unsigned* res) {
+    const int t = threadIdx.x, lane = t % 32;
+    if (t == 0) res[3] = 0u;
     __syncthreads();
-    if (warp == 0) {
-        u64 M = kKeyEmpty;
-        list_merge_keys<false>(M, wl, kHW * 32, p.k, lane);
+    for (unsigned i = t; i < total; i += kHT) {
+        const u64 key = fk[i];
+        if (key <= kth) {
+            const unsigned pos = atomicAdd(&res[3], 1u);
+            if (pos < 32u) outk[pos] = key;
+        }
+    }
+    __syncthreads();
+    if (t < 32) {
+        const unsigned cnt = min(res[3], 32u);
+        u64 v = (unsigned)lane < cnt ? outk[lane] : kKeyEmpty;
+#pragma unroll
+        for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                const u64 o = __shfl_xor_sync(kFull, v, stride);
+                const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
+                v = keep_min ? (o < v ? o : v) : (o > v ? o : v);
+            }
+        }
         if (lane < p.k) {
             const size_t o = (size_t)f * p.k + lane;
-            if (M == kKeyEmpty) {
+            if (v == kKeyEmpty) {
                 p.idx[o] = -1;
                 p.dist[o] = __int_as_float(0x7f800000);
             } else {
-                p.idx[o] = (int64_t)key_row(M);
-                p.dist[o] = key_dist(M);
+                p.idx[o] = (int64_t)key_row(v);
+                p.dist[o] = key_dist(v);
             }
         }
     }
     __syncthreads();
 }
 
+// Top k of fk[0, total) (distinct keys) written as frame f's result.
+__device__ void select_topk(const HierParams& p, int f, const u64* fk, unsigned total, unsigned* hs, u64* outk,
+                            unsigned* res, unsigned* tmp) {
+    const u64 kth = total > (unsigned)p.k ? block_kth_key<kHT>(fk, total, (unsigned)p.k, 0ull, ~0ull, hs, res, tmp)
+                                          : ~0ull;
+    write_topk(p, f, fk, total, kth, outk, res);
+}
+
 // Frame f whose boundary bin overflowed: refine the radix select over the
-// frame's coarse distances, collect the S rows, rank them (this CTA alone).
+// frame's coarse distances, collect the S rows, re-score and rank them (this
+// CTA alone).
 template <int CPL>
-__device__ void refine_frame(const HierParams& p, int f, unsigned char* region, u64* wl, unsigned* res,
-                             unsigned* tmp) {
+__device__ void refine_frame(const HierParams& p, int f, unsigned char* region, unsigned* res, unsigned* tmp) {
     const int t = threadIdx.x, warp = t / 32, lane = t % 32;
     unsigned* hsm = reinterpret_cast<unsigned*>(region);               // kBins
     u64* bin_keys = reinterpret_cast<u64*>(hsm + kBins);                // kHBinCap
-    int* short_rows = reinterpret_cast<int*>(bin_keys + kHBinCap);      // kHMaxShort
+    u64* fk = bin_keys + kHBinCap;                                      // kHMaxShort: rows, then full keys
+    u64* outk = fk + kHMaxShort;                                        // 32
     const float* dcf = p.dcbuf + (size_t)f * p.n;
     unsigned need = (unsigned)p.S;
     for (int i = t; i < kBins; i += kHT) hsm[i] = __ldcg(p.hist + (size_t)f * kBins + i);
     __syncthreads();
     find_bin<kHT>(hsm, need, res, tmp);
-    int shift = 52;
-    u64 lo = (u64)res[0] << shift, hi = lo + (1ull << shift);
+    u64 lo, hi;
+    bin_range(res[0], lo, hi);
     need -= res[1];
     unsigned in_bin = res[2];
-    while (in_bin > (unsigned)kHBinCap && shift > 0) {
-        const int nshift = shift >= 11 ? shift - 11 : 0;
-        const int dbits = shift - nshift;
+    while (in_bin > (unsigned)kHBinCap && hi > lo) {
+        const u64 span = hi - lo;
+        const int bits = 64 - __clzll((long long)span);
+        const int shift = bits > 11 ? bits - 11 : 0;
         __syncthreads();
         for (int i = t; i < kBins; i += kHT) hsm[i] = 0u;
         __syncthreads();
         for (int64_t r = t; r < p.n; r += kHT) {
             const u64 key = coarse_key(dcf, r);
-            if (key >= lo && key < hi) atomicAdd(&hsm[(unsigned)((key >> nshift) & ((1ull << dbits) - 1))], 1u);
+            if (key >= lo && key <= hi) atomicAdd(&hsm[(unsigned)((key - lo) >> shift)], 1u);
         }
         __syncthreads();
         find_bin<kHT>(hsm, need, res, tmp);
-        lo += (u64)res[0] << nshift;
-        hi = lo + (1ull << nshift);
+        const u64 nlo = lo + ((u64)res[0] << shift);
+        const u64 room = hi - nlo, width = (1ull << shift) - 1ull;
+        hi = nlo + (room < width ? room : width);
+        lo = nlo;
         need -= res[1];
         in_bin = res[2];
-        shift = nshift;
     }
     __syncthreads();
     if (t == 0) {
@@ -182,8 +227,8 @@ __device__ void refine_frame(const HierParams& p, int f, unsigned char* region, 
         const u64 key = coarse_key(dcf, r);
         if (key < lo) {
             const unsigned pos = atomicAdd(&res[0], 1u);
-            if (pos < (unsigned)kHMaxShort) short_rows[pos] = (int)r;
-        } else if (key < hi) {
+            if (pos < (unsigned)kHMaxShort) fk[pos] = (u64)r;
+        } else if (key <= hi) {
             const unsigned pos = atomicAdd(&res[1], 1u);
             if (pos < (unsigned)kHBinCap) bin_keys[pos] = key;
         }
@@ -193,30 +238,28 @@ __device__ void refine_frame(const HierParams& p, int f, unsigned char* region, 
     const unsigned nb = min(res[1], (unsigned)kHBinCap);
     need = min(need, nb);
     if (need > 0) {
-        const u64 cstar = block_kth_key<kHT>(bin_keys, nb, need, lo, shift, hsm, res, tmp);
+        const u64 cstar = block_kth_key<kHT>(bin_keys, nb, need, lo, hi, hsm, res, tmp);
         if (t == 0) res[0] = direct;
         __syncthreads();
         for (unsigned i = t; i < nb; i += kHT) {
             const u64 key = bin_keys[i];
             if (key <= cstar) {
                 const unsigned pos = atomicAdd(&res[0], 1u);
-                if (pos < (unsigned)kHMaxShort) short_rows[pos] = (int)key_row(key);
+                if (pos < (unsigned)kHMaxShort) fk[pos] = (u64)key_row(key);
             }
         }
         __syncthreads();
     }
-    const int total = (int)min(direct + need, (unsigned)kHMaxShort);
+    const unsigned total = min(direct + need, (unsigned)kHMaxShort);
     const float* q = p.Q + (size_t)f * p.D;
-    u64 L = kKeyEmpty, thr = kKeyEmpty;
-    for (int i = warp; i < total; i += kHW) {
-        const uint32_t r = (uint32_t)short_rows[i];
-        const u64 key = make_key(warp_dist<CPL>(p.X, p.D, q, r, lane), r);
-        if (key < thr) {
-            list_insert(L, key, p.k, lane);
-            thr = __shfl_sync(kFull, L, p.k - 1);
-        }
+    for (unsigned i = warp; i < total; i += kHW) {
+        const uint32_t r = (uint32_t)fk[i];
+        const float d = warp_dist<CPL>(p.X, p.D, q, r, lane);
+        __syncwarp();
+        if (lane == 0) fk[i] = make_key(d, r);
     }
-    finish_frame(p, f, L, wl);
+    __syncthreads();
+    select_topk(p, f, fk, total, hsm, outk, res, tmp);
 }
 
 template <int DC4, int CPL>
@@ -224,8 +267,7 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char* region = smem;                                           // kHRegion
     float4* qsc = reinterpret_cast<float4*>(smem + kHRegion);               // 8 frames x DC4
-    u64* wl = reinterpret_cast<u64*>(qsc + 8 * DC4);                        // kHW x 32
-    unsigned* fr = reinterpret_cast<unsigned*>(wl + kHW * 32);              // per frame: lo(2) hi(2) flags
+    unsigned* fr = reinterpret_cast<unsigned*>(qsc + 8 * DC4);              // per frame: lo(2) hi(2) flags
     unsigned* res = fr + 8 * 8;                                             // 4
     unsigned* tmp = res + 4;                                                // kHW
     volatile int* abort_sm = reinterpret_cast<volatile int*>(tmp + kHW);
@@ -263,7 +305,7 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
             }
             const float d = acc.x + acc.y;
             p.dcbuf[(size_t)f * p.n + row] = d;
-            atomicAdd(&hsm[f * kBins + (__float_as_uint(d) >> 20)], 1u);
+            atomicAdd(&hsm[f * kBins + coarse_digit(d)], 1u);
         }
     }
     __syncthreads();
@@ -273,7 +315,7 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
     }
     if (!grid_sync(p.bar, abort_sm, p.err)) return;
 
-    // ------------------------------------------------ B: boundary bin per frame, collect
+    // ------------------------------------------------ B: boundary bin per frame, collect, re-score
     const bool take_all = p.n <= p.S;
     if (warp < nf) {
         const int f = warp;
@@ -286,9 +328,10 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
         } else {
             const uint3 b = warp_find_bin(p.hist + (size_t)f * kBins, (unsigned)p.S, lane);
             if (lane == 0) {
-                const u64 lo = (u64)b.x << 52;
+                u64 lo, hi;
+                bin_range(b.x, lo, hi);
                 *reinterpret_cast<u64*>(&fr[f * 8 + 0]) = lo;
-                *reinterpret_cast<u64*>(&fr[f * 8 + 2]) = lo + (1ull << 52);
+                *reinterpret_cast<u64*>(&fr[f * 8 + 2]) = hi;
                 fr[f * 8 + 4] = b.z > (unsigned)kHBinCap ? 1u : 0u;
                 if (blockIdx.x == 0) {
                     p.ctl[f * kHCtl + cRefine] = fr[f * 8 + 4];
@@ -299,25 +342,30 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
     }
     __syncthreads();
     {
-        // Appends are counted per warp, summed per CTA, and placed with one
-        // global atomic per (frame, list) and chunk of kHT rows.
-        unsigned* wcnt = reinterpret_cast<unsigned*>(region);  // [2 nf][kHW] counts, then bases
+        // Appends are counted per warp, placed with one global atomic per
+        // (frame, list) and chunk of kHT rows, and queued in shared memory;
+        // then the CTA's warps re-score the queued rows, one row per warp.
+        unsigned* wcnt = reinterpret_cast<unsigned*>(region);  // [16][kHW] per-warp counts, then offsets
+        unsigned* gbase = wcnt + 16 * kHW;                      // [16] global slot of the CTA's first append
+        unsigned* ibase = gbase + 16;                           // [17] queue offsets per (frame, list)
+        int* q_row = reinterpret_cast<int*>(ibase + 32);        // queue: row
+        unsigned* q_meta = reinterpret_cast<unsigned*>(q_row + kHT * 8);  // queue: slot << 4 | frame << 1 | list
         const unsigned below = (1u << lane) - 1u;
         for (int64_t base = r0; base < r1; base += kHT) {
             const int64_t row = base + t;
             const bool valid = row < r1;
             unsigned rank[16];
-            u64 key[8];
+            u64 ckey[8];  // coarse keys of this row (boundary rows write theirs once placed)
 #pragma unroll
             for (int f = 0; f < 8; ++f) {
                 bool d = false, b = false;
-                key[f] = kKeyEmpty;
+                ckey[f] = kKeyEmpty;
                 if (f < nf && !fr[f * 8 + 4]) {
                     const u64 lo = *reinterpret_cast<const u64*>(&fr[f * 8 + 0]);
                     const u64 hi = *reinterpret_cast<const u64*>(&fr[f * 8 + 2]);
-                    key[f] = valid ? coarse_key(p.dcbuf + (size_t)f * p.n, row) : kKeyEmpty;
-                    d = valid && (take_all || key[f] < lo);
-                    b = valid && !d && key[f] < hi;
+                    ckey[f] = valid ? coarse_key(p.dcbuf + (size_t)f * p.n, row) : kKeyEmpty;
+                    d = valid && (take_all || ckey[f] < lo);
+                    b = valid && !d && ckey[f] <= hi;
                 }
                 const unsigned md = __ballot_sync(kFull, d), mb = __ballot_sync(kFull, b);
                 rank[2 * f] = d ? __popc(md & below) : ~0u;
@@ -328,28 +376,68 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
                 }
             }
             __syncthreads();
-            if (t < 2 * nf) {
+            if (t < 32) {
+                // lane j < 2 nf owns list j = 2 f + kind: CTA total, one global atomic, per-warp offsets
                 unsigned tot = 0;
-                for (int w = 0; w < kHW; ++w) tot += wcnt[t * kHW + w];
-                unsigned at = tot ? atomicAdd(&p.ctl[(t / 2) * kHCtl + ((t & 1) ? cInBin : cDirect)], tot) : 0u;
-                for (int w = 0; w < kHW; ++w) {
-                    const unsigned c = wcnt[t * kHW + w];
-                    wcnt[t * kHW + w] = at;
-                    at += c;
+                if (t < 2 * nf)
+                    for (int w = 0; w < kHW; ++w) tot += wcnt[t * kHW + w];
+                unsigned at = (t < 2 * nf && tot) ? atomicAdd(&p.ctl[(t / 2) * kHCtl + ((t & 1) ? cInBin : cDirect)], tot) : 0u;
+                unsigned incl = tot;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned v = __shfl_up_sync(kFull, incl, o);
+                    if (t >= o) incl += v;
                 }
+                if (t < 2 * nf) {
+                    gbase[t] = at;
+                    ibase[t] = incl - tot;
+                    unsigned run = 0;
+                    for (int w = 0; w < kHW; ++w) {
+                        const unsigned c = wcnt[t * kHW + w];
+                        wcnt[t * kHW + w] = run;
+                        run += c;
+                    }
+                }
+                if (t == 31) ibase[16] = incl;  // queue length (lanes >= 2 nf add 0)
             }
             __syncthreads();
 #pragma unroll
             for (int f = 0; f < 8; ++f) {
                 if (f < nf) {
-                    if (rank[2 * f] != ~0u) {
-                        const unsigned pos = wcnt[(2 * f) * kHW + warp] + rank[2 * f];
-                        if (pos < (unsigned)kHMaxShort) p.direct[(size_t)f * kHMaxShort + pos] = (int)row;
+#pragma unroll
+                    for (int kind = 0; kind < 2; ++kind) {
+                        const unsigned rk = rank[2 * f + kind];
+                        if (rk != ~0u) {
+                            const int j = 2 * f + kind;
+                            const unsigned local = wcnt[j * kHW + warp] + rk;
+                            const unsigned slot = gbase[j] + local;
+                            const unsigned cap = kind ? (unsigned)kHBinCap : (unsigned)kHMaxShort;
+                            if (slot < cap) {
+                                if (kind) p.bins[(size_t)f * kHBinCap + slot] = ckey[f];
+                                const unsigned qi = ibase[j] + local;
+                                q_row[qi] = (int)row;
+                                q_meta[qi] = (slot << 4) | ((unsigned)f << 1) | (unsigned)kind;
+                            } else {
+                                const unsigned qi = ibase[j] + local;
+                                q_row[qi] = -1;
+                                q_meta[qi] = 0u;
+                            }
+                        }
                     }
-                    if (rank[2 * f + 1] != ~0u) {
-                        const unsigned pos = wcnt[(2 * f + 1) * kHW + warp] + rank[2 * f + 1];
-                        if (pos < (unsigned)kHBinCap) p.bins[(size_t)f * kHBinCap + pos] = key[f];
-                    }
+                }
+            }
+            __syncthreads();
+            const unsigned nq_items = ibase[16];
+            for (unsigned i = warp; i < nq_items; i += kHW) {
+                const int r = q_row[i];
+                if (r < 0) continue;
+                const unsigned meta = q_meta[i];
+                const int f = (meta >> 1) & 7, kind = meta & 1;
+                const unsigned slot = meta >> 4;
+                const float d = warp_dist<CPL>(p.X, p.D, p.Q + (size_t)f * p.D, (uint32_t)r, lane);
+                if (lane == 0) {
+                    if (kind) p.fkb[(size_t)f * kHBinCap + slot] = make_key(d, (uint32_t)r);
+                    else p.fkd[(size_t)f * kHMaxShort + slot] = make_key(d, (uint32_t)r);
                 }
             }
             __syncthreads();
@@ -357,80 +445,62 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
     }
     if (!grid_sync(p.bar, abort_sm, p.err)) return;
 
-    // ------------------------------------------------ C: full distances of every collected row
-    unsigned* cnts = reinterpret_cast<unsigned*>(region);  // per frame: direct, in-bin (0 if refined)
-    if (t < nf) {
-        const bool rf = __ldcg(&p.ctl[t * kHCtl + cRefine]) != 0u;
-        cnts[2 * t] = rf ? 0u : min(__ldcg(&p.ctl[t * kHCtl + cDirect]), (unsigned)kHMaxShort);
-        cnts[2 * t + 1] = rf ? 0u : min(__ldcg(&p.ctl[t * kHCtl + cInBin]), (unsigned)kHBinCap);
-    }
-    __syncthreads();
-    {
-        unsigned total = 0;
-        for (int f = 0; f < nf; ++f) total += cnts[2 * f] + cnts[2 * f + 1];
-        const unsigned gw = blockIdx.x * kHW + warp, GW = gridDim.x * kHW;
-        for (unsigned item = gw; item < total; item += GW) {
-            unsigned j = item;
-            int f = 0;
-            while (j >= cnts[2 * f] + cnts[2 * f + 1]) {
-                j -= cnts[2 * f] + cnts[2 * f + 1];
-                ++f;
-            }
-            const bool is_direct = j < cnts[2 * f];
-            const uint32_t row = is_direct ? (uint32_t)__ldcg(p.direct + (size_t)f * kHMaxShort + j)
-                                           : key_row(__ldcg(p.bins + (size_t)f * kHBinCap + (j - cnts[2 * f])));
-            const float d = warp_dist<CPL>(p.X, p.D, p.Q + (size_t)f * p.D, row, lane);
-            if (lane == 0) {
-                if (is_direct) p.fkd[(size_t)f * kHMaxShort + j] = make_key(d, row);
-                else p.fkb[(size_t)f * kHBinCap + (j - cnts[2 * f])] = make_key(d, row);
-            }
-        }
-    }
-    if (!grid_sync(p.bar, abort_sm, p.err)) return;
-
-    // ------------------------------------------------ D: per frame, exact S-cut and top k
+    // ------------------------------------------------ C: per frame, exact S-cut and top k
     if ((int)blockIdx.x < nf) {
         const int f = blockIdx.x;
         if (__ldcg(&p.ctl[f * kHCtl + cRefine]) != 0u) {
-            refine_frame<CPL>(p, f, region, wl, res, tmp);
+            refine_frame<CPL>(p, f, region, res, tmp);
         } else {
             const unsigned cd = min(__ldcg(&p.ctl[f * kHCtl + cDirect]), (unsigned)kHMaxShort);
             const unsigned nb = min(__ldcg(&p.ctl[f * kHCtl + cInBin]), (unsigned)kHBinCap);
             const unsigned need = take_all ? 0u : min(__ldcg(&p.ctl[f * kHCtl + cNeed]), nb);
-            u64* sk = reinterpret_cast<u64*>(region);                   // kHBinCap
-            unsigned* hs = reinterpret_cast<unsigned*>(sk + kHBinCap);  // kBins
+            u64* sk = reinterpret_cast<u64*>(region);                   // kHBinCap coarse keys
+            u64* fk = sk + kHBinCap;                                    // kHMaxShort full keys
+            unsigned* hs = reinterpret_cast<unsigned*>(fk + kHMaxShort); // kBins
+            u64* outk = reinterpret_cast<u64*>(hs + kBins);             // 32
             for (unsigned i = t; i < nb; i += kHT) sk[i] = __ldcg(p.bins + (size_t)f * kHBinCap + i);
+            for (unsigned i = t; i < cd; i += kHT) fk[i] = __ldcg(p.fkd + (size_t)f * kHMaxShort + i);
             __syncthreads();
-            // last boundary key inside the shortlist
-            const u64 cstar =
-                need > 0 ? block_kth_key<kHT>(sk, nb, need, *reinterpret_cast<const u64*>(&fr[f * 8 + 0]), 52, hs, res, tmp)
-                         : 0ull;
-            u64 L = kKeyEmpty, thr = kKeyEmpty;
-            for (unsigned base = 0; base < cd + nb; base += kHT) {
-                const unsigned i = base + t;
-                u64 key = kKeyEmpty;
-                if (i < cd) {
-                    key = __ldcg(p.fkd + (size_t)f * kHMaxShort + i);
-                } else if (i < cd + nb && need > 0) {
-                    const unsigned j = i - cd;
-                    if (__ldcg(p.bins + (size_t)f * kHBinCap + j) <= cstar) key = __ldcg(p.fkb + (size_t)f * kHBinCap + j);
-                }
-                unsigned m = __ballot_sync(kFull, key < thr);
-                while (m) {
-                    const int j = __ffs(m) - 1;
-                    m &= m - 1;
-                    list_insert(L, __shfl_sync(kFull, key, j), p.k, lane);
-                }
-                thr = __shfl_sync(kFull, L, p.k - 1);
+            unsigned total = cd;
+            if (need > 0) {
+                // last boundary key inside the shortlist; exactly `need` keys are <= it
+                const u64 cstar = block_kth_key<kHT>(sk, nb, need, *reinterpret_cast<const u64*>(&fr[f * 8 + 0]),
+                                                     *reinterpret_cast<const u64*>(&fr[f * 8 + 2]), hs, res, tmp);
+                if (t == 0) res[3] = cd;
+                __syncthreads();
+                for (unsigned i = t; i < nb; i += kHT)
+                    if (sk[i] <= cstar) {
+                        const unsigned pos = atomicAdd(&res[3], 1u);
+                        if (pos < (unsigned)kHMaxShort) fk[pos] = __ldcg(p.fkb + (size_t)f * kHBinCap + i);
+                    }
+                __syncthreads();
+                total = min(res[3], (unsigned)kHMaxShort);
+                __syncthreads();
             }
-            finish_frame(p, f, L, wl);
+            select_topk(p, f, fk, total, hs, outk, res, tmp);
         }
+        __threadfence();  // this frame's idx / dist before the count
+        __syncthreads();
+        if (t == 0) atomicAdd(&p.bar[2], 1u);  // frame f done
     }
-    if (p.ap.a.nw == 0) return;
-    if (!grid_sync(p.bar, abort_sm, p.err)) return;
+    if (p.ap.a.nw == 0 || (int)blockIdx.x >= p.ap.a.nw) return;
 
-    // ------------------------------------------------ E: Algorithm 2 per window
-    if ((int)blockIdx.x < p.ap.a.nw && warp == 0) {
+    // ------------------------------------------------ D: Algorithm 2 per window
+    if (t == 0) {
+        volatile unsigned* done = p.bar + 2;
+        const u64 t0 = globaltimer();
+        while (*done < (unsigned)nf) {
+            if (globaltimer() - t0 > kWaitLimitNs) {
+                *abort_sm = 1;
+                record_error(p.err, kErrTimeout);
+                break;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    if (*abort_sm) return;
+    if (warp == 0) {
         const AggArgs& a = p.ap.a;
         const int w = blockIdx.x;
         const long long b0 = (long long)a.offsets[w] * a.per_frame, b1 = (long long)a.offsets[w + 1] * a.per_frame;
@@ -450,7 +520,7 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct HierLayout {
-    size_t dcbuf, hist, ctl, bar, zero_end, direct, bins, fkd, fkb, total;
+    size_t dcbuf, hist, ctl, bar, zero_end, bins, fkd, fkb, total;
 };
 
 HierLayout hlayout(const lhr_db* db, int nf) {
@@ -459,9 +529,8 @@ HierLayout hlayout(const lhr_db* db, int nf) {
     L.hist = a256((size_t)nf * db->n * sizeof(float));
     L.ctl = L.hist + (size_t)nf * kBins * sizeof(unsigned);
     L.bar = L.ctl + (size_t)nf * kHCtl * sizeof(unsigned);
-    L.zero_end = L.bar + 2 * sizeof(unsigned);
-    L.direct = a256(L.zero_end);
-    L.bins = a256(L.direct + (size_t)nf * kHMaxShort * sizeof(int));
+    L.zero_end = L.bar + 4 * sizeof(unsigned);
+    L.bins = a256(L.zero_end);
     L.fkd = a256(L.bins + (size_t)nf * kHBinCap * sizeof(u64));
     L.fkb = a256(L.fkd + (size_t)nf * kHMaxShort * sizeof(u64));
     L.total = a256(L.fkb + (size_t)nf * kHBinCap * sizeof(u64));
@@ -469,8 +538,7 @@ HierLayout hlayout(const lhr_db* db, int nf) {
 }
 
 size_t hier_smem(int dc4) {
-    return kHRegion + (size_t)8 * dc4 * sizeof(float4) + kHW * 32 * sizeof(u64) +
-           (8 * 8 + 4 + kHW + 4) * sizeof(unsigned);
+    return kHRegion + (size_t)8 * dc4 * sizeof(float4) + (8 * 8 + 4 + kHW + 4) * sizeof(unsigned);
 }
 
 template <int DC4, int CPL>
@@ -522,7 +590,6 @@ cudaError_t launch_hier_fused(const lhr_db* db, const float* q, int nq, int shor
     hp.hist = reinterpret_cast<unsigned*>(base + L.hist);
     hp.ctl = reinterpret_cast<unsigned*>(base + L.ctl);
     hp.bar = reinterpret_cast<unsigned*>(base + L.bar);
-    hp.direct = reinterpret_cast<int*>(base + L.direct);
     hp.bins = reinterpret_cast<u64*>(base + L.bins);
     hp.fkd = reinterpret_cast<u64*>(base + L.fkd);
     hp.fkb = reinterpret_cast<u64*>(base + L.fkb);

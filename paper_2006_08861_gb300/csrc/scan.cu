@@ -478,10 +478,12 @@ ScanConfig choose_config(const lhr_db* db, int nq) {
 }
 
 // ------------------------------------------------------------------ pilot
-// Distances of every pilot-sample row to every frame (one warp per row, up to
-// 8 frames per reduction round; the same direct-form FP32 arithmetic as the
-// scan's exact step), folded into the bucket minima read by pilot_bound:
+// Distances of every pilot-sample row to every frame (direct-form FP32, the
+// arithmetic of the scan's exact step up to the summation order), folded into
+// the bucket minima read by pilot_bound:
 // bmin[(f * n_sub + sub_p[j]) * 128 + j % 128] (float bits, preset to ~0u).
+// A warp takes 4 rows and 8 frames per round: 32 partial sums per lane, one
+// butterfly transpose-reduce, and lane l then holds (row l / 8, frame l % 8).
 template <int CPL>
 __global__ void __launch_bounds__(256) pilot_kernel(const float* Xp, const int32_t* sub_p, int64_t np, int D,
                                                     const float* Q, int nq, int n_sub, unsigned* bmin) {
@@ -489,48 +491,57 @@ __global__ void __launch_bounds__(256) pilot_kernel(const float* Xp, const int32
     const int D4 = D / 4;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
-    for (int64_t r = gw; r < np; r += nw) {
-        float4 x[CPL];
-        const float4* xr = reinterpret_cast<const float4*>(Xp + r * D);
+    for (int64_t r0 = gw * 4; r0 < np; r0 += nw * 4) {
+        float4 x[4][CPL];
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) {
-            const int c = lane + 32 * j;
-            x[j] = c < D4 ? __ldg(xr + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = 0; i < 4; ++i) {
+            const float4* xr = reinterpret_cast<const float4*>(Xp + (r0 + i) * D);
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                const int c = lane + 32 * j;
+                x[i][j] = (r0 + i < np && c < D4) ? __ldg(xr + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
-        const int sub = __ldg(sub_p + r);
+        const int64_t r = r0 + lane / 8;
+        const int sub = r < np ? __ldg(sub_p + r) : 0;
         for (int f0 = 0; f0 < nq; f0 += 8) {
-            float de[8];
+            float part[32];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                float2 acc = f2(0.f, 0.f);
-                if (f0 + i < nq) {
-                    const float4* qr = reinterpret_cast<const float4*>(Q + (size_t)(f0 + i) * D);
+            for (int f = 0; f < 8; ++f) {
+                float4 qv[CPL];
+                const float4* qr = reinterpret_cast<const float4*>(Q + (size_t)min(f0 + f, nq - 1) * D);
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) {
+                    const int c = lane + 32 * j;
+                    qv[j] = c < D4 ? __ldg(qr + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float2 acc = f2(0.f, 0.f);
 #pragma unroll
                     for (int j = 0; j < CPL; ++j) {
-                        const int c = lane + 32 * j;
-                        if (c < D4) {
-                            const float4 qv = __ldg(qr + c);
-                            const float2 d0 = __ffma2_rn(f2(x[j].x, x[j].y), f2(-1.f, -1.f), f2(qv.x, qv.y));
-                            const float2 d1 = __ffma2_rn(f2(x[j].z, x[j].w), f2(-1.f, -1.f), f2(qv.z, qv.w));
-                            acc = __ffma2_rn(d0, d0, acc);
-                            acc = __ffma2_rn(d1, d1, acc);
-                        }
+                        const float2 d0 = __ffma2_rn(f2(x[i][j].x, x[i][j].y), f2(-1.f, -1.f), f2(qv[j].x, qv[j].y));
+                        const float2 d1 = __ffma2_rn(f2(x[i][j].z, x[i][j].w), f2(-1.f, -1.f), f2(qv[j].z, qv[j].w));
+                        acc = __ffma2_rn(d0, d0, acc);
+                        acc = __ffma2_rn(d1, d1, acc);
                     }
+                    part[i * 8 + f] = acc.x + acc.y;
                 }
-                de[i] = acc.x + acc.y;
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int st = 16; st >= 1; st >>= 1) {
+                const bool upper = (lane & st) != 0;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) de[i] += __shfl_xor_sync(kFull, de[i], o);
+                for (int v = 0; v < st; ++v) {
+                    const float send = upper ? part[v] : part[v + st];
+                    const float keep = upper ? part[v + st] : part[v];
+                    part[v] = keep + __shfl_xor_sync(kFull, send, st);
+                }
             }
-            if (lane < 8 && f0 + lane < nq) {
-                float v = de[0];
-#pragma unroll
-                for (int i = 1; i < 8; ++i) v = lane == i ? de[i] : v;
-                atomicMin(bmin + ((size_t)(f0 + lane) * n_sub + sub) * kPilotBuckets + (r % kPilotBuckets),
-                          __float_as_uint(v));
-            }
+            const int f = f0 + lane % 8;
+            if (r < np && f < nq)
+                atomicMin(bmin + ((size_t)f * n_sub + sub) * kPilotBuckets + (r % kPilotBuckets),
+                          __float_as_uint(part[0]));
         }
     }
 }
@@ -581,7 +592,7 @@ cudaError_t launch_pilot(const lhr_db* db, const float* q, int nq, void* scratch
     if (e != cudaSuccess) return e;
     const int d4 = db->dim / 4;
     const int cpl = d4 <= 32 ? 1 : (d4 <= 64 ? 2 : 4);
-    const int grid = (int)std::min<int64_t>((db->n_pilot + 7) / 8, (int64_t)db->sms * 32);
+    const int grid = (int)std::min<int64_t>((db->n_pilot + 31) / 32, (int64_t)db->sms * 8);
     {
         ProfScope ps("scan_pilot", stream);
         if (cpl == 1) pilot_kernel<1><<<grid, 256, 0, stream>>>(db->Xp, db->sub_p, db->n_pilot, db->dim, q, nq, db->n_sub, bmin);

@@ -95,35 +95,37 @@ __device__ __forceinline__ uint3 warp_find_bin(const unsigned* hist, unsigned ne
 }
 
 // The need-th smallest (1-based) of the nb distinct keys keys[0, nb) in shared
-// memory, all of which lie in [lo, lo + 2^shift): radix refinement on 11-bit
-// digits, one histogram pass per digit, until one key is left in the range.
-// `hsm` holds kBins words, `res` 4 and `tmp` THREADS / 32; every thread of the
-// block calls it and gets the key.
+// memory, all of which lie in [lo, hi] (inclusive; any range): radix
+// refinement, each pass histogramming the keys still in range on the 11-bit
+// digit (key - lo) >> shift (shift chosen so the range fits 2048 bins), until
+// one key is left. `hsm` holds kBins words, `res` 4 and `tmp` THREADS / 32;
+// every thread of the block calls it and gets the key.
 template <int THREADS>
-__device__ u64 block_kth_key(const u64* keys, unsigned nb, unsigned need, u64 lo, int shift, unsigned* hsm,
+__device__ u64 block_kth_key(const u64* keys, unsigned nb, unsigned need, u64 lo, u64 hi, unsigned* hsm,
                              unsigned* res, unsigned* tmp) {
     const int t = threadIdx.x;
     for (;;) {
-        const int nshift = shift > 11 ? shift - 11 : 0;
-        const u64 hi = shift >= 64 ? ~0ull : lo + (1ull << shift) - 1ull;  // inclusive
-        const unsigned mask = (1u << (shift - nshift)) - 1u;
+        const u64 span = hi - lo;
+        if (span == 0) return lo;
+        const int bits = 64 - __clzll((long long)span);
+        const int shift = bits > 11 ? bits - 11 : 0;
         for (int i = t; i < kBins; i += THREADS) hsm[i] = 0u;
         __syncthreads();
         for (unsigned i = t; i < nb; i += THREADS) {
             const u64 key = keys[i];
-            if (key >= lo && key <= hi) atomicAdd(&hsm[(unsigned)(key >> nshift) & mask], 1u);
+            if (key >= lo && key <= hi) atomicAdd(&hsm[(unsigned)((key - lo) >> shift)], 1u);
         }
         __syncthreads();
         find_bin<THREADS>(hsm, need, res, tmp);
-        lo += (u64)res[0] << nshift;
+        const u64 nlo = lo + ((u64)res[0] << shift);
+        const u64 room = hi - nlo, width = (1ull << shift) - 1ull;
+        hi = nlo + (room < width ? room : width);
+        lo = nlo;
         need -= res[1];
-        const unsigned in_bin = res[2];
-        shift = nshift;
         if (shift == 0) return lo;
-        if (in_bin == 1u) break;
+        if (res[2] == 1u) break;
     }
-    // one key left in [lo, lo + 2^shift)
-    const u64 hi = lo + (1ull << shift) - 1ull;
+    // one key left in [lo, hi]
     u64* found = reinterpret_cast<u64*>(hsm);
     __syncthreads();
     for (unsigned i = t; i < nb; i += THREADS) {
