@@ -18,6 +18,7 @@ struct AggParams {
     int64_t n;
     long long rlim;       // floor(sqrt(r2max)): larger |dx| or |dy| is outside the circle
     int* err;
+    const u64* tile_keys;  // nullable: tile key of each candidate slot (as a.idx), gathered by the producer
 };
 
 __device__ __forceinline__ u64 tile_key(int tx, int ty) {
@@ -38,6 +39,50 @@ __device__ __forceinline__ T warp_sum(T v) {
 __device__ __forceinline__ void write_invalid(const AggArgs& a, int w) {
     a.status[w] = kErrInvalidArg;
     a.xy_out[2 * w] = a.xy_out[2 * w + 1] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// Sorts keys[0, 32 E) ascending in registers: element i = e * 32 + lane lives
+// in v[e] (a bitonic network; strides below 32 cross lanes by shuffles, the
+// others stay in the lane).
+template <int E>
+__device__ __forceinline__ void warp_sort_regs(u64 (&v)[E], int lane) {
+#pragma unroll
+    for (int size = 2; size <= 32 * E; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int es = stride / 32;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if (e & es) continue;
+                    const bool asc = ((e * 32) & size) == 0;
+                    const u64 a = v[e], b = v[e + es];
+                    const u64 lo = a < b ? a : b, hi = a < b ? b : a;
+                    v[e] = asc ? lo : hi;
+                    v[e + es] = asc ? hi : lo;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const u64 o = __shfl_xor_sync(kFull, v[e], stride);
+                    const bool asc = ((e * 32 + lane) & size) == 0;
+                    const bool keep_min = ((lane & stride) == 0) == asc;
+                    v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
+                }
+            }
+        }
+    }
+}
+
+// keys[0, 32 E) sorted in place through registers (entries >= n read as empty).
+template <int E>
+__device__ __noinline__ void warp_sort_smem(u64* keys, int n, int lane) {
+    u64 v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = e * 32 + lane < n ? keys[e * 32 + lane] : kKeyEmpty;
+    warp_sort_regs<E>(v, lane);
+#pragma unroll
+    for (int e = 0; e < E; ++e) keys[e * 32 + lane] = v[e];
 }
 
 // Algorithm 2 for one window of at most kWarpCand candidate slots, by a single
@@ -61,7 +106,7 @@ __device__ inline void aggregate_warp(const AggParams& p, int w, long long b0, l
         if (take) {
             cand_rows[pos] = (int)r;
             cand_d[pos] = a.dist != nullptr ? __ldcg(a.dist + b0 + i) : 0.f;
-            keys[pos] = tile_key(p.tile[2 * r], p.tile[2 * r + 1]);
+            keys[pos] = p.tile_keys != nullptr ? __ldcg(p.tile_keys + b0 + i) : tile_key(p.tile[2 * r], p.tile[2 * r + 1]);
         }
         C += __popc(m);
     }
@@ -74,26 +119,15 @@ __device__ inline void aggregate_warp(const AggParams& p, int w, long long b0, l
     int status = 0;
     int win_tx = 0, win_ty = 0;
     if (a.mode != 2) {
-        // step 2: binning = sort the tile keys, count runs
-        int p2 = 2;
-        while (p2 < C) p2 <<= 1;
-        for (int i = C + lane; i < p2; i += 32) keys[i] = kKeyEmpty;
+        // step 2: binning = sort the tile keys (in registers), count runs
+        static_assert(kWarpCand == 32 * 32, "sort widths below cover kWarpCand");
+        if (C <= 32) warp_sort_smem<1>(keys, C, lane);
+        else if (C <= 64) warp_sort_smem<2>(keys, C, lane);
+        else if (C <= 128) warp_sort_smem<4>(keys, C, lane);
+        else if (C <= 256) warp_sort_smem<8>(keys, C, lane);
+        else if (C <= 512) warp_sort_smem<16>(keys, C, lane);
+        else warp_sort_smem<32>(keys, C, lane);
         __syncwarp();
-        for (int size = 2; size <= p2; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = lane; i < p2 / 2; i += 32) {
-                    const int lo = 2 * i - (i & (stride - 1));
-                    const int hi = lo + stride;
-                    const bool up = (lo & size) == 0;
-                    const u64 x = keys[lo], y = keys[hi];
-                    if ((x > y) == up) {
-                        keys[lo] = y;
-                        keys[hi] = x;
-                    }
-                }
-                __syncwarp();
-            }
-        }
         int U = 0;
         for (int base = 0; base < C; base += 32) {
             const int i = base + lane;

@@ -72,6 +72,7 @@ struct HierParams {
     u64* fkd;         // nf x kHMaxShort full keys of the direct rows
     int64_t* idx;     // nf x k
     float* dist;
+    u64* ctk;         // nf x k tile keys of the results (Algorithm 2 reads them)
     agg::AggParams ap;  // windows over the frames (per_frame = k), ap.a.nw of them; nw = 0: none
     int* err;
 };
@@ -79,19 +80,19 @@ struct HierParams {
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 // Bounded grid-wide barrier (all CTAs are co-resident: cooperative launch).
-__device__ bool grid_sync(unsigned* bar, volatile int* abort_sm, int* err) {
+// bar[0] counts arrivals over the whole launch (zeroed before it); the j-th
+// barrier completes when it reaches j * gridDim.x, so the last arrival has
+// nothing more to do.
+__device__ bool grid_sync(unsigned* bar, unsigned& epoch, volatile int* abort_sm, int* err) {
     __syncthreads();
+    epoch += gridDim.x;
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = bar + 1;
-        const unsigned g = *gen;
         __threadfence();
-        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
-            bar[0] = 0u;
-            __threadfence();
-            atomicAdd(&bar[1], 1u);
-        } else {
+        const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
+        if (arrived < epoch) {
+            volatile unsigned* cnt = bar;
             const u64 t0 = globaltimer();
-            while (*gen == g) {
+            while (*cnt < epoch) {
                 if (globaltimer() - t0 > kWaitLimitNs) {
                     *abort_sm = 1;
                     record_error(err, kErrTimeout);
@@ -129,6 +130,47 @@ __device__ __forceinline__ float warp_dist(const float* X, int D, const float* q
     return d;
 }
 
+// Full-feature distances of up to 4 (row, frame) pairs by one warp, all loads
+// issued before any reduction (the rows usually come from HBM). Entries with
+// row < 0 are skipped (their result is unspecified).
+template <int CPL>
+__device__ __forceinline__ void warp_dist4(const float* X, int D, const float* Q, const int* rows, const int* frames,
+                                           float* out, int lane) {
+    const int D4 = D / 4;
+    float4 x[4][CPL];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4* xr = reinterpret_cast<const float4*>(X + (size_t)max(rows[i], 0) * D);
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            const int c = lane + 32 * j;
+            x[i][j] = (rows[i] >= 0 && c < D4) ? __ldg(xr + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4* qr = reinterpret_cast<const float4*>(Q + (size_t)frames[i] * D);
+        float2 acc = f2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            const int c = lane + 32 * j;
+            if (rows[i] >= 0 && c < D4) {
+                const float4 qv = __ldg(qr + c);
+                const float2 a = __ffma2_rn(f2(x[i][j].x, x[i][j].y), f2(-1.f, -1.f), f2(qv.x, qv.y));
+                const float2 b = __ffma2_rn(f2(x[i][j].z, x[i][j].w), f2(-1.f, -1.f), f2(qv.z, qv.w));
+                acc = __ffma2_rn(a, a, acc);
+                acc = __ffma2_rn(b, b, acc);
+            }
+        }
+        out[i] = acc.x + acc.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) out[i] += __shfl_xor_sync(kFull, out[i], o);
+    }
+}
+
 // Writes frame f's final top k: the keys of fk[0, total) that are <= kth
 // (at most 32 of them, distinct) are gathered, sorted by warp 0 and written.
 __device__ void write_topk(const HierParams& p, int f, const u64* fk, unsigned total, u64 kth, u64* outk,
@@ -162,8 +204,10 @@ __device__ void write_topk(const HierParams& p, int f, const u64* fk, unsigned t
                 p.idx[o] = -1;
                 p.dist[o] = __int_as_float(0x7f800000);
             } else {
-                p.idx[o] = (int64_t)key_row(v);
+                const uint32_t r = key_row(v);
+                p.idx[o] = (int64_t)r;
                 p.dist[o] = key_dist(v);
+                if (p.ctk != nullptr) p.ctk[o] = agg::tile_key(__ldg(p.ap.tile + 2 * r), __ldg(p.ap.tile + 2 * r + 1));
             }
         }
     }
@@ -173,8 +217,36 @@ __device__ void write_topk(const HierParams& p, int f, const u64* fk, unsigned t
 // Top k of fk[0, total) (distinct keys) written as frame f's result.
 __device__ void select_topk(const HierParams& p, int f, const u64* fk, unsigned total, unsigned* hs, u64* outk,
                             unsigned* res, unsigned* tmp) {
-    const u64 kth = total > (unsigned)p.k ? block_kth_key<kHT>(fk, total, (unsigned)p.k, 0ull, ~0ull, hs, res, tmp)
-                                          : ~0ull;
+    u64 kth = ~0ull;
+    if (total > (unsigned)p.k) {
+        // the keys' range first, so the radix passes split it from the start
+        u64* mm = reinterpret_cast<u64*>(hs);  // [kHW] minima, [kHW] maxima
+        u64 lo = ~0ull, hi = 0ull;
+        for (unsigned i = threadIdx.x; i < total; i += kHT) {
+            const u64 v = fk[i];
+            lo = v < lo ? v : lo;
+            hi = v > hi ? v : hi;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const u64 a = __shfl_xor_sync(kFull, lo, o), b = __shfl_xor_sync(kFull, hi, o);
+            lo = a < lo ? a : lo;
+            hi = b > hi ? b : hi;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            mm[threadIdx.x / 32] = lo;
+            mm[kHW + threadIdx.x / 32] = hi;
+        }
+        __syncthreads();
+        lo = ~0ull;
+        hi = 0ull;
+        for (int w = 0; w < kHW; ++w) {
+            lo = mm[w] < lo ? mm[w] : lo;
+            hi = mm[kHW + w] > hi ? mm[kHW + w] : hi;
+        }
+        __syncthreads();
+        kth = block_kth_key<kHT>(fk, total, (unsigned)p.k, lo, hi, hs, res, tmp);
+    }
     write_topk(p, f, fk, total, kth, outk, res);
 }
 
@@ -277,10 +349,20 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
     const int64_t per = (p.n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = min(p.n, (int64_t)blockIdx.x * per), r1 = min(p.n, r0 + per);
     if (t == 0) *abort_sm = 0;
+    unsigned epoch = 0;  // barrier target (same in every thread)
 
     // ------------------------------------------------ A: coarse distances + histograms
+    // Thread t scores rows r0 + t + i kHT; with at most two such rows each
+    // (in_regs) the distances also stay in registers for phase B.
+    const bool in_regs = r1 - r0 <= 2 * kHT;
+    float dreg[2][8];
     unsigned* hsm = reinterpret_cast<unsigned*>(region);  // nf x kBins
+    unsigned* drange = hsm + 8 * kBins;                    // per frame: lowest, highest digit seen
     for (int i = t; i < nf * kBins; i += kHT) hsm[i] = 0u;
+    if (t < 8) {
+        drange[2 * t] = kBins;
+        drange[2 * t + 1] = 0u;
+    }
     const int dc4 = p.dc / 4;
     for (int i = t; i < 8 * DC4; i += kHT) {
         const int f = i / DC4, c = i % DC4;
@@ -288,32 +370,65 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
                                      : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    for (int64_t row = r0 + t; row < r1; row += kHT) {
-        float4 x[DC4];
-        const float4* xr = reinterpret_cast<const float4*>(p.Xc + row * p.dc);
+    {
+        unsigned dlo[8], dhi[8];
 #pragma unroll
-        for (int c = 0; c < DC4; ++c) x[c] = c < dc4 ? __ldg(xr + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int f = 0; f < nf; ++f) {
-            float2 acc = f2(0.f, 0.f);
+        for (int f = 0; f < 8; ++f) {
+            dlo[f] = kBins;
+            dhi[f] = 0u;
+        }
+        int slot = 0;
+        for (int64_t row = r0 + t; row < r1; row += kHT, ++slot) {
+            float4 x[DC4];
+            const float4* xr = reinterpret_cast<const float4*>(p.Xc + row * p.dc);
 #pragma unroll
-            for (int c = 0; c < DC4; ++c) {
-                const float4 qv = qsc[f * DC4 + c];
-                const float2 a = __ffma2_rn(f2(x[c].x, x[c].y), f2(-1.f, -1.f), f2(qv.x, qv.y));
-                const float2 b = __ffma2_rn(f2(x[c].z, x[c].w), f2(-1.f, -1.f), f2(qv.z, qv.w));
-                acc = __ffma2_rn(a, a, acc);
-                acc = __ffma2_rn(b, b, acc);
+            for (int c = 0; c < DC4; ++c) x[c] = c < dc4 ? __ldg(xr + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int f = 0; f < 8; ++f) {
+                if (f >= nf) break;
+                float2 acc = f2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < DC4; ++c) {
+                    const float4 qv = qsc[f * DC4 + c];
+                    const float2 a = __ffma2_rn(f2(x[c].x, x[c].y), f2(-1.f, -1.f), f2(qv.x, qv.y));
+                    const float2 b = __ffma2_rn(f2(x[c].z, x[c].w), f2(-1.f, -1.f), f2(qv.z, qv.w));
+                    acc = __ffma2_rn(a, a, acc);
+                    acc = __ffma2_rn(b, b, acc);
+                }
+                const float d = acc.x + acc.y;
+                p.dcbuf[(size_t)f * p.n + row] = d;
+                if (slot == 0) dreg[0][f] = d;
+                else if (slot == 1) dreg[1][f] = d;
+                const unsigned g = coarse_digit(d);
+                dlo[f] = min(dlo[f], g);
+                dhi[f] = max(dhi[f], g);
+                atomicAdd(&hsm[f * kBins + g], 1u);
             }
-            const float d = acc.x + acc.y;
-            p.dcbuf[(size_t)f * p.n + row] = d;
-            atomicAdd(&hsm[f * kBins + coarse_digit(d)], 1u);
+        }
+#pragma unroll
+        for (int f = 0; f < 8; ++f) {
+            if (f >= nf) break;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                dlo[f] = min(dlo[f], __shfl_xor_sync(kFull, dlo[f], o));
+                dhi[f] = max(dhi[f], __shfl_xor_sync(kFull, dhi[f], o));
+            }
+            if (lane == 0 && dlo[f] <= dhi[f]) {
+                atomicMin(&drange[2 * f], dlo[f]);
+                atomicMax(&drange[2 * f + 1], dhi[f]);
+            }
         }
     }
     __syncthreads();
-    for (int i = t; i < nf * kBins; i += kHT) {
-        const unsigned v = hsm[i];
-        if (v) atomicAdd(&p.hist[i], v);
+    // only the digits this CTA met are flushed
+    for (int f = 0; f < nf; ++f) {
+        const unsigned lo = drange[2 * f], hi = drange[2 * f + 1];
+        for (unsigned g = lo + t; g <= hi; g += kHT) {
+            const unsigned v = hsm[f * kBins + g];
+            if (v) atomicAdd(&p.hist[(size_t)f * kBins + g], v);
+        }
     }
-    if (!grid_sync(p.bar, abort_sm, p.err)) return;
+    if (!grid_sync(p.bar, epoch, abort_sm, p.err)) return;
 
     // ------------------------------------------------ B: boundary bin per frame, collect, re-score
     const bool take_all = p.n <= p.S;
@@ -342,37 +457,80 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
     }
     __syncthreads();
     {
-        // Appends are counted per warp, placed with one global atomic per
-        // (frame, list) and chunk of kHT rows, and queued in shared memory;
-        // then the CTA's warps re-score the queued rows, one row per warp.
+        // Rows are taken two per thread (rows base + t and base + t + kHT) per
+        // round; appends are counted per warp, placed with one global atomic
+        // per (frame, list) and round, and queued in shared memory; the CTA's
+        // warps re-score the queue (4 rows per warp at a time) when the next
+        // round might not fit, and at the end. A row that finds the queue full
+        // is re-scored by its own thread.
+        constexpr unsigned kQCap = kHT * 8;
         unsigned* wcnt = reinterpret_cast<unsigned*>(region);  // [16][kHW] per-warp counts, then offsets
         unsigned* gbase = wcnt + 16 * kHW;                      // [16] global slot of the CTA's first append
-        unsigned* ibase = gbase + 16;                           // [17] queue offsets per (frame, list)
+        unsigned* ibase = gbase + 16;                           // [16] queue offsets per (frame, list); [16] fill
         int* q_row = reinterpret_cast<int*>(ibase + 32);        // queue: row
-        unsigned* q_meta = reinterpret_cast<unsigned*>(q_row + kHT * 8);  // queue: slot << 4 | frame << 1 | list
+        unsigned* q_meta = reinterpret_cast<unsigned*>(q_row + kQCap);  // queue: slot << 4 | frame << 1 | list
         const unsigned below = (1u << lane) - 1u;
-        for (int64_t base = r0; base < r1; base += kHT) {
-            const int64_t row = base + t;
-            const bool valid = row < r1;
-            unsigned rank[16];
-            u64 ckey[8];  // coarse keys of this row (boundary rows write theirs once placed)
+        auto drain = [&](unsigned nitems) {
+            for (unsigned i0 = 4 * warp; i0 < nitems; i0 += 4 * kHW) {
+                int rows[4], frames[4];
+                unsigned meta[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned i = i0 + u;
+                    rows[u] = i < nitems ? q_row[i] : -1;
+                    meta[u] = i < nitems ? q_meta[i] : 0u;
+                    frames[u] = (int)((meta[u] >> 1) & 7u);
+                }
+                float d[4];
+                warp_dist4<CPL>(p.X, p.D, p.Q, rows, frames, d, lane);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (lane == u && rows[u] >= 0) {
+                        const unsigned slot = meta[u] >> 4;
+                        const u64 key = make_key(d[u], (uint32_t)rows[u]);
+                        if (meta[u] & 1u) p.fkb[(size_t)frames[u] * kHBinCap + slot] = key;
+                        else p.fkd[(size_t)frames[u] * kHMaxShort + slot] = key;
+                    }
+                }
+            }
+        };
+        unsigned qfill = 0;  // same value in every thread
+        for (int64_t base = r0; base < r1; base += 2 * kHT) {
+            if (qfill + (unsigned)(2 * kHT * nf) > kQCap && qfill > 0) {
+                drain(qfill);
+                qfill = 0;
+                __syncthreads();
+            }
+            // code[i][f]: 0xffff = row i takes no part in frame f's lists, else
+            // list << 15 | rank of the row among the warp's appends to that list
+            unsigned code[2][8];
+            float dv[2][8];  // coarse distances of the two rows
 #pragma unroll
             for (int f = 0; f < 8; ++f) {
-                bool d = false, b = false;
-                ckey[f] = kKeyEmpty;
-                if (f < nf && !fr[f * 8 + 4]) {
-                    const u64 lo = *reinterpret_cast<const u64*>(&fr[f * 8 + 0]);
-                    const u64 hi = *reinterpret_cast<const u64*>(&fr[f * 8 + 2]);
-                    ckey[f] = valid ? coarse_key(p.dcbuf + (size_t)f * p.n, row) : kKeyEmpty;
-                    d = valid && (take_all || ckey[f] < lo);
-                    b = valid && !d && ckey[f] <= hi;
+                unsigned mdv[2], mbv[2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int64_t row = base + t + i * kHT;
+                    const bool valid = row < r1;
+                    bool d = false, b = false;
+                    dv[i][f] = 0.f;
+                    if (f < nf && !fr[f * 8 + 4] && valid) {
+                        dv[i][f] = in_regs ? dreg[i][f] : __ldcg(p.dcbuf + (size_t)f * p.n + row);
+                        const u64 key = ((u64)__float_as_uint(dv[i][f]) << 32) | (u64)row;
+                        const u64 lo = *reinterpret_cast<const u64*>(&fr[f * 8 + 0]);
+                        const u64 hi = *reinterpret_cast<const u64*>(&fr[f * 8 + 2]);
+                        d = take_all || key < lo;
+                        b = !d && key <= hi;
+                    }
+                    mdv[i] = __ballot_sync(kFull, d);
+                    mbv[i] = __ballot_sync(kFull, b);
+                    const unsigned pre_d = i ? __popc(mdv[0]) : 0u, pre_b = i ? __popc(mbv[0]) : 0u;
+                    code[i][f] = d ? pre_d + __popc(mdv[i] & below)
+                                   : (b ? 0x8000u | (pre_b + __popc(mbv[i] & below)) : 0xffffu);
                 }
-                const unsigned md = __ballot_sync(kFull, d), mb = __ballot_sync(kFull, b);
-                rank[2 * f] = d ? __popc(md & below) : ~0u;
-                rank[2 * f + 1] = b ? __popc(mb & below) : ~0u;
                 if (lane == 0 && f < nf) {
-                    wcnt[(2 * f) * kHW + warp] = __popc(md);
-                    wcnt[(2 * f + 1) * kHW + warp] = __popc(mb);
+                    wcnt[(2 * f) * kHW + warp] = __popc(mdv[0]) + __popc(mdv[1]);
+                    wcnt[(2 * f + 1) * kHW + warp] = __popc(mbv[0]) + __popc(mbv[1]);
                 }
             }
             __syncthreads();
@@ -381,7 +539,8 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
                 unsigned tot = 0;
                 if (t < 2 * nf)
                     for (int w = 0; w < kHW; ++w) tot += wcnt[t * kHW + w];
-                unsigned at = (t < 2 * nf && tot) ? atomicAdd(&p.ctl[(t / 2) * kHCtl + ((t & 1) ? cInBin : cDirect)], tot) : 0u;
+                const unsigned at =
+                    (t < 2 * nf && tot) ? atomicAdd(&p.ctl[(t / 2) * kHCtl + ((t & 1) ? cInBin : cDirect)], tot) : 0u;
                 unsigned incl = tot;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -390,7 +549,7 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
                 }
                 if (t < 2 * nf) {
                     gbase[t] = at;
-                    ibase[t] = incl - tot;
+                    ibase[t] = qfill + incl - tot;
                     unsigned run = 0;
                     for (int w = 0; w < kHW; ++w) {
                         const unsigned c = wcnt[t * kHW + w];
@@ -398,52 +557,56 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
                         run += c;
                     }
                 }
-                if (t == 31) ibase[16] = incl;  // queue length (lanes >= 2 nf add 0)
+                if (t == 31) ibase[16] = incl;  // items this round (lanes >= 2 nf add 0)
             }
             __syncthreads();
 #pragma unroll
-            for (int f = 0; f < 8; ++f) {
-                if (f < nf) {
+            for (int i = 0; i < 2; ++i) {
+                const int64_t row = base + t + i * kHT;
 #pragma unroll
-                    for (int kind = 0; kind < 2; ++kind) {
-                        const unsigned rk = rank[2 * f + kind];
-                        if (rk != ~0u) {
-                            const int j = 2 * f + kind;
-                            const unsigned local = wcnt[j * kHW + warp] + rk;
-                            const unsigned slot = gbase[j] + local;
-                            const unsigned cap = kind ? (unsigned)kHBinCap : (unsigned)kHMaxShort;
-                            if (slot < cap) {
-                                if (kind) p.bins[(size_t)f * kHBinCap + slot] = ckey[f];
-                                const unsigned qi = ibase[j] + local;
-                                q_row[qi] = (int)row;
-                                q_meta[qi] = (slot << 4) | ((unsigned)f << 1) | (unsigned)kind;
-                            } else {
-                                const unsigned qi = ibase[j] + local;
-                                q_row[qi] = -1;
-                                q_meta[qi] = 0u;
+                for (int f = 0; f < 8; ++f) {
+                    if (f >= nf) break;
+                    {
+                        if (code[i][f] == 0xffffu) continue;
+                        const int kind = (int)(code[i][f] >> 15);
+                        const unsigned rk = code[i][f] & 0x7fffu;
+                        const int j = 2 * f + kind;
+                        const unsigned local = wcnt[j * kHW + warp] + rk;
+                        const unsigned slot = gbase[j] + local;
+                        const unsigned cap = kind ? (unsigned)kHBinCap : (unsigned)kHMaxShort;
+                        const bool kept = slot < cap;  // else a boundary overflow: the frame is refined in phase C
+                        if (kept && kind)
+                            p.bins[(size_t)f * kHBinCap + slot] = ((u64)__float_as_uint(dv[i][f]) << 32) | (u64)row;
+                        const unsigned qi = ibase[j] + local;
+                        if (qi < kQCap) {
+                            q_row[qi] = kept ? (int)row : -1;
+                            q_meta[qi] = (slot << 4) | ((unsigned)f << 1) | (unsigned)kind;
+                        } else if (kept) {
+                            // queue full: this thread re-scores the row alone
+                            const float4* xr = reinterpret_cast<const float4*>(p.X + (size_t)row * p.D);
+                            const float4* qr = reinterpret_cast<const float4*>(p.Q + (size_t)f * p.D);
+                            float a = 0.f;
+                            for (int c = 0; c < p.D / 4; ++c) {
+                                const float4 xv = __ldg(xr + c), qv = __ldg(qr + c);
+                                a = fmaf(qv.x - xv.x, qv.x - xv.x, a);
+                                a = fmaf(qv.y - xv.y, qv.y - xv.y, a);
+                                a = fmaf(qv.z - xv.z, qv.z - xv.z, a);
+                                a = fmaf(qv.w - xv.w, qv.w - xv.w, a);
                             }
+                            const u64 key = make_key(a, (uint32_t)row);
+                            if (kind) p.fkb[(size_t)f * kHBinCap + slot] = key;
+                            else p.fkd[(size_t)f * kHMaxShort + slot] = key;
                         }
                     }
                 }
             }
-            __syncthreads();
-            const unsigned nq_items = ibase[16];
-            for (unsigned i = warp; i < nq_items; i += kHW) {
-                const int r = q_row[i];
-                if (r < 0) continue;
-                const unsigned meta = q_meta[i];
-                const int f = (meta >> 1) & 7, kind = meta & 1;
-                const unsigned slot = meta >> 4;
-                const float d = warp_dist<CPL>(p.X, p.D, p.Q + (size_t)f * p.D, (uint32_t)r, lane);
-                if (lane == 0) {
-                    if (kind) p.fkb[(size_t)f * kHBinCap + slot] = make_key(d, (uint32_t)r);
-                    else p.fkd[(size_t)f * kHMaxShort + slot] = make_key(d, (uint32_t)r);
-                }
-            }
+            // entries of this round that did not fit were handled in place
+            qfill = min(qfill + ibase[16], kQCap);
             __syncthreads();
         }
+        drain(qfill);
     }
-    if (!grid_sync(p.bar, abort_sm, p.err)) return;
+    if (!grid_sync(p.bar, epoch, abort_sm, p.err)) return;
 
     // ------------------------------------------------ C: per frame, exact S-cut and top k
     if ((int)blockIdx.x < nf) {

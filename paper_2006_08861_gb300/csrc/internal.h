@@ -103,6 +103,10 @@ struct ProfScope {
 size_t scan_scratch_bytes(const lhr_db* db, int nq, int k, bool pilot);
 cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t* idx, float* dist,
                         void* scratch, bool pilot, cudaStream_t stream);
+// Weighted exhaustive scan: d_w = sum_j w_j (q_j - x_j)^2, w device (D), >= 0.
+size_t scan_weighted_scratch_bytes(const lhr_db* db, int nq, int k);
+cudaError_t launch_scan_weighted(const lhr_db* db, const float* q, int nq, int k, const float* w, int64_t* idx,
+                                 float* dist, void* scratch, cudaStream_t stream);
 
 struct AggArgs;
 

@@ -64,6 +64,8 @@ struct ScanParams {
     int k;
     int stages;
     const unsigned* bmin;  // nullable: [nq][n_sub][kPilotBuckets] pilot bucket minima (float bits; ~0u = empty)
+    const float* w;        // nullable: per-dimension weights (>= 0) of the weighted distance; NULL = all 1
+    const float* xmax_w;   // nullable: device max over rows of sum_j w_j x_j^2 (weighted scans)
     float xmax;          // sqrt(max ||x||^2)
     float margin_scale;  // 2 (gamma_D + 3u)
     u64* partial;        // [qblock][QB][nchunks][k]
@@ -133,7 +135,8 @@ __global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(cons
 
     float* stage_buf = reinterpret_cast<float*>(smem);
     float* qs = stage_buf + NS * stage_floats;                            // QB x D
-    u64* full = reinterpret_cast<u64*>(qs + (size_t)QB * D);
+    float* ws = qs + (size_t)QB * D;                                      // D weights
+    u64* full = reinterpret_cast<u64*>(ws + D);
     u64* empty = full + NS;
     u64* lists = empty + NS;                                              // [warps][QB][32]
     unsigned* thr_sh = reinterpret_cast<unsigned*>(lists + (size_t)warps * QB * 32);  // QB float bits
@@ -161,6 +164,7 @@ __global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(cons
         reinterpret_cast<float4*>(qs)[i] =
             qi < p.nq ? reinterpret_cast<const float4*>(p.Q)[(size_t)qi * D4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    for (int i = threadIdx.x; i < D; i += blockDim.x) ws[i] = p.w != nullptr ? p.w[i] : 1.f;
     for (int i = threadIdx.x; i < warps * QB * 32; i += blockDim.x) lists[i] = kKeyEmpty;
     if (threadIdx.x < QB) thr_sh[threadIdx.x] = 0x7f800000u;  // +inf
     __syncthreads();
@@ -199,13 +203,16 @@ __global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(cons
             float a = 0.f;
 #pragma unroll
             for (int j = 0; j < CPL; ++j) {
+                // registers hold w * q; ||q||_w^2 = sum_j (w_j q_j) q_j
                 const int c = lane + 32 * j;
-                qreg[q][j] = c < D4 ? reinterpret_cast<const float4*>(qs + (size_t)q * D)[c]
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
-                a = fmaf(qreg[q][j].x, qreg[q][j].x, a);
-                a = fmaf(qreg[q][j].y, qreg[q][j].y, a);
-                a = fmaf(qreg[q][j].z, qreg[q][j].z, a);
-                a = fmaf(qreg[q][j].w, qreg[q][j].w, a);
+                const float4 qv = c < D4 ? reinterpret_cast<const float4*>(qs + (size_t)q * D)[c]
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 wv = c < D4 ? reinterpret_cast<const float4*>(ws)[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+                qreg[q][j] = make_float4(wv.x * qv.x, wv.y * qv.y, wv.z * qv.z, wv.w * qv.w);
+                a = fmaf(qreg[q][j].x, qv.x, a);
+                a = fmaf(qreg[q][j].y, qv.y, a);
+                a = fmaf(qreg[q][j].z, qv.z, a);
+                a = fmaf(qreg[q][j].w, qv.w, a);
             }
             qpart[q] = a;
         }
@@ -222,7 +229,7 @@ __global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(cons
             for (int f = warp; f < QB && qblock * QB + f < p.nq; f += warps) pilot_bound(p, qblock * QB + f, ch.z, lane, &thr_sh[f]);
         const int myq = lane % QB;
         const bool q_valid = (qblock * QB + myq) < p.nq;
-        const float rad = p.xmax + sqrtf(qn);
+        const float rad = (p.xmax_w != nullptr ? sqrtf(__ldg(p.xmax_w)) * 1.0001f : p.xmax) + sqrtf(qn);
         const float margin = p.margin_scale * rad * rad;
         float thr_own = __int_as_float(0x7f800000);  // k-th distance of this warp's list for frame myq
         u64* wlist = lists + (size_t)warp * QB * 32;
@@ -304,16 +311,18 @@ __global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(cons
                     // exact direct-form distance of (row rj, frame qj)
                     const float4* xr = reinterpret_cast<const float4*>(sbf + (size_t)rj * D);
                     const float4* qr = reinterpret_cast<const float4*>(qs + (size_t)qj * D);
+                    const float4* wr = reinterpret_cast<const float4*>(ws);
                     float2 acc = f2(0.f, 0.f);
 #pragma unroll
                     for (int jj = 0; jj < CPL; ++jj) {
                         const int c = lane + 32 * jj;
                         if (c < D4) {
-                            const float4 x = xr[c], qv = qr[c];
+                            // w (q - x)^2; with w = 1 the product is exact and this is sum (q - x)^2
+                            const float4 x = xr[c], qv = qr[c], wv = wr[c];
                             const float2 d0 = __ffma2_rn(f2(x.x, x.y), f2(-1.f, -1.f), f2(qv.x, qv.y));
                             const float2 d1 = __ffma2_rn(f2(x.z, x.w), f2(-1.f, -1.f), f2(qv.z, qv.w));
-                            acc = __ffma2_rn(d0, d0, acc);
-                            acc = __ffma2_rn(d1, d1, acc);
+                            acc = __ffma2_rn(__fmul2_rn(d0, f2(wv.x, wv.y)), d0, acc);
+                            acc = __ffma2_rn(__fmul2_rn(d1, f2(wv.z, wv.w)), d1, acc);
                         }
                     }
                     float de = acc.x + acc.y;
@@ -453,7 +462,7 @@ ScanConfig choose_config(const lhr_db* db, int nq) {
     while (qb < nq && qb < qb_max) qb *= 2;
     c.qb = qb;
     const size_t stage_bytes = (size_t)kRPS * db->dim * sizeof(float);
-    const size_t qs_bytes = (size_t)qb * db->dim * sizeof(float);
+    const size_t qs_bytes = (size_t)(qb + 1) * db->dim * sizeof(float);  // frames + weights
     auto smem_for = [&](int w, int per) {
         const int ns = per * w;
         return ns * stage_bytes + qs_bytes + 2 * ns * sizeof(u64) + (size_t)w * qb * 32 * sizeof(u64) +
@@ -486,7 +495,8 @@ ScanConfig choose_config(const lhr_db* db, int nq) {
 // butterfly transpose-reduce, and lane l then holds (row l / 8, frame l % 8).
 template <int CPL>
 __global__ void __launch_bounds__(256) pilot_kernel(const float* Xp, const int32_t* sub_p, int64_t np, int D,
-                                                    const float* Q, int nq, int n_sub, unsigned* bmin) {
+                                                    const float* Q, int nq, int n_sub, const float* w,
+                                                    unsigned* bmin) {
     const int lane = threadIdx.x % 32;
     const int D4 = D / 4;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
@@ -504,6 +514,13 @@ __global__ void __launch_bounds__(256) pilot_kernel(const float* Xp, const int32
         }
         const int64_t r = r0 + lane / 8;
         const int sub = r < np ? __ldg(sub_p + r) : 0;
+        float4 wv[CPL];
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            const int c = lane + 32 * j;
+            wv[j] = (w != nullptr && c < D4) ? __ldg(reinterpret_cast<const float4*>(w) + c)
+                                             : make_float4(1.f, 1.f, 1.f, 1.f);
+        }
         for (int f0 = 0; f0 < nq; f0 += 8) {
             float part[32];
 #pragma unroll
@@ -522,8 +539,8 @@ __global__ void __launch_bounds__(256) pilot_kernel(const float* Xp, const int32
                     for (int j = 0; j < CPL; ++j) {
                         const float2 d0 = __ffma2_rn(f2(x[i][j].x, x[i][j].y), f2(-1.f, -1.f), f2(qv[j].x, qv[j].y));
                         const float2 d1 = __ffma2_rn(f2(x[i][j].z, x[i][j].w), f2(-1.f, -1.f), f2(qv[j].z, qv[j].w));
-                        acc = __ffma2_rn(d0, d0, acc);
-                        acc = __ffma2_rn(d1, d1, acc);
+                        acc = __ffma2_rn(__fmul2_rn(d0, f2(wv[j].x, wv[j].y)), d0, acc);
+                        acc = __ffma2_rn(__fmul2_rn(d1, f2(wv[j].z, wv[j].w)), d1, acc);
                     }
                     part[i * 8 + f] = acc.x + acc.y;
                 }
@@ -544,6 +561,37 @@ __global__ void __launch_bounds__(256) pilot_kernel(const float* Xp, const int32
                           __float_as_uint(part[0]));
         }
     }
+}
+
+// Weighted row norms sum_j w_j x_j^2 (internal order) and their maximum (float
+// bits, atomicMax; the values are >= 0); one warp per row. Block 0 also checks
+// the weights: a negative or non-finite one records LHR_ERR_INVALID_ARG.
+__global__ void __launch_bounds__(256) wnorm_kernel(const float* X, int64_t n, int D, const float* w, float* xnw,
+                                                    unsigned* max_bits, int* err) {
+    const int lane = threadIdx.x % 32;
+    const int D4 = D / 4;
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < D; i += blockDim.x)
+            if (!(w[i] >= 0.f && w[i] < __int_as_float(0x7f800000))) record_error(err, kErrInvalidArg);
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
+    unsigned mx = 0u;
+    for (int64_t r = gw; r < n; r += nw) {
+        const float4* xr = reinterpret_cast<const float4*>(X + r * D);
+        float a = 0.f;
+        for (int c = lane; c < D4; c += 32) {
+            const float4 x = __ldg(xr + c), wv = __ldg(reinterpret_cast<const float4*>(w) + c);
+            a = fmaf(wv.x * x.x, x.x, a);
+            a = fmaf(wv.y * x.y, x.y, a);
+            a = fmaf(wv.z * x.z, x.z, a);
+            a = fmaf(wv.w * x.w, x.w, a);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
+        if (lane == 0) xnw[r] = a;
+        mx = max(mx, __float_as_uint(a));
+    }
+    if (lane == 0 && mx) atomicMax(max_bits, mx);
 }
 
 template <int QB, int CPL>
@@ -585,8 +633,8 @@ bool use_pilot(const lhr_db* db, int nq) { return db->Xp != nullptr && nq <= kPi
 
 size_t pilot_bytes(const lhr_db* db, int nq) { return align256((size_t)nq * db->n_sub * kPilotBuckets * sizeof(unsigned)); }
 
-cudaError_t launch_pilot(const lhr_db* db, const float* q, int nq, void* scratch, unsigned** bmin_out,
-                         cudaStream_t stream) {
+cudaError_t launch_pilot(const lhr_db* db, const float* q, int nq, const float* w, void* scratch,
+                         unsigned** bmin_out, cudaStream_t stream) {
     unsigned* bmin = reinterpret_cast<unsigned*>(scratch);
     cudaError_t e = cudaMemsetAsync(bmin, 0xff, (size_t)nq * db->n_sub * kPilotBuckets * sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
@@ -595,16 +643,27 @@ cudaError_t launch_pilot(const lhr_db* db, const float* q, int nq, void* scratch
     const int grid = (int)std::min<int64_t>((db->n_pilot + 31) / 32, (int64_t)db->sms * 8);
     {
         ProfScope ps("scan_pilot", stream);
-        if (cpl == 1) pilot_kernel<1><<<grid, 256, 0, stream>>>(db->Xp, db->sub_p, db->n_pilot, db->dim, q, nq, db->n_sub, bmin);
-        else if (cpl == 2) pilot_kernel<2><<<grid, 256, 0, stream>>>(db->Xp, db->sub_p, db->n_pilot, db->dim, q, nq, db->n_sub, bmin);
-        else pilot_kernel<4><<<grid, 256, 0, stream>>>(db->Xp, db->sub_p, db->n_pilot, db->dim, q, nq, db->n_sub, bmin);
+        if (cpl == 1)
+            pilot_kernel<1><<<grid, 256, 0, stream>>>(db->Xp, db->sub_p, db->n_pilot, db->dim, q, nq, db->n_sub, w, bmin);
+        else if (cpl == 2)
+            pilot_kernel<2><<<grid, 256, 0, stream>>>(db->Xp, db->sub_p, db->n_pilot, db->dim, q, nq, db->n_sub, w, bmin);
+        else
+            pilot_kernel<4><<<grid, 256, 0, stream>>>(db->Xp, db->sub_p, db->n_pilot, db->dim, q, nq, db->n_sub, w, bmin);
     }
     *bmin_out = bmin;
     return cudaGetLastError();
 }
 
+// Weighted scans: the weights, the weighted row norms and their device max.
+struct ScanWeights {
+    const float* w;
+    const float* xnw;
+    const float* xmax_w;
+};
+
 cudaError_t scan_pass(const lhr_db* db, const ScanSrc& src, const char* label, const float* q, int nq, int k,
-                      const unsigned* bmin, int64_t* idx, float* dist, void* scratch, cudaStream_t stream) {
+                      const unsigned* bmin, const ScanWeights* wt, int64_t* idx, float* dist, void* scratch,
+                      cudaStream_t stream) {
     const ScanConfig c = choose_config(db, nq);
     const int nqb = (nq + c.qb - 1) / c.qb;
     ScanParams p{};
@@ -621,9 +680,15 @@ cudaError_t scan_pass(const lhr_db* db, const ScanSrc& src, const char* label, c
     p.k = k;
     p.stages = c.stages;
     p.bmin = bmin;
-    // 2 (gamma_D + 3u) with u = 2^-24 and gamma_D = D u / (1 - D u), slightly rounded up
+    if (wt != nullptr) {
+        p.w = wt->w;
+        p.xnorm = wt->xnw;
+        p.xmax_w = wt->xmax_w;
+    }
+    // 2 (gamma_{D+4} + 3u) with u = 2^-24 and gamma_m = m u / (1 - m u), slightly
+    // rounded up (the weighted form rounds w q and w (q - x) once more)
     const double u = 1.0 / 16777216.0;
-    const double gamma = db->dim * u / (1.0 - db->dim * u);
+    const double gamma = (db->dim + 4) * u / (1.0 - (db->dim + 4) * u);
     p.margin_scale = (float)(2.0 * (gamma + 3.0 * u) * 1.0001);
     // max ||x|| over the whole database bounds the sample's too
     p.xmax = (float)(sqrt((double)db->xnorm_max) * 1.0001);
@@ -658,22 +723,53 @@ size_t scan_scratch_bytes(const lhr_db* db, int nq, int k, bool pilot) {
     return pilot && use_pilot(db, nq) ? main + pilot_bytes(db, nq) : main;
 }
 
+namespace {
+
 // With a pilot sample (every 64th row): a bound on each frame's k-th distance
 // per subspace, taken from the sample (pilot_bound), seeds the full scan's
 // thresholds, so only rows that can still reach a top k are ever recomputed
 // and inserted. Every key of the final top k is <= that bound: the k sample
 // rows reaching it are database rows the full scan meets again.
-cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t* idx, float* dist, void* scratch,
-                        bool pilot, cudaStream_t stream) {
+cudaError_t scan_with_pilot(const lhr_db* db, const float* q, int nq, int k, const ScanWeights* wt, int64_t* idx,
+                            float* dist, void* scratch, bool pilot, cudaStream_t stream) {
     const ScanSrc full{db->X, db->xnorm, db->chunks, db->nchunks, db->chunk_off, db->perm};
     unsigned* bmin = nullptr;
     if (pilot && use_pilot(db, nq)) {
         const ScanConfig c = choose_config(db, nq);
         unsigned char* ps = reinterpret_cast<unsigned char*>(scratch) + pass_bytes(c, db->nchunks, db->n_sub, nq, k);
-        cudaError_t e = launch_pilot(db, q, nq, ps, &bmin, stream);
+        cudaError_t e = launch_pilot(db, q, nq, wt ? wt->w : nullptr, ps, &bmin, stream);
         if (e != cudaSuccess) return e;
     }
-    return scan_pass(db, full, "scan_topk_kernel", q, nq, k, bmin, idx, dist, scratch, stream);
+    return scan_pass(db, full, "scan_topk_kernel", q, nq, k, bmin, wt, idx, dist, scratch, stream);
+}
+
+}  // namespace
+
+cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t* idx, float* dist, void* scratch,
+                        bool pilot, cudaStream_t stream) {
+    return scan_with_pilot(db, q, nq, k, nullptr, idx, dist, scratch, pilot, stream);
+}
+
+size_t scan_weighted_scratch_bytes(const lhr_db* db, int nq, int k) {
+    return align256(((size_t)db->n + 1) * sizeof(float)) + scan_scratch_bytes(db, nq, k, true);
+}
+
+cudaError_t launch_scan_weighted(const lhr_db* db, const float* q, int nq, int k, const float* w, int64_t* idx,
+                                 float* dist, void* scratch, cudaStream_t stream) {
+    float* xnw = reinterpret_cast<float*>(scratch);
+    float* xmax_w = xnw + db->n;
+    void* rest = reinterpret_cast<unsigned char*>(scratch) + align256(((size_t)db->n + 1) * sizeof(float));
+    cudaError_t e = cudaMemsetAsync(xmax_w, 0, sizeof(float), stream);
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps("wnorm_kernel", stream);
+        const int grid = (int)std::min<int64_t>((db->n + 7) / 8, (int64_t)db->sms * 16);
+        wnorm_kernel<<<grid, 256, 0, stream>>>(db->X, db->n, db->dim, w, xnw, reinterpret_cast<unsigned*>(xmax_w),
+                                               db->err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const ScanWeights wt{w, xnw, xmax_w};
+    return scan_with_pilot(db, q, nq, k, &wt, idx, dist, rest, true, stream);
 }
 
 }  // namespace lhr
