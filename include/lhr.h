@@ -216,6 +216,57 @@ lhr_status lhr_query_static(const lhr_db* db, const float* q, int32_t nq, int32_
                             void* cuda_stream);
 
 /*
+ * Soft retrieval -- a differentiable relaxation of Algorithm 1's selection
+ * (§3.1) and of the window aggregation (§3.2) with learnable per-dimension
+ * feature weights w and a temperature tau. The paper defines no gradient; the
+ * form below is this library's, stated here in full.
+ *
+ *   d_w(q, x) = sum_j w_j (q_j - x_j)^2            (w_j >= 0; w = 1: §4's distance squared)
+ *   per frame f: the top k rows of each subspace by d_w (ties: lower row),
+ *                held fixed when differentiating
+ *   per window b: l_i = -d_i / tau over the window's m n_s k candidates,
+ *                 p = softmax(l), y^_b = sum_i p_i xy_i        (FP64 sums)
+ *   lhr_loc_mse:  L = (1/B) sum_b ||y^_b - y_b||^2
+ *
+ * lhr_query_weighted -- the selection alone: lhr_query's exhaustive FP32 scan
+ * with d_w. q nq x D float32 (device, 16-byte aligned); w D float32 (device,
+ * 16-byte aligned, every w_j finite and >= 0: a negative or non-finite weight
+ * records LHR_ERR_INVALID_ARG in the error word and the results are
+ * meaningless); 1 <= k <= 32; idx / dist nq x n_s x k as lhr_query, dist = d_w.
+ *
+ * lhr_soft_forward -- selection, then the window softmax. frames W x D and
+ * offsets nw + 1 as lhr_query_window (windows disjoint and in order); tau one
+ * float32 on the device (> 0, else the window's y^ is NaN and
+ * LHR_ERR_INVALID_ARG is recorded). Outputs (device): idx, dist W x n_s x k;
+ * p W x n_s x k float64 softmax weights (0 for padding slots); yhat nw x 2
+ * float64. Needs D <= 1024 and n_s k <= 1024 (else LHR_ERR_UNSUPPORTED).
+ *
+ * lhr_soft_backward -- given g_yhat = dL/dy^ (nw x 2 float64, device) and the
+ * forward's idx, dist, p, yhat, writes
+ *   dq   W x D float32:  dL/dq_fj = sum_{i in f} dL/dd_i 2 w_j (q_fj - x_ij)
+ *   dw   D float32:      dL/dw_j  = sum_i dL/dd_i (q_f(i)j - x_ij)^2
+ *   dtau 1 float32:      dL/dtau  = sum_i dL/dl_i d_i / tau^2
+ * with dL/dl_i = p_i g_b . (xy_i - y^_b) and dL/dd_i = -dL/dl_i / tau. The
+ * rows are re-read (no distance tile is kept); sums over windows run in a
+ * fixed order, so the result is deterministic.
+ *
+ * lhr_loc_mse -- loss = L (one float64) and/or grad = scale * dL/dy^
+ * (nw x 2 float64); scale is one float64 on the device, NULL = 1. Either
+ * output may be NULL, not both. Runs on the current device.
+ */
+lhr_status lhr_query_weighted(const lhr_db* db, const float* q, int32_t nq, int32_t k, const float* w,
+                              int64_t* idx, float* dist, void* cuda_stream);
+lhr_status lhr_soft_forward(const lhr_db* db, const float* frames, const int32_t* offsets, int32_t W, int32_t nw,
+                            int32_t k, const float* w, const float* tau, int64_t* idx, float* dist, double* p,
+                            double* yhat, void* cuda_stream);
+lhr_status lhr_soft_backward(const lhr_db* db, const float* frames, const int32_t* offsets, int32_t W, int32_t nw,
+                             int32_t k, const float* w, const float* tau, const int64_t* idx, const float* dist,
+                             const double* p, const double* yhat, const double* g_yhat, float* dq, float* dw,
+                             float* dtau, void* cuda_stream);
+lhr_status lhr_loc_mse(const double* yhat, const double* y, int32_t nw, const double* scale, double* loss,
+                       double* grad, void* cuda_stream);
+
+/*
  * Instrumentation (no counterpart in the paper): per-kernel CUDA-event timing.
  * lhr_profile_enable(1) makes every later launch record an event pair on its
  * stream around each kernel; lhr_profile_read synchronizes those events and

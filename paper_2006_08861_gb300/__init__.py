@@ -71,6 +71,10 @@ def _load():
         "lhr_aggregate_2d": [P, P, P, I64, P, I32, ctypes.POINTER(AggParams), P, P, P],
         "lhr_db_error": [P, ctypes.POINTER(I32), P],
         "lhr_query_static": [P, P, I32, I32, P, P, P],
+        "lhr_query_weighted": [P, P, I32, I32, P, P, P, P],
+        "lhr_soft_forward": [P, P, P, I32, I32, I32, P, P, P, P, P, P, P],
+        "lhr_soft_backward": [P, P, P, I32, I32, I32, P, P, P, P, P, P, P, P, P, P, P],
+        "lhr_loc_mse": [P, P, I32, P, P, P, P],
         "lhr_profile_enable": [I32],
         "lhr_profile_read": [ctypes.c_char_p, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double), I32],
     }
@@ -273,3 +277,128 @@ def lhr_db_error(db: Database, stream=None) -> int:
     e = ctypes.c_int32()
     _check(_lib.lhr_db_error(db.handle, ctypes.byref(e), _stream(stream)))
     return e.value
+
+
+# ------------------------------------------------------------------ soft retrieval
+def lhr_query_weighted(db: Database, q, k: int, w, out=None, stream=None):
+    """Exhaustive top-k by the weighted distance sum_j w_j (q_j - x_j)^2:
+    (idx int64 [nq, n_s, k], dist float32 [nq, n_s, k])."""
+    torch = _torch()
+    q = _dev_tensor(q, torch.float32, "q")
+    w = _dev_tensor(w, torch.float32, "w")
+    nq = q.shape[0]
+    if out is None:
+        idx = torch.empty((nq, db.n_subspaces, k), dtype=torch.int64, device=q.device)
+        dist = torch.empty((nq, db.n_subspaces, k), dtype=torch.float32, device=q.device)
+    else:
+        idx, dist = out
+    _check(_lib.lhr_query_weighted(db.handle, _ptr(q), nq, k, _ptr(w), _ptr(idx), _ptr(dist), _stream(stream)))
+    return idx, dist
+
+
+def lhr_soft_forward(db: Database, frames, offsets, k: int, w, tau, stream=None):
+    """Selection by the weighted distance, then the window softmax:
+    (idx [W, n_s, k], dist [W, n_s, k], p float64 [W, n_s, k], yhat float64 [nw, 2])."""
+    torch = _torch()
+    frames = _dev_tensor(frames, torch.float32, "frames")
+    offsets = _dev_tensor(offsets, torch.int32, "offsets")
+    w = _dev_tensor(w, torch.float32, "w")
+    tau = _dev_tensor(tau, torch.float32, "tau")
+    W, nw = frames.shape[0], offsets.shape[0] - 1
+    dev = frames.device
+    idx = torch.empty((W, db.n_subspaces, k), dtype=torch.int64, device=dev)
+    dist = torch.empty((W, db.n_subspaces, k), dtype=torch.float32, device=dev)
+    p = torch.empty((W, db.n_subspaces, k), dtype=torch.float64, device=dev)
+    yhat = torch.empty((nw, 2), dtype=torch.float64, device=dev)
+    _check(_lib.lhr_soft_forward(db.handle, _ptr(frames), _ptr(offsets), W, nw, k, _ptr(w), _ptr(tau), _ptr(idx),
+                                 _ptr(dist), _ptr(p), _ptr(yhat), _stream(stream)))
+    return idx, dist, p, yhat
+
+
+def lhr_soft_backward(db: Database, frames, offsets, k: int, w, tau, idx, dist, p, yhat, g_yhat, stream=None):
+    """Gradients (dq float32 [W, D], dw float32 [D], dtau float32 [1]) given dL/dyhat."""
+    torch = _torch()
+    frames = _dev_tensor(frames, torch.float32, "frames")
+    g_yhat = _dev_tensor(g_yhat, torch.float64, "g_yhat")
+    W, nw = frames.shape[0], offsets.shape[0] - 1
+    dq = torch.empty_like(frames)
+    dw = torch.empty_like(w)
+    dtau = torch.empty((1,), dtype=torch.float32, device=frames.device)
+    _check(_lib.lhr_soft_backward(db.handle, _ptr(frames), _ptr(offsets), W, nw, k, _ptr(w), _ptr(tau), _ptr(idx),
+                                  _ptr(dist), _ptr(p), _ptr(yhat), _ptr(g_yhat), _ptr(dq), _ptr(dw), _ptr(dtau),
+                                  _stream(stream)))
+    return dq, dw, dtau
+
+
+def lhr_loc_mse(yhat, y, scale=None, loss=True, grad=False, stream=None):
+    """L = mean_b ||yhat_b - y_b||^2 (float64 [1]) and/or scale * dL/dyhat (float64 [nw, 2])."""
+    torch = _torch()
+    yhat = _dev_tensor(yhat, torch.float64, "yhat")
+    y = _dev_tensor(y, torch.float64, "y")
+    nw = yhat.shape[0]
+    lo = torch.empty((1,), dtype=torch.float64, device=yhat.device) if loss else None
+    gr = torch.empty_like(yhat) if grad else None
+    sc = None if scale is None else _dev_tensor(scale, torch.float64, "scale")
+    _check(_lib.lhr_loc_mse(_ptr(yhat), _ptr(y), nw, _ptr(sc), _ptr(lo), _ptr(gr), _stream(stream)))
+    return lo, gr
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class SoftRetrieval(torch.autograd.Function):
+        """y^ = soft_retrieval(frames, w, tau): forward and backward are the
+        library's kernels (lhr_soft_forward / lhr_soft_backward)."""
+
+        @staticmethod
+        def forward(ctx, frames, w, tau, db, offsets, k):
+            frames, w, tau = frames.contiguous(), w.contiguous(), tau.contiguous()
+            idx, dist, p, yhat = lhr_soft_forward(db, frames, offsets, k, w, tau)
+            ctx.save_for_backward(frames, w, tau, offsets, idx, dist, p, yhat)
+            ctx.db, ctx.k = db, k
+            ctx.tau_shape = tau.shape
+            return yhat
+
+        @staticmethod
+        def backward(ctx, g):
+            frames, w, tau, offsets, idx, dist, p, yhat = ctx.saved_tensors
+            dq, dw, dtau = lhr_soft_backward(ctx.db, frames, offsets, ctx.k, w, tau, idx, dist, p, yhat,
+                                             g.contiguous().to(torch.float64))
+            return dq, dw, dtau.reshape(ctx.tau_shape), None, None, None
+
+    class LocMSE(torch.autograd.Function):
+        """L = mean_b ||y^_b - y_b||^2 (lhr_loc_mse)."""
+
+        @staticmethod
+        def forward(ctx, yhat, y):
+            yhat, y = yhat.contiguous(), y.contiguous()
+            loss, _ = lhr_loc_mse(yhat, y, loss=True, grad=False)
+            ctx.save_for_backward(yhat, y)
+            return loss.reshape(())
+
+        @staticmethod
+        def backward(ctx, g):
+            yhat, y = ctx.saved_tensors
+            _, grad = lhr_loc_mse(yhat, y, scale=g.reshape(1).to(torch.float64).contiguous(), loss=False, grad=True)
+            return grad, None
+
+    return SoftRetrieval, LocMSE
+
+
+_AUTOGRAD = None
+
+
+def soft_retrieval(db: Database, frames, offsets, w, tau, k: int):
+    """Differentiable window positions y^ (float64 [nw, 2]) w.r.t. frames, w and tau."""
+    global _AUTOGRAD
+    if _AUTOGRAD is None:
+        _AUTOGRAD = _make_autograd()
+    return _AUTOGRAD[0].apply(frames, w, tau, db, offsets, k)
+
+
+def loc_mse(yhat, y):
+    """Differentiable mean squared 2-D error of the window positions."""
+    global _AUTOGRAD
+    if _AUTOGRAD is None:
+        _AUTOGRAD = _make_autograd()
+    return _AUTOGRAD[1].apply(yhat, y)

@@ -127,7 +127,7 @@ static bool is_device_ptr(const void* p) {
 
 static void free_db(lhr_db* db) {
     if (!db) return;
-    void* bufs[] = {db->X, db->xnorm, db->Xc, db->perm, db->xy, db->tile, db->chunks, db->chunk_off,
+    void* bufs[] = {db->X, db->xnorm, db->Xc, db->perm, db->iperm, db->xy, db->tile, db->chunks, db->chunk_off,
                     db->Xb, db->snb, db->X8, db->sn8, db->Xb_s, db->snb_s, db->X8_s, db->sn8_s,
                     db->Xp, db->sub_p, db->err};
     for (void* b : bufs)
@@ -345,6 +345,12 @@ lhr_status lhr_build_db(const float* feats, const double* xy, const int32_t* sub
     if (need_perm) {
         if ((e = dalloc(&db->perm, (size_t)n)) != cudaSuccess) return bail(cuda_fail(e, "allocate perm"));
         cudaMemcpyAsync(db->perm, perm_h.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        std::vector<int32_t> iperm_h(n);
+        for (int64_t i = 0; i < n; ++i) iperm_h[perm_h[i]] = (int32_t)i;
+        if ((e = dalloc(&db->iperm, (size_t)n)) != cudaSuccess) return bail(cuda_fail(e, "allocate inverse perm"));
+        cudaMemcpyAsync(db->iperm, iperm_h.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        // iperm_h is read by the copy: finish it before the vector goes out of scope
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(cuda_fail(e, "copy inverse perm"));
         const float* src = feats;
         if (!feats_dev) {
             if ((e = dalloc(&tmp, (size_t)n * D)) != cudaSuccess) return bail(cuda_fail(e, "allocate staging"));
@@ -524,6 +530,86 @@ lhr_status lhr_aggregate_2d(const lhr_db* db, const int64_t* idx, const float* d
     ag.status = status;
     cudaError_t e = launch_aggregate(db, ag, reinterpret_cast<cudaStream_t>(cuda_stream));
     if (e != cudaSuccess) return cuda_fail(e, "aggregation launch");
+    return LHR_OK;
+}
+
+// ---------------------------------------------------------------- soft retrieval
+static lhr_status check_soft(const lhr_db* db, int32_t k, const float* w, const float* tau) {
+    if (!db) return fail(LHR_ERR_INVALID_ARG, "db is NULL");
+    if (!w || !tau) return fail(LHR_ERR_INVALID_ARG, "w and tau must be non-NULL");
+    if (reinterpret_cast<uintptr_t>(w) % 16) return fail(LHR_ERR_INVALID_ARG, "w must be 16-byte aligned");
+    if (k < 1 || k > 32) return fail(LHR_ERR_INVALID_ARG, "k must be in [1, 32]");
+    if (db->dim > 1024) return fail(LHR_ERR_UNSUPPORTED, "soft retrieval supports D <= 1024");
+    if ((int64_t)db->n_sub * k > 1024) return fail(LHR_ERR_UNSUPPORTED, "soft retrieval supports n_s * k <= 1024");
+    return LHR_OK;
+}
+
+lhr_status lhr_query_weighted(const lhr_db* db, const float* q, int32_t nq, int32_t k, const float* w,
+                              int64_t* idx, float* dist, void* cuda_stream) {
+    if (!db) return fail(LHR_ERR_INVALID_ARG, "db is NULL");
+    if (!q || !w || !idx || !dist) return fail(LHR_ERR_INVALID_ARG, "q, w, idx and dist must be non-NULL");
+    if (reinterpret_cast<uintptr_t>(q) % 16 || reinterpret_cast<uintptr_t>(w) % 16)
+        return fail(LHR_ERR_INVALID_ARG, "q and w must be 16-byte aligned");
+    if (nq < 1) return fail(LHR_ERR_INVALID_ARG, "nq must be >= 1");
+    if (k < 1 || k > 32) return fail(LHR_ERR_INVALID_ARG, "k must be in [1, 32]");
+    DeviceGuard g(db->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    Scratch scr;
+    cudaError_t e = scr.alloc(scan_weighted_scratch_bytes(db, nq, k), s);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+    e = launch_scan_weighted(db, q, nq, k, w, idx, dist, scr.ptr, s);
+    if (e != cudaSuccess) return cuda_fail(e, "weighted scan launch");
+    return LHR_OK;
+}
+
+lhr_status lhr_soft_forward(const lhr_db* db, const float* frames, const int32_t* offsets, int32_t W, int32_t nw,
+                            int32_t k, const float* w, const float* tau, int64_t* idx, float* dist, double* p,
+                            double* yhat, void* cuda_stream) {
+    lhr_status st = check_soft(db, k, w, tau);
+    if (st != LHR_OK) return st;
+    if (!frames || !offsets || !idx || !dist || !p || !yhat)
+        return fail(LHR_ERR_INVALID_ARG, "frames, offsets, idx, dist, p and yhat must be non-NULL");
+    if (reinterpret_cast<uintptr_t>(frames) % 16) return fail(LHR_ERR_INVALID_ARG, "frames must be 16-byte aligned");
+    if (W < 1 || nw < 1) return fail(LHR_ERR_INVALID_ARG, "W and nw must be >= 1");
+    DeviceGuard g(db->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    Scratch scr;
+    cudaError_t e = scr.alloc(scan_weighted_scratch_bytes(db, W, k), s);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+    if ((e = launch_scan_weighted(db, frames, W, k, w, idx, dist, scr.ptr, s)) != cudaSuccess)
+        return cuda_fail(e, "weighted scan launch");
+    if ((e = launch_soft_forward(db, frames, offsets, W, nw, k, w, tau, idx, dist, p, yhat, s)) != cudaSuccess)
+        return cuda_fail(e, "soft forward launch");
+    return LHR_OK;
+}
+
+lhr_status lhr_soft_backward(const lhr_db* db, const float* frames, const int32_t* offsets, int32_t W, int32_t nw,
+                             int32_t k, const float* w, const float* tau, const int64_t* idx, const float* dist,
+                             const double* p, const double* yhat, const double* g_yhat, float* dq, float* dw,
+                             float* dtau, void* cuda_stream) {
+    lhr_status st = check_soft(db, k, w, tau);
+    if (st != LHR_OK) return st;
+    if (!frames || !offsets || !idx || !dist || !p || !yhat || !g_yhat || !dq || !dw || !dtau)
+        return fail(LHR_ERR_INVALID_ARG, "every array argument must be non-NULL");
+    if (W < 1 || nw < 1) return fail(LHR_ERR_INVALID_ARG, "W and nw must be >= 1");
+    DeviceGuard g(db->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    Scratch scr;
+    cudaError_t e = scr.alloc(soft_backward_scratch_bytes(db, nw), s);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+    e = launch_soft_backward(db, frames, offsets, W, nw, k, w, tau, idx, dist, p, yhat, g_yhat, dq, dw, dtau, scr.ptr,
+                             s);
+    if (e != cudaSuccess) return cuda_fail(e, "soft backward launch");
+    return LHR_OK;
+}
+
+lhr_status lhr_loc_mse(const double* yhat, const double* y, int32_t nw, const double* scale, double* loss,
+                       double* grad, void* cuda_stream) {
+    if (!yhat || !y) return fail(LHR_ERR_INVALID_ARG, "yhat and y must be non-NULL");
+    if (!loss && !grad) return fail(LHR_ERR_INVALID_ARG, "ask for the loss, the gradient or both");
+    if (nw < 1) return fail(LHR_ERR_INVALID_ARG, "nw must be >= 1");
+    cudaError_t e = launch_loc_mse(yhat, y, nw, scale, loss, grad, reinterpret_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "location loss launch");
     return LHR_OK;
 }
 

@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct HierLayout {
-    size_t dcbuf, hist, ctl, bar, zero_end, bins, fkd, fkb, total;
+    size_t dcbuf, hist, ctl, bar, zero_end, bins, fkd, fkb, ctk, total;
 };
 
 HierLayout hlayout(const lhr_db* db, int nf) {
@@ -696,7 +696,8 @@ HierLayout hlayout(const lhr_db* db, int nf) {
     L.bins = a256(L.zero_end);
     L.fkd = a256(L.bins + (size_t)nf * kHBinCap * sizeof(u64));
     L.fkb = a256(L.fkd + (size_t)nf * kHMaxShort * sizeof(u64));
-    L.total = a256(L.fkb + (size_t)nf * kHBinCap * sizeof(u64));
+    L.ctk = a256(L.fkb + (size_t)nf * kHBinCap * sizeof(u64));
+    L.total = a256(L.ctk + (size_t)nf * 32 * sizeof(u64));
     return L;
 }
 
@@ -756,6 +757,7 @@ cudaError_t launch_hier_fused(const lhr_db* db, const float* q, int nq, int shor
     hp.bins = reinterpret_cast<u64*>(base + L.bins);
     hp.fkd = reinterpret_cast<u64*>(base + L.fkd);
     hp.fkb = reinterpret_cast<u64*>(base + L.fkb);
+    hp.ctk = agg_args ? reinterpret_cast<u64*>(base + L.ctk) : nullptr;  // tile keys only feed Algorithm 2
     hp.idx = idx;
     hp.dist = dist;
     hp.err = db->err;
@@ -766,6 +768,7 @@ cudaError_t launch_hier_fused(const lhr_db* db, const float* q, int nq, int shor
         hp.ap.n = db->n;
         hp.ap.rlim = (long long)floor(sqrt((double)agg_args->r2max)) + 1;
         hp.ap.err = db->err;
+        hp.ap.tile_keys = hp.ctk;  // written with the results, in the same slots as idx
     } else {
         hp.ap.a.nw = 0;
     }

@@ -34,6 +34,7 @@ struct lhr_db {
     float xnorm_max = 0.f;      // max over rows of ||x||^2
     float* Xc = nullptr;        // n x coarse_dim (coarse prefix slab), or nullptr
     int32_t* perm = nullptr;    // n, or nullptr
+    int32_t* iperm = nullptr;   // n: internal row of each caller row, or nullptr (with perm)
     // Caller's order.
     double* xy = nullptr;       // n x 2
     int32_t* tile = nullptr;    // n x 2 (tx, ty) = floor(xy / tile_m)
@@ -149,6 +150,18 @@ struct AggArgs {
 };
 cudaError_t launch_aggregate(const lhr_db* db, const AggArgs& a, cudaStream_t stream);
 long long circle_r2_limit(double radius_m, double tile_m);
+
+// Soft retrieval forward / backward and the location loss (soft.cu).
+size_t soft_backward_scratch_bytes(const lhr_db* db, int nw);
+cudaError_t launch_soft_forward(const lhr_db* db, const float* frames, const int32_t* offsets, int W, int nw, int k,
+                                const float* w, const float* tau, const int64_t* idx, const float* dist, double* p,
+                                double* yhat, cudaStream_t stream);
+cudaError_t launch_soft_backward(const lhr_db* db, const float* frames, const int32_t* offsets, int W, int nw, int k,
+                                 const float* w, const float* tau, const int64_t* idx, const float* dist,
+                                 const double* p, const double* yhat, const double* g, float* dq, float* dw,
+                                 float* dtau, void* scratch, cudaStream_t stream);
+cudaError_t launch_loc_mse(const double* yhat, const double* y, int nw, const double* scale, double* loss,
+                           double* grad, cudaStream_t stream);
 
 // Database construction helpers (build.cu).
 cudaError_t launch_build_derived(lhr_db* db, cudaStream_t stream);

@@ -1,0 +1,314 @@
+// Soft retrieval: a differentiable relaxation of the retrieval of §3.1 and the
+// aggregation of §3.2 (the paper itself has no gradient; this form lets
+// per-dimension feature weights w and a temperature tau be learned).
+//
+// Per window b of frames f (consecutive frames, offsets[b] .. offsets[b+1]):
+//   * each frame's top k rows per subspace are chosen by the weighted squared
+//     distance d_i = sum_j w_j (q_fj - x_ij)^2 (the weighted exhaustive scan,
+//     scan.cu); the choice is held fixed when differentiating;
+//   * logits l_i = -d_i / tau over all m n_s k candidates of the window (one
+//     joint softmax), p = softmax(l), y^_b = sum_i p_i xy_i (FP64 sums);
+//   * loss L = (1/B) sum_b ||y^_b - y_b||^2 (lhr_loc_mse).
+// Backward, with g_b = dL/dy^_b given:
+//   dL/dl_i  = p_i g_b . (xy_i - y^_b)
+//   dL/dd_i  = -(1/tau) dL/dl_i
+//   dL/dtau  = sum_i dL/dl_i d_i / tau^2
+//   dL/dw_j  = sum_i dL/dd_i (q_f(i)j - x_ij)^2
+//   dL/dq_fj = sum_{i in f} dL/dd_i 2 w_j (q_fj - x_ij)
+// The backward pass recomputes (q - x) from the rows instead of storing any
+// distance tile: one block per window gathers its m n_s k rows once.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace lhr {
+namespace {
+
+constexpr int kSoftThreads = 256;
+constexpr int kMaxSlots = 1024;  // candidate slots per frame (n_s k) the backward stages in shared memory
+
+template <typename T>
+__device__ T block_reduce(T v, T* red, bool is_max) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T u = __shfl_xor_sync(kFull, v, o);
+        v = is_max ? (u > v ? u : v) : v + u;
+    }
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T s = red[0];
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) s = is_max ? (red[i] > s ? red[i] : s) : s + red[i];
+        red[0] = s;
+    }
+    __syncthreads();
+    const T r = red[0];
+    __syncthreads();
+    return r;
+}
+
+struct SoftArgs {
+    const float* frames;    // W x D
+    const int32_t* offsets; // nw + 1
+    int W, nw, D, kc;       // kc = n_s k candidate slots per frame
+    const int64_t* idx;     // W x kc (caller's rows; -1 = padding)
+    const float* dist;      // W x kc weighted distances
+    const double* xy;       // n x 2 (caller's order)
+    const float* X;         // n x D (internal order)
+    const int32_t* iperm;   // caller row -> internal row, or nullptr
+    int64_t n;
+    const float* w;         // D
+    const float* tau;       // 1
+    double* p;              // W x kc softmax weights (forward output, backward input)
+    double* yhat;           // nw x 2
+    const double* g;        // nw x 2 dL/dy^
+    float* dq;              // W x D
+    double* dw_part;        // nw x D
+    double* dtau_part;      // nw
+    int* err;
+};
+
+__device__ __forceinline__ bool window_ok(const SoftArgs& a, int b, int& f0, int& f1) {
+    f0 = a.offsets[b];
+    f1 = a.offsets[b + 1];
+    return f0 >= 0 && f1 > f0 && f1 <= a.W;
+}
+
+// One block per window: the joint softmax over its candidates and y^.
+__global__ void __launch_bounds__(kSoftThreads) soft_forward_kernel(const SoftArgs a) {
+    __shared__ double red[kSoftThreads / 32];
+    const int b = blockIdx.x, t = threadIdx.x;
+    int f0, f1;
+    const double tau = (double)__ldg(a.tau);
+    const bool ok = window_ok(a, b, f0, f1) && tau > 0.0 && tau < INFINITY;
+    if (!ok) {
+        if (t == 0) {
+            record_error(a.err, kErrInvalidArg);
+            a.yhat[2 * b] = a.yhat[2 * b + 1] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+        return;
+    }
+    const int64_t c0 = (int64_t)f0 * a.kc, c1 = (int64_t)f1 * a.kc;
+    double mx = -INFINITY;
+    for (int64_t c = c0 + t; c < c1; c += kSoftThreads)
+        if (a.idx[c] >= 0) mx = fmax(mx, -(double)a.dist[c] / tau);
+    mx = block_reduce(mx, red, true);
+    double z = 0.0, sx = 0.0, sy = 0.0;
+    for (int64_t c = c0 + t; c < c1; c += kSoftThreads) {
+        const int64_t r = a.idx[c];
+        double e = 0.0;
+        if (r >= 0 && r < a.n) {
+            e = exp(-(double)a.dist[c] / tau - mx);
+            z += e;
+            sx += e * a.xy[2 * r];
+            sy += e * a.xy[2 * r + 1];
+        }
+        a.p[c] = e;
+    }
+    z = block_reduce(z, red, false);
+    sx = block_reduce(sx, red, false);
+    sy = block_reduce(sy, red, false);
+    if (!(z > 0.0)) {
+        if (t == 0) {
+            record_error(a.err, kErrInvalidArg);
+            a.yhat[2 * b] = a.yhat[2 * b + 1] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+        return;
+    }
+    for (int64_t c = c0 + t; c < c1; c += kSoftThreads) a.p[c] /= z;
+    if (t == 0) {
+        a.yhat[2 * b] = sx / z;
+        a.yhat[2 * b + 1] = sy / z;
+    }
+}
+
+// One block per window: dL/dd per candidate, then, frame by frame, the rows
+// are re-read once and dq, the window's share of dw and of dtau are formed.
+__global__ void __launch_bounds__(kSoftThreads) soft_backward_kernel(const SoftArgs a) {
+    __shared__ double red[kSoftThreads / 32];
+    __shared__ float dd_s[kMaxSlots];
+    __shared__ int row_s[kMaxSlots];
+    const int b = blockIdx.x, t = threadIdx.x;
+    const int D = a.D;
+    int f0, f1;
+    const double tau = (double)__ldg(a.tau);
+    if (!window_ok(a, b, f0, f1) || !(tau > 0.0 && tau < INFINITY)) {
+        for (int j = t; j < D; j += kSoftThreads) a.dw_part[(size_t)b * D + j] = 0.0;
+        if (t == 0) a.dtau_part[b] = 0.0;
+        return;
+    }
+    const double gx = a.g[2 * b], gy = a.g[2 * b + 1];
+    const double yx = a.yhat[2 * b], yy = a.yhat[2 * b + 1];
+    double dtau = 0.0;
+    float dw_acc[4] = {0.f, 0.f, 0.f, 0.f};  // dims t, t + 256, ... (D <= 1024)
+    for (int f = f0; f < f1; ++f) {
+        for (int s = t; s < a.kc; s += kSoftThreads) {
+            const int64_t c = (int64_t)f * a.kc + s;
+            const int64_t r = a.idx[c];
+            float dd = 0.f;
+            int ir = -1;
+            if (r >= 0 && r < a.n) {
+                const double dl = a.p[c] * (gx * (a.xy[2 * r] - yx) + gy * (a.xy[2 * r + 1] - yy));
+                dtau += dl * (double)a.dist[c] / (tau * tau);
+                dd = (float)(-dl / tau);
+                ir = a.iperm ? a.iperm[r] : (int)r;
+            }
+            dd_s[s] = dd;
+            row_s[s] = ir;
+        }
+        __syncthreads();
+        const float* q = a.frames + (size_t)f * D;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = t + u * kSoftThreads;
+            if (j >= D) break;
+            const float qj = q[j], wj = __ldg(a.w + j);
+            float gq = 0.f, gw = 0.f;
+            int s = 0;
+            for (; s + 4 <= a.kc; s += 4) {
+                float x[4];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) x[v] = row_s[s + v] >= 0 ? __ldg(a.X + (size_t)row_s[s + v] * D + j) : qj;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const float diff = qj - x[v];
+                    gq = fmaf(dd_s[s + v], diff, gq);
+                    gw = fmaf(dd_s[s + v] * diff, diff, gw);
+                }
+            }
+            for (; s < a.kc; ++s) {
+                const float x = row_s[s] >= 0 ? __ldg(a.X + (size_t)row_s[s] * D + j) : qj;
+                const float diff = qj - x;
+                gq = fmaf(dd_s[s], diff, gq);
+                gw = fmaf(dd_s[s] * diff, diff, gw);
+            }
+            a.dq[(size_t)f * D + j] = 2.f * wj * gq;
+            dw_acc[u] += gw;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int j = t + u * kSoftThreads;
+        if (j < D) a.dw_part[(size_t)b * D + j] = (double)dw_acc[u];
+    }
+    dtau = block_reduce(dtau, red, false);
+    if (t == 0) a.dtau_part[b] = dtau;
+}
+
+// dw_j = sum over windows (fixed order), dtau likewise (block 0).
+__global__ void __launch_bounds__(kSoftThreads) soft_reduce_kernel(const double* dw_part, const double* dtau_part,
+                                                                   int nw, int D, float* dw, float* dtau) {
+    const int j = blockIdx.x * kSoftThreads + threadIdx.x;
+    if (j < D) {
+        double s = 0.0;
+        for (int b = 0; b < nw; ++b) s += dw_part[(size_t)b * D + j];
+        dw[j] = (float)s;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < nw; ++b) s += dtau_part[b];
+        *dtau = (float)s;
+    }
+}
+
+// L = (1/B) sum_b ||y^_b - y_b||^2 and, scaled by *scale (1 if NULL),
+// dL/dy^_b = 2 (y^_b - y_b) / B.
+__global__ void __launch_bounds__(kSoftThreads) loc_mse_kernel(const double* yhat, const double* y, int nw,
+                                                               const double* scale, double* loss, double* grad) {
+    __shared__ double red[kSoftThreads / 32];
+    const double sc = scale ? *scale : 1.0;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nw; b += kSoftThreads) {
+        const double ex = yhat[2 * b] - y[2 * b], ey = yhat[2 * b + 1] - y[2 * b + 1];
+        s += ex * ex + ey * ey;
+        if (grad) {
+            grad[2 * b] = sc * 2.0 * ex / nw;
+            grad[2 * b + 1] = sc * 2.0 * ey / nw;
+        }
+    }
+    s = block_reduce(s, red, false);
+    if (loss && threadIdx.x == 0) *loss = s / nw;
+}
+
+}  // namespace
+
+size_t soft_backward_scratch_bytes(const lhr_db* db, int nw) {
+    return ((size_t)nw * db->dim + nw) * sizeof(double);
+}
+
+cudaError_t launch_soft_forward(const lhr_db* db, const float* frames, const int32_t* offsets, int W, int nw, int k,
+                                const float* w, const float* tau, const int64_t* idx, const float* dist, double* p,
+                                double* yhat, cudaStream_t stream) {
+    SoftArgs a{};
+    a.frames = frames;
+    a.offsets = offsets;
+    a.W = W;
+    a.nw = nw;
+    a.D = db->dim;
+    a.kc = db->n_sub * k;
+    a.idx = idx;
+    a.dist = dist;
+    a.xy = db->xy;
+    a.X = db->X;
+    a.iperm = db->iperm;
+    a.n = db->n;
+    a.w = w;
+    a.tau = tau;
+    a.p = p;
+    a.yhat = yhat;
+    a.err = db->err;
+    ProfScope ps("soft_forward_kernel", stream);
+    soft_forward_kernel<<<nw, kSoftThreads, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_soft_backward(const lhr_db* db, const float* frames, const int32_t* offsets, int W, int nw, int k,
+                                 const float* w, const float* tau, const int64_t* idx, const float* dist,
+                                 const double* p, const double* yhat, const double* g, float* dq, float* dw,
+                                 float* dtau, void* scratch, cudaStream_t stream) {
+    SoftArgs a{};
+    a.frames = frames;
+    a.offsets = offsets;
+    a.W = W;
+    a.nw = nw;
+    a.D = db->dim;
+    a.kc = db->n_sub * k;
+    a.idx = idx;
+    a.dist = dist;
+    a.xy = db->xy;
+    a.X = db->X;
+    a.iperm = db->iperm;
+    a.n = db->n;
+    a.w = w;
+    a.tau = tau;
+    a.p = const_cast<double*>(p);
+    a.yhat = const_cast<double*>(yhat);
+    a.g = g;
+    a.dq = dq;
+    a.dw_part = reinterpret_cast<double*>(scratch);
+    a.dtau_part = a.dw_part + (size_t)nw * db->dim;
+    a.err = db->err;
+    // frames outside every window keep a zero gradient
+    cudaError_t e = cudaMemsetAsync(dq, 0, (size_t)W * db->dim * sizeof(float), stream);
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps("soft_backward_kernel", stream);
+        soft_backward_kernel<<<nw, kSoftThreads, 0, stream>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    soft_reduce_kernel<<<(db->dim + kSoftThreads - 1) / kSoftThreads, kSoftThreads, 0, stream>>>(
+        a.dw_part, a.dtau_part, nw, db->dim, dw, dtau);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loc_mse(const double* yhat, const double* y, int nw, const double* scale, double* loss,
+                           double* grad, cudaStream_t stream) {
+    loc_mse_kernel<<<1, kSoftThreads, 0, stream>>>(yhat, y, nw, scale, loss, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace lhr

@@ -14,6 +14,8 @@ from .floorplan import (  # noqa: F401
     make_database,
     make_point_queries,
     make_windows,
+    db_seed,
+    query_seed,
     path_length,
     path_positions,
 )

@@ -26,11 +26,12 @@ def _sep(d, r):
     return left and right
 
 
-def check_list(q, X, g_idx, g_dist, o_idx, o_dist, k, rows=None, where=""):
+def check_list(q, X, g_idx, g_dist, o_idx, o_dist, k, rows=None, where="", w=None):
     """One query's GPU list (k entries) against the oracle's top-(k+1) list.
 
     ``rows`` restricts the candidate rows (a subspace); ``o_idx``/``o_dist``
-    must hold at least k entries (k+1 when available) in oracle order.
+    must hold at least k entries (k+1 when available) in oracle order; ``w``
+    are per-dimension distance weights (None = 1).
     Returns the number of positions compared bit-exactly.
     """
     g_idx = np.asarray(g_idx)
@@ -46,7 +47,7 @@ def check_list(q, X, g_idx, g_dist, o_idx, o_dist, k, rows=None, where=""):
     assert len(set(gi.tolist())) == n_avail, f"{where}: duplicate rows"
     if rows is not None:
         assert np.isin(gi, rows).all(), f"{where}: row outside the subspace"
-    exact = oret.sq_dist(q, X[gi])
+    exact = oret.sq_dist(q, X[gi], w)
     err = np.abs(g_dist[:n_avail] - exact)
     assert np.all(err <= DIST_RTOL * exact + 1e-7), \
         f"{where}: distance error {np.max(err / np.maximum(exact, 1e-12)):.3g} rel"
