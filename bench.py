@@ -532,6 +532,117 @@ def run_precision(args, rank, world, local):
     return out
 
 
+def run_differentiation(args, rank, world, local):
+    """N = 200,000 x 256 database, B = 256 windows of m = 5 frames, k = 32,
+    w = 1, tau = 0.1: one step is the soft retrieval's forward (weighted
+    selection + window softmax), the location loss, and the backward (dq, dw,
+    dtau), through the autograd functions a user calls."""
+    import torch
+    import paper_2006_08861_gb300 as lhr
+    import synth
+    from oracle import soft
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    c = synth.CONFIGS["differentiation"]
+    db = synth.make_database(c["n"], c["dim"], seed=synth.db_seed(c["index"]))
+    B, m, k = c["nw"], c["m"], c["k"]
+    n_sets = 2
+    win = synth.make_windows(db, B * n_sets, m, seed=synth.query_seed(c["index"]) + 7919 * rank)
+    h = lhr.lhr_build_db(db.feats, db.xy)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    frames_all = torch.from_numpy(win.frames).to(dev)
+    y_all = torch.from_numpy(win.true_xy.astype(np.float64)).to(dev)
+    offs = torch.arange(0, (B + 1) * m, m, dtype=torch.int32, device=dev)
+    w = torch.ones(c["dim"], dtype=torch.float32, device=dev, requires_grad=True)
+    tau = torch.full((1,), 0.1, dtype=torch.float32, device=dev, requires_grad=True)
+
+    def step(i):
+        j = i % n_sets
+        fr = frames_all[j * B * m:(j + 1) * B * m].clone().requires_grad_(True)
+        yhat = lhr.soft_retrieval(h, fr, offs, w, tau, k)
+        loss = lhr.loc_mse(yhat, y_all[j * B:(j + 1) * B])
+        loss.backward()
+        return loss, fr
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = []
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier(world)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(args.warmup + i)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    tot = max_over_ranks(sum(ms), world)
+    # per-kernel shares in an instrumented pass
+    lhr.lhr_profile_read(None, reset=True)
+    lhr.lhr_profile_enable(True)
+    for i in range(args.steps):
+        flush.zero_()
+        step(i)
+    torch.cuda.synchronize()
+    lhr.lhr_profile_enable(False)
+    share = {}
+    for name in ("wnorm_kernel", "scan_pilot", "scan_topk_kernel", "soft_forward_kernel", "soft_backward_kernel"):
+        n_l, t_ms = lhr.lhr_profile_read(name, reset=True)
+        if n_l:
+            share[name] = (n_l, t_ms)
+    n_scan, t_scan = share.get("scan_topk_kernel", (1, float("nan")))
+    # the selection is FP32 SIMT arithmetic: 3 flops per (frame, row, dim) (sub, fma)
+    flops = 3.0 * B * m * c["n"] * c["dim"]
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock (GHz), TFLOP/s
+    achieved = 2.0 * B * m * c["n"] * c["dim"] / (t_scan / n_scan / 1e3) / 1e12
+    # gradient check of one window against the FP64 oracle (selection from the GPU)
+    loss, fr = step(0)
+    g_fr = fr.grad.detach().cpu().numpy()
+    idx = lhr.lhr_soft_forward(h, frames_all[:B * m], offs, k, w.detach(), tau.detach())[0].cpu().numpy()[:, 0]
+    ref = soft.forward_backward(win.frames[:m], np.array([0, m], np.int32), db.feats, db.xy,
+                                win.true_xy[:1].astype(np.float64), np.ones(c["dim"]), float(np.float32(0.1)),
+                                idx=idx[:m])
+    dq_err = float(np.max(np.abs(g_fr[:m] - ref["dq"] / B)) / max(np.max(np.abs(ref["dq"] / B)), 1e-30))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        soft.forward_backward(win.frames[:m], np.array([0, m], np.int32), db.feats, db.xy,
+                              win.true_xy[:1].astype(np.float64), np.ones(c["dim"]), 0.1, k=k)
+        el = time.perf_counter() - t0
+        cpu = {"value": round(1.0 / el, 4), "unit": "windows/s (fwd+bwd)", "cores": 1, "kind": "oracle",
+               "sample": "1 window of 5 frames: exhaustive FP64 weighted selection over 200,000 rows, softmax, "
+                         "analytic gradients (numpy, one thread)"}
+    tot_all = sum(v[1] for v in share.values())
+    out = {
+        "metric": METRIC, "value": round(B * args.steps * world / (tot / 1e3), 1), "unit": "windows/s (fwd+bwd)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "differentiation", "desc": "N=200000 D=256, B=256 windows of m=5, k=32, w=1, "
+                                                          "tau=0.1: soft retrieval forward + location loss + backward",
+                   "l2": "flushed before every timed step", "launch": "eager (autograd)"},
+        "roofline": {"bound": "alu", "kernel": "scan_topk_kernel (weighted selection)",
+                     "achieved": round(achieved, 2), "peak": round(alu_peak, 1),
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (derived)", "unit": "TFLOP/s",
+                     "frac": round(achieved / alu_peak, 4), "traffic": None,
+                     "avg_launch_us": round(t_scan / n_scan * 1e3, 1),
+                     "algorithmic_flops_per_launch": 2.0 * B * m * c["n"] * c["dim"],
+                     "kernel_share": {n: round(v[1] / tot_all, 4) for n, v in share.items()}},
+        "grad_check": {"dq_max_rel_err_vs_fp64_window0": dq_err, "loss": float(loss.item())},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "gpu_launches": round(sum(v[0] for v in share.values()) / args.steps) + 2,
+    }
+    h.close()
+    return out
+
+
 def run_reference(args, spec, rank, world):
     """The FP64 oracle as the reference arm: each step is a bounded sample."""
     if rank != 0:
@@ -564,7 +675,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="hierarchical", choices=["hierarchical", "tiny", "hbm_scan", "precision"])
+    ap.add_argument("--workload", default="hierarchical",
+                    choices=["hierarchical", "tiny", "hbm_scan", "precision", "differentiation"])
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
@@ -579,11 +691,12 @@ def main(argv=None):
             import torch
             torch.cuda.set_device(local)
         dist.init_process_group(backend)
-    if args.workload == "precision":
-        out = None if args.impl == "reference" else run_precision(args, rank, world, local)
+    if args.workload in ("precision", "differentiation"):
+        run = run_precision if args.workload == "precision" else run_differentiation
+        out = None if args.impl == "reference" else run(args, rank, world, local)
         if args.impl == "reference" and rank == 0:
-            out = {"impl": "reference", "unavailable": "the precision workload's reference arm is the FP64 oracle; "
-                                                       "run --workload hierarchical for the timed reference"}
+            out = {"impl": "reference", "unavailable": f"the {args.workload} workload's reference arm is the FP64 "
+                                                       "oracle; run --workload hierarchical for the timed reference"}
     else:
         spec = workload_spec(args.workload)
         if args.impl == "reference":

@@ -267,6 +267,59 @@ lhr_status lhr_loc_mse(const double* yhat, const double* y, int32_t nw, const do
                        double* grad, void* cuda_stream);
 
 /*
+ * Serving runtime (no counterpart in the paper's own system, which localizes
+ * one user at a time): continuous batching of requests from many concurrent
+ * user streams. Each submitted frame is retrieved once (lhr_query's path for
+ * `shortlist`) and its top k is cached in the stream's device ring; a request
+ * for the stream's last m frames (Algorithm 2, §3.2) gathers the cached
+ * candidates. A scheduler thread forms ticks of up to max_batch_frames queued
+ * frames, oldest first, and launches each on one of n_lanes CUDA streams when
+ * a lane is free and the tick's scratch fits mem_budget_bytes beside the ticks
+ * in flight, so ticks overlap on the device. Results equal lhr_query /
+ * lhr_aggregate_2d on the same frames: batching changes the schedule only.
+ */
+typedef struct lhr_server lhr_server;
+typedef struct {
+    int32_t n_streams;        /* user streams, ids 0 .. n_streams - 1 */
+    int32_t max_window;       /* longest window m a request may ask for (>= 1) */
+    int32_t ring_frames;      /* frames (and top-k lists) kept per stream on the device, > max_window */
+    int32_t max_batch_frames; /* frames per tick, i.e. per retrieval launch (>= 1) */
+    int32_t n_lanes;          /* CUDA streams the ticks rotate over (>= 2) */
+    int32_t k;                /* top k per frame and subspace (1 .. 32) */
+    int32_t shortlist;        /* 0: exhaustive FP32 scan; S: coarse-to-fine (the db needs a coarse level) */
+    int32_t reserved;         /* 0 */
+    int64_t mem_budget_bytes; /* device scratch the ticks in flight may hold together (> 0) */
+    lhr_agg_params agg;       /* Algorithm 2 parameters of every window */
+} lhr_server_config;
+
+typedef struct {
+    int64_t request_id; /* as submitted */
+    int32_t stream_id;
+    int32_t m;          /* frames in the window (fewer than asked when the stream had fewer) */
+    int32_t status;     /* LHR_OK, LHR_WARN_LOW_CONFIDENCE or an error */
+    int32_t reserved;
+    double xy[2];       /* the window's position, metres */
+    double latency_us;  /* submission of the window's last frame -> result on the host */
+} lhr_server_result;
+
+/* Allocates the rings and lanes and starts the scheduler thread. db must
+ * outlive the server. */
+lhr_status lhr_server_create(const lhr_db* db, const lhr_server_config* cfg, lhr_server** out);
+/* Queues one frame (D float32, host memory, copied before return) of a stream;
+ * window_m > 0 also requests the position of the stream's last window_m frames
+ * (this one included). Thread-safe; never blocks on the GPU. */
+lhr_status lhr_server_submit(lhr_server* s, int32_t stream_id, const float* frame, int32_t window_m,
+                             int64_t request_id);
+/* Moves up to max_results finished windows into out (waiting up to wait_ms
+ * for the first); *n_out receives the count. LHR_ERR_CUDA once a tick failed. */
+lhr_status lhr_server_poll(lhr_server* s, lhr_server_result* out, int32_t max_results, int32_t* n_out,
+                           int32_t wait_ms);
+/* Waits until every submitted frame is processed (LHR_ERR_TIMEOUT after timeout_ms). */
+lhr_status lhr_server_drain(lhr_server* s, int32_t timeout_ms);
+/* Finishes queued work, stops the scheduler and frees everything. */
+lhr_status lhr_server_destroy(lhr_server* s);
+
+/*
  * Instrumentation (no counterpart in the paper): per-kernel CUDA-event timing.
  * lhr_profile_enable(1) makes every later launch record an event pair on its
  * stream around each kernel; lhr_profile_read synchronizes those events and

@@ -49,6 +49,19 @@ class AggParams(ctypes.Structure):
                 ("toler_pct", ctypes.c_int32), ("tau", ctypes.c_float)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int32), ("max_window", ctypes.c_int32), ("ring_frames", ctypes.c_int32),
+                ("max_batch_frames", ctypes.c_int32), ("n_lanes", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("shortlist", ctypes.c_int32), ("reserved", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64),
+                ("agg", AggParams)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_int64), ("stream_id", ctypes.c_int32), ("m", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("xy", ctypes.c_double * 2),
+                ("latency_us", ctypes.c_double)]
+
+
 class LhrError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"lhr status {status}: {msg}")
@@ -75,6 +88,11 @@ def _load():
         "lhr_soft_forward": [P, P, P, I32, I32, I32, P, P, P, P, P, P, P],
         "lhr_soft_backward": [P, P, P, I32, I32, I32, P, P, P, P, P, P, P, P, P, P, P],
         "lhr_loc_mse": [P, P, I32, P, P, P, P],
+        "lhr_server_create": [P, ctypes.POINTER(ServerConfig), ctypes.POINTER(P)],
+        "lhr_server_submit": [P, I32, P, I32, I64],
+        "lhr_server_poll": [P, ctypes.POINTER(ServerResult), I32, ctypes.POINTER(I32), I32],
+        "lhr_server_drain": [P, I32],
+        "lhr_server_destroy": [P],
         "lhr_profile_enable": [I32],
         "lhr_profile_read": [ctypes.c_char_p, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double), I32],
     }
@@ -402,3 +420,72 @@ def loc_mse(yhat, y):
     if _AUTOGRAD is None:
         _AUTOGRAD = _make_autograd()
     return _AUTOGRAD[1].apply(yhat, y)
+
+
+# ------------------------------------------------------------------ serving
+class Server:
+    """Continuous-batching request loop over one database (lhr_server_*).
+
+    submit() queues one frame of a user stream (a float32 host array of D
+    values) and optionally asks for the position of that stream's last m
+    frames; poll() returns finished windows as dicts (request_id, stream_id,
+    m, status, xy, latency_us)."""
+
+    def __init__(self, db: Database, n_streams: int, max_window: int, k: int, shortlist: int = 0,
+                 ring_frames: int | None = None, max_batch_frames: int = 64, n_lanes: int = 2,
+                 mem_budget_bytes: int = 1 << 30, mode: str = "tile", top_c: int = 10, radius_m: float = 3.0,
+                 toler_pct: int = 20, tau: float = 1.0):
+        self.db = db
+        ring = ring_frames if ring_frames is not None else 2 * max_window + max_batch_frames
+        cfg = ServerConfig(n_streams, max_window, ring, max_batch_frames, n_lanes, k, shortlist, 0,
+                           mem_budget_bytes, agg_params(mode, top_c, radius_m, toler_pct, tau))
+        h = ctypes.c_void_p()
+        _check(_lib.lhr_server_create(db.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._buf = (ServerResult * 4096)()
+
+    def submit(self, stream_id: int, frame, window_m: int = 0, request_id: int = -1):
+        f = np.ascontiguousarray(frame, dtype=np.float32)
+        if f.size != self.db.dim:
+            raise ValueError(f"frame must hold {self.db.dim} values")
+        _check(_lib.lhr_server_submit(self._h, stream_id, ctypes.c_void_p(f.ctypes.data), window_m, request_id))
+
+    def poll(self, wait_ms: int = 0, max_results: int = 4096):
+        n = ctypes.c_int32()
+        _check(_lib.lhr_server_poll(self._h, self._buf, min(max_results, 4096), ctypes.byref(n), wait_ms))
+        return [dict(request_id=r.request_id, stream_id=r.stream_id, m=r.m, status=r.status,
+                     xy=(r.xy[0], r.xy[1]), latency_us=r.latency_us) for r in self._buf[:n.value]]
+
+    def drain(self, timeout_ms: int = 60000):
+        _check(_lib.lhr_server_drain(self._h, timeout_ms))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lhr_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lhr_server_create(db: Database, **cfg) -> Server:
+    return Server(db, **cfg)
+
+
+def lhr_server_submit(server: Server, stream_id: int, frame, window_m: int = 0, request_id: int = -1):
+    server.submit(stream_id, frame, window_m, request_id)
+
+
+def lhr_server_poll(server: Server, wait_ms: int = 0, max_results: int = 4096):
+    return server.poll(wait_ms, max_results)
+
+
+def lhr_server_drain(server: Server, timeout_ms: int = 60000):
+    server.drain(timeout_ms)
+
+
+def lhr_server_destroy(server: Server):
+    server.close()

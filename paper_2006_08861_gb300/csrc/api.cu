@@ -140,7 +140,7 @@ static cudaError_t dalloc(T** p, size_t count) {
     return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count * sizeof(T), 16));
 }
 
-static lhr_status check_query_params(const lhr_db* db, const lhr_query_params* p) {
+lhr_status check_query_params(const lhr_db* db, const lhr_query_params* p) {
     if (!p) return fail(LHR_ERR_INVALID_ARG, "query params are NULL");
     if (p->k < 1 || p->k > 32) return fail(LHR_ERR_INVALID_ARG, "k must be in [1, 32]");
     if (p->shortlist < 0) return fail(LHR_ERR_INVALID_ARG, "shortlist must be >= 0");
@@ -164,8 +164,8 @@ static lhr_status check_query_params(const lhr_db* db, const lhr_query_params* p
 }
 
 // Retrieval for `nq` frames into idx/dist ([nq][n_sub][k]).
-static lhr_status run_retrieval(const lhr_db* db, const float* q, int nq, const lhr_query_params* p, int64_t* idx,
-                                float* dist, cudaStream_t s) {
+lhr_status run_retrieval(const lhr_db* db, const float* q, int nq, const lhr_query_params* p, int64_t* idx,
+                         float* dist, cudaStream_t s) {
     Scratch scr;
     cudaError_t e;
     if (p->score != LHR_F32) {
@@ -193,7 +193,7 @@ static lhr_status run_retrieval(const lhr_db* db, const float* q, int nq, const 
     return LHR_OK;
 }
 
-static lhr_status check_agg_params(const lhr_agg_params* a) {
+lhr_status check_agg_params(const lhr_agg_params* a) {
     if (!a) return fail(LHR_ERR_INVALID_ARG, "aggregation params are NULL");
     if (a->mode != LHR_AGG_TILE && a->mode != LHR_AGG_TILE_CENTROID && a->mode != LHR_AGG_SOFTMAX)
         return fail(LHR_ERR_INVALID_ARG, "unknown aggregation mode");
@@ -205,7 +205,7 @@ static lhr_status check_agg_params(const lhr_agg_params* a) {
     return LHR_OK;
 }
 
-static AggArgs make_agg(const lhr_db* db, const lhr_agg_params* a) {
+AggArgs make_agg(const lhr_db* db, const lhr_agg_params* a) {
     AggArgs g{};
     g.mode = (int)a->mode;
     g.top_c = a->top_c;

@@ -149,6 +149,15 @@ struct AggArgs {
     int32_t* status;
 };
 cudaError_t launch_aggregate(const lhr_db* db, const AggArgs& a, cudaStream_t stream);
+
+// Request plumbing of the C ABI (api.cu), shared with the serving runtime.
+lhr_status check_query_params(const lhr_db* db, const lhr_query_params* p);
+lhr_status check_agg_params(const lhr_agg_params* a);
+AggArgs make_agg(const lhr_db* db, const lhr_agg_params* a);
+// Retrieval for nq frames with the path p selects (fused, coarse-to-fine,
+// exhaustive or low-precision); scratch from the stream-ordered pool.
+lhr_status run_retrieval(const lhr_db* db, const float* q, int nq, const lhr_query_params* p, int64_t* idx,
+                         float* dist, cudaStream_t s);
 long long circle_r2_limit(double radius_m, double tile_m);
 
 // Soft retrieval forward / backward and the location loss (soft.cu).

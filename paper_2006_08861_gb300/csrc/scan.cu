@@ -627,7 +627,7 @@ size_t pass_bytes(const ScanConfig& c, int nchunks, int n_sub, int nq, int k) {
            align256(nqb * c.qb * (size_t)n_sub * sizeof(unsigned));
 }
 
-constexpr int kPilotMaxFrames = 256;  // larger requests scan without the pilot
+constexpr int kPilotMaxFrames = 4096;  // larger requests scan without the pilot
 
 bool use_pilot(const lhr_db* db, int nq) { return db->Xp != nullptr && nq <= kPilotMaxFrames; }
 

@@ -46,3 +46,26 @@ def test_circle_limit_host_rule_matches_paper_constants():
     # 30 cm tiles must give 10 tiles, squared 100 (§3.2).
     from oracle.aggregate import circle_r2_limit
     assert circle_r2_limit(3.0, 0.3) == 100
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the ctypes mirrors of the ABI structs have the C compiler's sizes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "lhr.h"\nint main(void) { printf("%zu %zu %zu %zu %zu", '
+                   'sizeof(lhr_db_config), sizeof(lhr_query_params), sizeof(lhr_agg_params), '
+                   'sizeof(lhr_server_config), sizeof(lhr_server_result)); return 0; }\n')
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    import __graft_entry__
+    __graft_entry__._build_ext().build()
+    import paper_2006_08861_gb300 as lhr
+    want = [ctypes.sizeof(c) for c in (lhr.DbConfig, lhr.QueryParams, lhr.AggParams, lhr.ServerConfig,
+                                       lhr.ServerResult)]
+    assert got == want
