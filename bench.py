@@ -643,6 +643,114 @@ def run_differentiation(args, rank, world, local):
     return out
 
 
+def run_serving(args, rank, world, local):
+    """N = 1,000,000 x 256 database (coarse prefix 32, shortlist 512, k = 20,
+    Algorithm 2 tile mode); 64 user streams, each sending frames with
+    exponential inter-arrival times (15 frames/s per stream) and asking, with
+    every frame, for the position of its last m frames, m uniform in 3..10.
+    The server batches continuously; the arrivals are replayed at 1x, 10x and
+    100x speed and all at once (saturation). Beside it, the per-request path:
+    each window alone through lhr_query_window, one after another."""
+    import torch
+    import paper_2006_08861_gb300 as lhr
+    import synth
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    c = synth.CONFIGS["serving"]
+    db = synth.make_database(c["n"], c["dim"], seed=synth.db_seed(c["index"]))
+    h = lhr.lhr_build_db(db.feats, db.xy, coarse_dim=32)
+    n_streams, fps, k, S = c["streams"], c["fps"], c["k"], 512
+    rng = np.random.default_rng(synth.query_seed(c["index"]) + 7919 * rank)
+    per_stream = 64
+    walks = [synth.make_windows(db, 1, per_stream, seed=synth.query_seed(c["index"]) + 100 * s + 7919 * rank).frames
+             for s in range(n_streams)]
+    # arrival schedule: (time s, stream, frame index, window m)
+    events = []
+    for s in range(n_streams):
+        t = 0.0
+        for f in range(per_stream):
+            t += rng.exponential(1.0 / fps)
+            events.append((t, s, f, int(rng.integers(c["m_lo"], c["m_hi"] + 1))))
+    events.sort()
+    levels = {}
+
+    def run_level(speed):
+        srv = lhr.Server(h, n_streams=n_streams, max_window=c["m_hi"], k=k, shortlist=S, max_batch_frames=64,
+                         n_lanes=3, mem_budget_bytes=2 << 30)
+        t0 = time.perf_counter()
+        for i, (t, s, f, m) in enumerate(events):
+            if speed is not None:
+                due = t0 + t / speed
+                while True:
+                    now = time.perf_counter()
+                    if now >= due:
+                        break
+                    if due - now > 2e-4:
+                        time.sleep(due - now - 1e-4)
+            srv.submit(s, walks[s][f], window_m=m, request_id=i)
+        srv.drain(600000)
+        el = time.perf_counter() - t0
+        res = srv.poll(max_results=4096)
+        while len(res) < len(events):
+            more = srv.poll(wait_ms=100)
+            if not more:
+                break
+            res += more
+        srv.close()
+        lat = sorted(r["latency_us"] for r in res)
+        offered = None if speed is None else round(n_streams * fps * speed, 1)
+        return {"windows_per_s": round(len(res) / el, 1), "offered_windows_per_s": offered,
+                "p50_us": round(lat[len(lat) // 2], 1), "p99_us": round(lat[int(len(lat) * 0.99)], 1),
+                "windows": len(res)}
+
+    run_level(None)  # warm: pools, function attributes
+    clocks = ClockSampler(local)
+    clocks.start()
+    for name, speed in (("1x", 1.0), ("10x", 10.0), ("100x", 100.0), ("saturation", None)):
+        if name == "1x" and args.steps < 10:
+            continue  # the real-time replay takes the schedule's length (about 4 s); skipped on short runs
+        levels[name] = run_level(speed)
+    clk = clocks.stop()
+    # per-request path: every window alone, synchronously, on a sample of the schedule
+    sample = events[:min(len(events), 400)]
+    lat = []
+    offs = torch.tensor([0, 0], dtype=torch.int32, device=dev)
+    frames_dev = [torch.from_numpy(w).to(dev) for w in walks]
+    t0 = time.perf_counter()
+    for (t, s, f, m) in sample:
+        lo = max(0, f - m + 1)
+        offs[1] = f + 1 - lo
+        a = time.perf_counter()
+        lhr.lhr_query_window(h, frames_dev[s][lo:f + 1], offs, k, shortlist=S)
+        torch.cuda.synchronize()
+        lat.append((time.perf_counter() - a) * 1e6)
+    el = time.perf_counter() - t0
+    lat.sort()
+    per_req = {"windows_per_s": round(len(sample) / el, 1), "p50_us": round(lat[len(lat) // 2], 1),
+               "p99_us": round(lat[int(len(lat) * 0.99)], 1), "windows": len(sample),
+               "path": "lhr_query_window per window, synchronous, coarse-to-fine FP32"}
+    sat = levels["saturation"]
+    total = max_over_ranks(len(events) / sat["windows_per_s"], world)
+    out = {
+        "metric": METRIC, "value": round(len(events) * world / total, 1), "unit": "windows/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 / sat["windows_per_s"], 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving", "desc": "N=1000000 D=256, coarse prefix 32, shortlist 512, k=20; 64 "
+                                                  "streams x 15 fps, Poisson arrivals, window m uniform 3..10 per "
+                                                  "request, one window per frame; continuous batching (<= 64 "
+                                                  "frames per tick, 3 lanes)",
+                   "value_is": "saturation throughput (all arrivals at once)"},
+        "load_levels": levels, "per_request_fp32": per_req,
+        "latency_us": {"p50": sat["p50_us"], "p99": sat["p99_us"], "what": "submit -> result on the host, saturation"},
+        "clocks": clk, "cpu_baseline": None,
+        "gpu_launches": None,
+    }
+    h.close()
+    return out
+
+
 def run_reference(args, spec, rank, world):
     """The FP64 oracle as the reference arm: each step is a bounded sample."""
     if rank != 0:
@@ -676,7 +784,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="hierarchical",
-                    choices=["hierarchical", "tiny", "hbm_scan", "precision", "differentiation"])
+                    choices=["hierarchical", "tiny", "hbm_scan", "precision", "differentiation", "serving"])
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
@@ -691,8 +799,9 @@ def main(argv=None):
             import torch
             torch.cuda.set_device(local)
         dist.init_process_group(backend)
-    if args.workload in ("precision", "differentiation"):
-        run = run_precision if args.workload == "precision" else run_differentiation
+    if args.workload in ("precision", "differentiation", "serving"):
+        run = {"precision": run_precision, "differentiation": run_differentiation,
+               "serving": run_serving}[args.workload]
         out = None if args.impl == "reference" else run(args, rank, world, local)
         if args.impl == "reference" and rank == 0:
             out = {"impl": "reference", "unavailable": f"the {args.workload} workload's reference arm is the FP64 "
