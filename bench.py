@@ -37,6 +37,12 @@ if ROOT not in sys.path:
 
 METRIC = "queries/s and % of HBM/TC roofline, low-precision vs FP32 at recall@k≥0.999; p99"
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each workload's dominant
+# kernel, from one ncu capture of the current kernel: hier_fused_kernel on this very workload;
+# scan_topk_kernel on 500,000 x 256 rows (518.4 MB), scaled by rows to the 2,000,000-row launch.
+# Re-measure (or set None) whenever the kernel changes.
+TRAFFIC = {"hierarchical": ("hier_fused_kernel", 14.02e6), "hbm_scan": ("scan_topk_kernel", 4 * 518.4e6)}
+
 
 # ------------------------------------------------------------------ ranks
 def dist_env():
@@ -348,7 +354,9 @@ def run_ours(args, spec, rank, world, local):
     achieved = alg_bytes / avg_s / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak,
                 "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
-                "traffic": None, "avg_launch_us": round(avg_s * 1e6, 3),
+                "traffic": (TRAFFIC[spec["name"]][1] if spec["name"] in TRAFFIC and TRAFFIC[spec["name"]][0] == dom
+                            else None),
+                "avg_launch_us": round(avg_s * 1e6, 3),
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel_share": {n: round(v[1] / sum(x[1] for x in kern.values()), 4) for n, v in kern.items()}}
 

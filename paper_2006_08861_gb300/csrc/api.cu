@@ -373,7 +373,7 @@ lhr_status lhr_build_db(const float* feats, const double* xy, const int32_t* sub
     // Scan partition: about one chunk per SM over the whole database, never
     // crossing a subspace boundary.
     int64_t cr = (n + db->sms - 1) / db->sms;
-    cr = std::max<int64_t>(32, (cr + 15) / 16 * 16);
+    cr = std::max<int64_t>(256, (cr + 15) / 16 * 16);  // small databases: fewer, longer chunks (short merge tail)
     db->chunk_rows = (int)cr;
     std::vector<int4> chunks;
     db->chunk_off_h.assign(db->n_sub + 1, 0);

@@ -56,6 +56,7 @@ constexpr int kTile = 128;        // queries per CTA (UMMA M) and rows per tile 
 constexpr int kSliceBytes = 128;  // K bytes per smem row (one 128-byte swizzle atom)
 constexpr int kSliceTile = kTile * kSliceBytes;  // 16 KB per tile slice
 constexpr int kStages = 6;
+constexpr int kSnSlots = 8;       // (s_j, n_j) tiles in flight: deeper than the operand ring, so never its limit
 constexpr int kBuf = 32;          // survivor buffer entries per epilogue thread
 constexpr int kThreads = 192;
 
@@ -233,8 +234,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = smem;                                   // slices x 16 KB
     unsigned char* sB = sA + (size_t)p.slices * kSliceTile;     // kStages x 16 KB
-    float2* sSN = reinterpret_cast<float2*>(sB + (size_t)kStages * kSliceTile);  // 2 x 128
-    u64* sBuf = reinterpret_cast<u64*>(sSN + 2 * kTile);        // main / full pass: kBuf x 128 (slot-major)
+    float2* sSN = reinterpret_cast<float2*>(sB + (size_t)kStages * kSliceTile);  // kSnSlots x 128
+    u64* sBuf = reinterpret_cast<u64*>(sSN + kSnSlots * kTile);  // main / full pass: kBuf x 128 (slot-major)
     u64* bars = MODE != kModePilot ? sBuf + kBuf * kTile : sBuf;
     u64* full = bars;
     u64* empty = full + kStages;
@@ -242,8 +243,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     u64* acc_full = a_full + 1;
     u64* acc_empty = acc_full + 2;
     u64* sn_full = acc_empty + 2;
-    u64* sn_empty = sn_full + 2;
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sn_empty + 2);
+    u64* sn_empty = sn_full + kSnSlots;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sn_empty + kSnSlots);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
     const int64_t row0 = (int64_t)chunk * p.chunk_rows;
@@ -263,6 +264,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = 0; i < 2; ++i) {
             mbar_init(&acc_full[i], 1);
             mbar_init(&acc_empty[i], 4);
+        }
+        for (int i = 0; i < kSnSlots; ++i) {
             mbar_init(&sn_full[i], 1);
             mbar_init(&sn_empty[i], 4);
         }
@@ -286,10 +289,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_arrive_expect_tx(a_full, (uint32_t)p.slices * kSliceTile);
             for (int s = 0; s < p.slices; ++s)
                 tma_load_2d(sA + (size_t)s * kSliceTile, &tmA, s * kElemPerSlice, qblock * kTile, a_full);
+            int sn_issued = 0, b_issued = 0;
             for (int t = 0; t < ntiles && !*abort_flag; ++t) {
                 const int64_t r = row0 + (int64_t)t * kTile;
-                const int slot = t & 1;
-                if (!mbar_wait(&sn_empty[slot], (uint32_t)((t >> 1) & 1) ^ 1u, abort_flag)) {
+                const int slot = t % kSnSlots;
+                if (!mbar_wait(&sn_empty[slot], (uint32_t)((t / kSnSlots) & 1) ^ 1u, abort_flag)) {
                     *abort_flag = 1;
                     record_error(p.err, kErrTimeout);
                     break;
@@ -298,6 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t snb = (uint32_t)((nr + 1) / 2) * 16u;
                 mbar_arrive_expect_tx(&sn_full[slot], snb);
                 bulk_g2s(sSN + slot * kTile, p.sn + r, snb, &sn_full[slot]);
+                ++sn_issued;
                 for (int s = 0; s < p.slices; ++s) {
                     const int it = t * p.slices + s;
                     const int st = it % kStages;
@@ -308,7 +313,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     mbar_arrive_expect_tx(&full[st], kSliceTile);
                     tma_load_2d(sB + (size_t)st * kSliceTile, &tmB, s * kElemPerSlice, (int)r, &full[st]);
+                    ++b_issued;
                 }
+            }
+            if (*abort_flag) {
+                // let this thread's copies still in flight land before the CTA exits (bounded waits)
+                mbar_wait(a_full, 0u, nullptr);
+                for (int t = sn_issued > kSnSlots ? sn_issued - kSnSlots : 0; t < sn_issued; ++t)
+                    mbar_wait(&sn_full[t % kSnSlots], (uint32_t)((t / kSnSlots) & 1), nullptr);
+                for (int it = b_issued > kStages ? b_issued - kStages : 0; it < b_issued; ++it)
+                    mbar_wait(&full[it % kStages], (uint32_t)((it / kStages) & 1), nullptr);
             }
         }
     } else if (warp == 1) {
@@ -385,7 +399,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int t = 0; t < ntiles; ++t) {
             const int a = t & 1;
             const uint32_t par = (uint32_t)((t >> 1) & 1);
-            if (!mbar_wait(&acc_full[a], par, abort_flag) || !mbar_wait(&sn_full[a], par, abort_flag)) {
+            const int sl = t % kSnSlots;
+            if (!mbar_wait(&acc_full[a], par, abort_flag) ||
+                !mbar_wait(&sn_full[sl], (uint32_t)((t / kSnSlots) & 1), abort_flag)) {
                 if (lane == 0) {
                     *abort_flag = 1;
                     record_error(p.err, kErrTimeout);
@@ -395,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const int64_t r = row0 + (int64_t)t * kTile;
             const int nr = (int)((row1 - r) < kTile ? (row1 - r) : kTile);
-            const float2* snt = sSN + a * kTile;
+            const float2* snt = sSN + sl * kTile;
 #pragma unroll 1
             for (int c0 = 0; c0 < kTile; c0 += 32) {
                 uint32_t v[32];
@@ -457,7 +473,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&acc_empty[a]);
-                mbar_arrive(&sn_empty[a]);
+                mbar_arrive(&sn_empty[sl]);
             }
         }
         if (MODE == kModePilot && qvalid) {
@@ -741,8 +757,9 @@ LowpPlan plan(const lhr_db* db, int nq, bool fp8, int W) {
 }
 
 size_t tc_smem(int slices, int mode) {
-    return 1024 + (size_t)slices * kSliceTile + (size_t)kStages * kSliceTile + 2 * kTile * sizeof(float2) +
-           (mode != kModePilot ? (size_t)kBuf * kTile * sizeof(u64) : 0) + (2 * kStages + 9) * sizeof(u64) + 16;
+    return 1024 + (size_t)slices * kSliceTile + (size_t)kStages * kSliceTile + kSnSlots * kTile * sizeof(float2) +
+           (mode != kModePilot ? (size_t)kBuf * kTile * sizeof(u64) : 0) +
+           (2 * kStages + 5 + 2 * kSnSlots) * sizeof(u64) + 16;
 }
 
 template <bool kFp8, int MODE, int WMAX>

@@ -232,6 +232,7 @@ __global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(cons
         const float rad = (p.xmax_w != nullptr ? sqrtf(__ldg(p.xmax_w)) * 1.0001f : p.xmax) + sqrtf(qn);
         const float margin = p.margin_scale * rad * rad;
         float thr_own = __int_as_float(0x7f800000);  // k-th distance of this warp's list for frame myq
+        const int jr = (p.k + warps - 1) / warps;      // rank read from every warp's list for the CTA bound
         u64* wlist = lists + (size_t)warp * QB * 32;
         const volatile unsigned* thr_v = thr_sh;     // other warps lower it with atomicMin
         // grid-wide per-frame bound: the smallest k-th distance any warp of any
@@ -343,6 +344,19 @@ __global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(cons
                     }
                     __syncwarp();
                 }
+            }
+            // CTA bound from every warp's list: warp w's jr-th key has jr rows
+            // at or below it, the warps' rows are disjoint and warps x jr >= k,
+            // so the largest of those keys bounds the CTA's k-th. A list read
+            // while its owner inserts is at worst stale, i.e. larger: still valid.
+            // (With a pilot bound the lists rarely beat it: skipped.)
+            if (p.bmin == nullptr && lane < QB) {
+                u64 b = 0ull;
+                for (int w = 0; w < warps; ++w) {
+                    const u64 v = reinterpret_cast<const volatile u64*>(lists)[((size_t)w * QB + lane) * 32 + jr - 1];
+                    b = v > b ? v : b;
+                }
+                if (b != kKeyEmpty) atomicMin(&thr_sh[lane], __float_as_uint(key_dist(b)));
             }
             // exchange bounds with the rest of the grid (gbound was loaded at the
             // stage's start): publish ours only when it is better, so the few
