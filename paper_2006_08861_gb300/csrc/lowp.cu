@@ -19,9 +19,12 @@
 //           N = 128 rows, K = 16 BF16 / 32 FP8 per instruction) into two
 //           128-column FP32 accumulators in TMEM, alternating per tile;
 //           tcgen05.commit frees smem stages and publishes accumulators.
-//   warps 2-5 epilogue: thread = query (its TMEM lane); tcgen05.ld 32 columns
-//           at a time, score = fma(-2 s_q, s_j dot, n_j). What happens to a
-//           score depends on the pass:
+//   warps 2-9 epilogue: two warps per TMEM lane quadrant, each taking half of
+//           a tile's 128 columns; thread = (query = its TMEM lane, column half);
+//           tcgen05.ld 32 columns at a time, the next load in flight while the
+//           current 32 are scored, score = fma(-2 s_q, s_j dot, n_j). What
+//           happens to a score depends on the pass (per-thread lists cover the
+//           thread's column half and count as separate chunk lists):
 //     pilot  over every 64th database row (a copy built with the database):
 //            the thread keeps its query's 8 smallest sample keys in a static
 //            register network;
@@ -57,8 +60,11 @@ constexpr int kSliceBytes = 128;  // K bytes per smem row (one 128-byte swizzle 
 constexpr int kSliceTile = kTile * kSliceBytes;  // 16 KB per tile slice
 constexpr int kStages = 6;
 constexpr int kSnSlots = 8;       // (s_j, n_j) tiles in flight: deeper than the operand ring, so never its limit
-constexpr int kBuf = 32;          // survivor buffer entries per epilogue thread
-constexpr int kThreads = 192;
+constexpr int kBuf = 16;          // survivor buffer entries per epilogue thread
+constexpr int kHalves = 2;        // epilogue warps per TMEM lane quadrant (each takes a column range)
+constexpr int kEpiWarps = 4 * kHalves;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreads = 64 + kEpiThreads;  // producer, MMA issuer, epilogue
 
 // ------------------------------------------------------------------ PTX
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, u64* bar) {
@@ -92,6 +98,30 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, u64 adesc, u64 bdesc, ui
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
             : "memory");
     }
+}
+
+// tcgen05.ld of 32 columns without the wait: the registers are valid only after
+// tmem_ld_wait on the same array, which names them so nothing reads them earlier.
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -207,7 +237,7 @@ __device__ __noinline__ void flush_buffer(u64* list, const u64* buf, int stride,
 __device__ __noinline__ int append_candidates(const TcParams& p, int64_t qi, const u64* buf, int nb) {
     const unsigned pos = atomicAdd(&p.cnt[qi], (unsigned)nb);
     for (int i = 0; i < nb; ++i)
-        if (pos + i < (unsigned)kCap) p.cand[(size_t)qi * kCap + pos + i] = buf[i * kTile];
+        if (pos + i < (unsigned)kCap) p.cand[(size_t)qi * kCap + pos + i] = buf[i * kEpiThreads];
     return 0;
 }
 
@@ -235,8 +265,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char* sA = smem;                                   // slices x 16 KB
     unsigned char* sB = sA + (size_t)p.slices * kSliceTile;     // kStages x 16 KB
     float2* sSN = reinterpret_cast<float2*>(sB + (size_t)kStages * kSliceTile);  // kSnSlots x 128
-    u64* sBuf = reinterpret_cast<u64*>(sSN + kSnSlots * kTile);  // main / full pass: kBuf x 128 (slot-major)
-    u64* bars = MODE != kModePilot ? sBuf + kBuf * kTile : sBuf;
+    u64* sBuf = reinterpret_cast<u64*>(sSN + kSnSlots * kTile);  // main / full: kBuf x kEpiThreads (slot-major)
+    u64* bars = MODE != kModePilot ? sBuf + kBuf * kEpiThreads : sBuf;
     u64* full = bars;
     u64* empty = full + kStages;
     u64* a_full = empty + kStages;
@@ -263,11 +293,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_init(a_full, 1);
         for (int i = 0; i < 2; ++i) {
             mbar_init(&acc_full[i], 1);
-            mbar_init(&acc_empty[i], 4);
+            mbar_init(&acc_empty[i], kEpiWarps);
         }
         for (int i = 0; i < kSnSlots; ++i) {
             mbar_init(&sn_full[i], 1);
-            mbar_init(&sn_empty[i], 4);
+            mbar_init(&sn_empty[i], kEpiWarps);
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -367,6 +397,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------ epilogue
         const int quad = warp & 3;                 // TMEM lane quadrant this warp may access
         const int qrow = quad * 32 + lane;         // query row within the block
+        const int ew = warp - 2;                   // epilogue warp 0 .. kEpiWarps-1
+        const int half = ew / 4;                   // column half of every tile this warp scores
+        const int lchunk = chunk * kHalves + half; // this thread's list slot among the chunk lists
         const int64_t qi = (int64_t)qblock * kTile + qrow;
         const bool qvalid = qi < p.nq;
         const float m = qvalid ? p.qm[qi] : 0.f;
@@ -379,8 +412,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (MODE == kModeMain && qvalid) {
             // tau = the kPilotR-th smallest pilot key; one pilot chunk's list per
             // pass, its loads issued together
-            const u64* pl = p.pilot + (size_t)qi * p.pchunks * kPilotR;
-            for (int c = 0; c < p.pchunks; ++c) {
+            const u64* pl = p.pilot + (size_t)qi * p.pchunks * kHalves * kPilotR;
+            for (int c = 0; c < p.pchunks * kHalves; ++c) {
                 u64 kk[kPilotR];
 #pragma unroll
                 for (int i = 0; i < kPilotR; ++i) kk[i] = __ldcg(pl + (size_t)c * kPilotR + i);
@@ -395,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int i = 0; i < WMAX; ++i) list[i] = kKeyEmpty;
         u64 thr = kKeyEmpty;
         int nb = 0;
-        u64* buf = sBuf + (warp - 2) * 32 + lane;
+        u64* buf = sBuf + ew * 32 + lane;
         for (int t = 0; t < ntiles; ++t) {
             const int a = t & 1;
             const uint32_t par = (uint32_t)((t >> 1) & 1);
@@ -412,10 +445,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t r = row0 + (int64_t)t * kTile;
             const int nr = (int)((row1 - r) < kTile ? (row1 - r) : kTile);
             const float2* snt = sSN + sl * kTile;
-#pragma unroll 1
-            for (int c0 = 0; c0 < kTile; c0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kTile + c0), v);
+            // 32 columns at a time; the second load is in flight while the first is scored
+            auto score32 = [&](const uint32_t(&v)[32], const int c0) {
                 if (MODE == kModeMain && qvalid) {
                     // branch-free scoring of 32 columns (packed pairs) into a
                     // survivor mask; survivors are rare and handled after
@@ -440,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if ((mask >> j) & 1u) {
                                 const u64 key = score_key(sc[j], (uint32_t)(r + c0 + j));
                                 if (key <= tau) {
-                                    buf[nb * kTile] = key;
+                                    buf[nb * kEpiThreads] = key;
                                     if (++nb == kBuf) nb = append_candidates(p, qi, buf, nb);
                                 }
                             }
@@ -458,9 +489,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         } else {
                             const u64 key = score_key(score, (uint32_t)(r + col));
                             if (col < nr && key < thr) {
-                                buf[nb * kTile] = key;
+                                buf[nb * kEpiThreads] = key;
                                 if (++nb == kBuf) {
-                                    flush_buffer<WMAX>(list, buf, kTile, nb, p.W);
+                                    flush_buffer<WMAX>(list, buf, kEpiThreads, nb, p.W);
                                     nb = 0;
                                     thr = list[p.W - 1];
                                 }
@@ -468,7 +499,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                 }
-            }
+                        };
+            static_assert(kTile / kHalves == 64, "two 32-column loads per warp and tile");
+            const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kTile);
+            const int cb = half * (kTile / kHalves);
+            uint32_t va[32], vb[32];
+            tmem_ld32_issue(tbase + (uint32_t)cb, va);
+            tmem_ld_wait(va);
+            tmem_ld32_issue(tbase + (uint32_t)(cb + 32), vb);
+            score32(va, cb);
+            tmem_ld_wait(vb);
+            score32(vb, cb + 32);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
@@ -477,15 +518,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         if (MODE == kModePilot && qvalid) {
-            u64* dst = p.partial + ((size_t)qi * p.nchunks + chunk) * kPilotR;
+            u64* dst = p.partial + ((size_t)qi * p.nchunks * kHalves + lchunk) * kPilotR;
 #pragma unroll
             for (int i = 0; i < kPilotR; ++i) dst[i] = net[i];
         }
         if (MODE == kModeMain && nb) append_candidates(p, qi, buf, nb);
         if (MODE == kModeFull) {
-            if (nb) flush_buffer<WMAX>(list, buf, kTile, nb, p.W);
+            if (nb) flush_buffer<WMAX>(list, buf, kEpiThreads, nb, p.W);
             if (qvalid) {
-                u64* dst = p.partial + ((size_t)qi * p.nchunks + chunk) * p.W;
+                u64* dst = p.partial + ((size_t)qi * p.nchunks * kHalves + lchunk) * p.W;
                 for (int i = 0; i < p.W; ++i) dst[i] = list[i];
             }
         }
@@ -749,16 +790,16 @@ LowpPlan plan(const lhr_db* db, int nq, bool fp8, int W) {
     const int elem = fp8 ? 1 : 2;
     pl.codes_bytes = a256((size_t)pl.nq_pad * db->dim * elem);
     pl.qm_bytes = a256((size_t)pl.nq_pad * sizeof(float));
-    pl.pilot_bytes = pl.sampled ? a256((size_t)nq * pl.pilot.nchunks * kPilotR * sizeof(u64)) : 0;
+    pl.pilot_bytes = pl.sampled ? a256((size_t)nq * pl.pilot.nchunks * kHalves * kPilotR * sizeof(u64)) : 0;
     pl.cnt_bytes = pl.sampled ? a256((size_t)nq * sizeof(unsigned)) : 0;
     pl.cand_bytes = pl.sampled ? a256((size_t)nq * kCap * sizeof(u64)) : 0;
-    pl.partial_bytes = a256((size_t)nq * pl.main.nchunks * W * sizeof(u64));
+    pl.partial_bytes = a256((size_t)nq * pl.main.nchunks * kHalves * W * sizeof(u64));
     return pl;
 }
 
 size_t tc_smem(int slices, int mode) {
     return 1024 + (size_t)slices * kSliceTile + (size_t)kStages * kSliceTile + kSnSlots * kTile * sizeof(float2) +
-           (mode != kModePilot ? (size_t)kBuf * kTile * sizeof(u64) : 0) +
+           (mode != kModePilot ? (size_t)kBuf * kEpiThreads * sizeof(u64) : 0) +
            (2 * kStages + 5 + 2 * kSnSlots) * sizeof(u64) + 16;
 }
 
@@ -872,7 +913,7 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
         e = cudaFuncSetAttribute(merge_rerank_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm); \
         if (e != cudaSuccess) return e;                                                                        \
         ProfScope ps("merge_rerank_kernel", stream);                                                           \
-        merge_rerank_kernel<C><<<blocks, kMergeWarps * 32, msm, stream>>>(partial, pl.main.nchunks, W, candp, cnt, \
+        merge_rerank_kernel<C><<<blocks, kMergeWarps * 32, msm, stream>>>(partial, pl.main.nchunks * kHalves, W, candp, cnt, \
                                                                             db->X, db->dim, q, nq, k, idx, dist); \
     } while (0)
     if (cpl == 1) LHR_MR(1);
