@@ -100,13 +100,29 @@ __device__ __forceinline__ bool mbar_try_wait(u64* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// try_wait with a suspend-time hint: the thread sleeps (issuing nothing) until
+// the phase completes or about `ns` nanoseconds pass.
+__device__ __forceinline__ bool mbar_try_wait_sleep(u64* bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Waits for the phase of `bar` with the given parity; false if it did not
-// complete within kWaitLimitNs or if `abort` was raised meanwhile.
+// complete within kWaitLimitNs or if `abort` was raised meanwhile. Between
+// checks the thread sleeps in the barrier (up to 20 us at a time), so waiting
+// warps take no issue slots from the warps that work.
 __device__ __forceinline__ bool mbar_wait(u64* bar, uint32_t parity, volatile int* abort) {
     if (mbar_try_wait(bar, parity)) return true;
     const u64 t0 = globaltimer();
     for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
         if (abort != nullptr && *abort) return false;
         if (globaltimer() - t0 > kWaitLimitNs) return false;
     }

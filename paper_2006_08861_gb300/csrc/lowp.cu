@@ -448,10 +448,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             // 32 columns at a time; the second load is in flight while the first is scored
             auto score32 = [&](const uint32_t(&v)[32], const int c0) {
                 if (MODE == kModeMain && qvalid) {
-                    // branch-free scoring of 32 columns (packed pairs) into a
-                    // survivor mask; survivors are rare and handled after
+                    // scores of 32 columns (packed pairs), then their minimum by a
+                    // balanced tree (one min per score, short dependency chains);
+                    // the rare block whose minimum is <= tau gets its survivor
+                    // mask and appends
                     float sc[32];
-                    unsigned mask = 0u;
 #pragma unroll
                     for (int j = 0; j < 32; j += 2) {
                         const float4 s4 = *reinterpret_cast<const float4*>(snt + c0 + j);  // s_j n_j s_j+1 n_j+1
@@ -460,11 +461,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const float2 s2 = __ffma2_rn(make_float2(m, m), prod, make_float2(s4.y, s4.w));
                         sc[j] = s2.x;
                         sc[j + 1] = s2.y;
-                        mask |= (s2.x <= tau_score ? 1u : 0u) << j;
-                        mask |= (s2.y <= tau_score ? 1u : 0u) << (j + 1);
                     }
-                    const int valid = nr - c0;
-                    if (valid < 32) mask &= valid > 0 ? ((1u << valid) - 1u) : 0u;
+                    float mn[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) mn[j] = fminf(sc[2 * j], sc[2 * j + 1]);
+#pragma unroll
+                    for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                        for (int j = 0; j < w; ++j) mn[j] = fminf(mn[j], mn[j + w]);
+                    unsigned mask = 0u;
+                    if (mn[0] <= tau_score) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) mask |= (sc[j] <= tau_score ? 1u : 0u) << j;
+                        const int valid = nr - c0;
+                        if (valid < 32) mask &= valid > 0 ? ((1u << valid) - 1u) : 0u;
+                    }
                     if (mask) {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
