@@ -328,7 +328,7 @@ def run_ours(args, spec, rank, world, local):
     lhr.lhr_profile_enable(False)
     kern = {}
     for name in ("hier_fused_kernel", "coarse_kernel", "collect_kernel", "shortlist_kernel", "aggregate_kernel",
-                 "scan_pilot", "scan_topk_kernel"):
+                 "scan_pilot", "scan_topk_kernel", "small_topk_kernel"):
         cnt, tot = lhr.lhr_profile_read(name, reset=True)
         if cnt:
             kern[name] = (cnt, tot)
@@ -346,7 +346,7 @@ def run_ours(args, spec, rank, world, local):
     elif dom == "shortlist_kernel":
         alg_bytes = S * D * 4 + D * 4           # one frame's shortlist rows per CTA; m CTAs per launch
         alg_bytes *= m
-    elif dom == "scan_topk_kernel":
+    elif dom in ("scan_topk_kernel", "small_topk_kernel"):
         alg_bytes = spec["n"] * D * 4 + (B if spec["name"] == "hbm_scan" else B * m) * D * 4
     else:
         alg_bytes = m * k * 8

@@ -608,6 +608,158 @@ __global__ void __launch_bounds__(256) wnorm_kernel(const float* X, int64_t n, i
     if (lane == 0 && mx) atomicMax(max_bits, mx);
 }
 
+// ------------------------------------------------------------------ small databases
+// Databases of at most kSmallRows rows: one CTA per (frame, subspace) scores
+// every row of the subspace (a warp per row, four rows in flight, the scan's
+// exact direct-form arithmetic, so the distances are the same to the bit),
+// keeps the keys in shared memory and selects the top k by radix select; no
+// per-warp lists, no merge tail.
+constexpr int kSmallThreads = 512;
+constexpr int64_t kSmallRows = 16384;
+
+template <int CPL>
+__global__ void __launch_bounds__(kSmallThreads) small_topk_kernel(const float* X, int D, const float* Q,
+                                                                   const float* w, const int4* chunks,
+                                                                   const int32_t* chunk_off, int n_sub,
+                                                                   const int32_t* perm, int k, int64_t* idx,
+                                                                   float* dist) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int f = blockIdx.x, sub = blockIdx.y, t = threadIdx.x, warp = t / 32, lane = t % 32;
+    const int D4 = D / 4;
+    const int c0 = chunk_off[sub], c1 = chunk_off[sub + 1];
+    const int r0 = c1 > c0 ? chunks[c0].x : 0, r1 = c1 > c0 ? chunks[c1 - 1].y : 0;
+    const int cnt = r1 - r0;
+    float* qs = reinterpret_cast<float*>(smem);          // D
+    float* ws = qs + D;                                   // D
+    unsigned* hs = reinterpret_cast<unsigned*>(ws + D);   // kBins
+    unsigned* res = hs + sel::kBins;                      // 4
+    unsigned* tmp = res + 4;                              // kSmallThreads / 32
+    u64* mm = reinterpret_cast<u64*>(tmp + kSmallThreads / 32);  // 2 x 16 (min, max per warp)
+    u64* outk = mm + 32;                                  // 32
+    u64* keys = outk + 32;                                // cnt
+    for (int i = t; i < D; i += kSmallThreads) {
+        qs[i] = Q[(size_t)f * D + i];
+        ws[i] = w != nullptr ? w[i] : 1.f;
+    }
+    __syncthreads();
+    const float4* qr = reinterpret_cast<const float4*>(qs);
+    const float4* wr = reinterpret_cast<const float4*>(ws);
+    u64 lo = ~0ull, hi = 0ull;
+    for (int i0 = warp * 4; i0 < cnt; i0 += (kSmallThreads / 32) * 4) {
+        float4 x[4][CPL];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4* xr = reinterpret_cast<const float4*>(X + (size_t)(r0 + min(i0 + u, cnt - 1)) * D);
+#pragma unroll
+            for (int jj = 0; jj < CPL; ++jj) {
+                const int c = lane + 32 * jj;
+                x[u][jj] = c < D4 ? __ldg(xr + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float2 acc = f2(0.f, 0.f);
+#pragma unroll
+            for (int jj = 0; jj < CPL; ++jj) {
+                const int c = lane + 32 * jj;
+                if (c < D4) {
+                    const float4 qv = qr[c], wv = wr[c];
+                    const float2 d0 = __ffma2_rn(f2(x[u][jj].x, x[u][jj].y), f2(-1.f, -1.f), f2(qv.x, qv.y));
+                    const float2 d1 = __ffma2_rn(f2(x[u][jj].z, x[u][jj].w), f2(-1.f, -1.f), f2(qv.z, qv.w));
+                    acc = __ffma2_rn(__fmul2_rn(d0, f2(wv.x, wv.y)), d0, acc);
+                    acc = __ffma2_rn(__fmul2_rn(d1, f2(wv.z, wv.w)), d1, acc);
+                }
+            }
+            float de = acc.x + acc.y;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) de += __shfl_xor_sync(kFull, de, o);
+            if (i0 + u < cnt) {
+                const u64 key = make_key(de, (uint32_t)(r0 + i0 + u));
+                if (lane == 0) keys[i0 + u] = key;
+                lo = key < lo ? key : lo;
+                hi = key > hi ? key : hi;
+            }
+        }
+    }
+    if (lane == 0) {
+        mm[warp] = lo;
+        mm[16 + warp] = hi;
+    }
+    __syncthreads();
+    const int kk = min(k, cnt);
+    u64 kth = ~0ull;
+    if (cnt > kk) {
+        lo = ~0ull;
+        hi = 0ull;
+        for (int i = 0; i < kSmallThreads / 32; ++i) {
+            lo = mm[i] < lo ? mm[i] : lo;
+            hi = mm[16 + i] > hi ? mm[16 + i] : hi;
+        }
+        kth = sel::block_kth_key<kSmallThreads>(keys, (unsigned)cnt, (unsigned)kk, lo, hi, hs, res, tmp);
+    }
+    if (t == 0) res[3] = 0u;
+    __syncthreads();
+    for (int i = t; i < cnt; i += kSmallThreads)
+        if (keys[i] <= kth) {
+            const unsigned pos = atomicAdd(&res[3], 1u);
+            if (pos < 32u) outk[pos] = keys[i];
+        }
+    __syncthreads();
+    if (t < 32) {
+        const unsigned n_out = min(res[3], 32u);
+        u64 v = (unsigned)lane < n_out ? outk[lane] : kKeyEmpty;
+#pragma unroll
+        for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                const u64 o = __shfl_xor_sync(kFull, v, stride);
+                const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
+                v = keep_min ? (o < v ? o : v) : (o > v ? o : v);
+            }
+        }
+        if (lane < k) {
+            const size_t o = ((size_t)f * n_sub + sub) * k + lane;
+            if (v == kKeyEmpty) {
+                idx[o] = -1;
+                dist[o] = __int_as_float(0x7f800000);
+            } else {
+                const uint32_t r = key_row(v);
+                idx[o] = perm ? (int64_t)perm[r] : (int64_t)r;
+                dist[o] = key_dist(v);
+            }
+        }
+    }
+}
+
+cudaError_t launch_small(const lhr_db* db, const float* q, int nq, int k, const float* w, int64_t* idx, float* dist,
+                         cudaStream_t stream) {
+    const int d4 = db->dim / 4;
+    const int cpl = d4 <= 32 ? 1 : (d4 <= 64 ? 2 : 4);
+    int64_t rows_max = 0;
+    for (int64_t r : db->sub_rows_h) rows_max = std::max(rows_max, r);
+    const size_t smem = (size_t)(2 * db->dim + sel::kBins + 4 + kSmallThreads / 32) * sizeof(float) +
+                        (64 + (size_t)std::max<int64_t>(rows_max, 1)) * sizeof(u64) + 16;
+    const dim3 grid(nq, db->n_sub);
+    ProfScope ps("small_topk_kernel", stream);
+#define LHR_SMALL(C)                                                                                                  \
+    do {                                                                                                              \
+        cudaError_t e = cudaFuncSetAttribute(small_topk_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                               \
+        small_topk_kernel<C><<<grid, kSmallThreads, smem, stream>>>(db->X, db->dim, q, w, db->chunks, db->chunk_off,  \
+                                                                    db->n_sub, db->perm, k, idx, dist);               \
+    } while (0)
+    if (cpl == 1) LHR_SMALL(1);
+    else if (cpl == 2) LHR_SMALL(2);
+    else LHR_SMALL(4);
+#undef LHR_SMALL
+    return cudaGetLastError();
+}
+
+__global__ void check_weights_kernel(const float* w, int D, int* err) {
+    for (int i = threadIdx.x; i < D; i += blockDim.x)
+        if (!(w[i] >= 0.f && w[i] < __int_as_float(0x7f800000))) record_error(err, kErrInvalidArg);
+}
+
 template <int QB, int CPL>
 cudaError_t launch_t(const ScanConfig& c, const ScanParams& p, int nqb, const char* label, cudaStream_t stream) {
     auto kern = scan_topk_kernel<QB, CPL>;
@@ -761,6 +913,7 @@ cudaError_t scan_with_pilot(const lhr_db* db, const float* q, int nq, int k, con
 
 cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t* idx, float* dist, void* scratch,
                         bool pilot, cudaStream_t stream) {
+    if (db->n <= kSmallRows) return launch_small(db, q, nq, k, nullptr, idx, dist, stream);
     return scan_with_pilot(db, q, nq, k, nullptr, idx, dist, scratch, pilot, stream);
 }
 
@@ -770,6 +923,13 @@ size_t scan_weighted_scratch_bytes(const lhr_db* db, int nq, int k) {
 
 cudaError_t launch_scan_weighted(const lhr_db* db, const float* q, int nq, int k, const float* w, int64_t* idx,
                                  float* dist, void* scratch, cudaStream_t stream) {
+    if (db->n <= kSmallRows) {
+        // the weights are checked here as the large path's norm kernel does
+        cudaError_t e = launch_small(db, q, nq, k, w, idx, dist, stream);
+        if (e != cudaSuccess) return e;
+        check_weights_kernel<<<1, 256, 0, stream>>>(w, db->dim, db->err);
+        return cudaGetLastError();
+    }
     float* xnw = reinterpret_cast<float*>(scratch);
     float* xmax_w = xnw + db->n;
     void* rest = reinterpret_cast<unsigned char*>(scratch) + align256(((size_t)db->n + 1) * sizeof(float));
