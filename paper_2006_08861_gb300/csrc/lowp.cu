@@ -13,16 +13,18 @@
 // tc_kernel, one CTA per (128-query block, database chunk), 6 warps:
 //   warp 0  producer: TMA (cp.async.bulk.tensor.2d, 128-byte swizzle) of the
 //           block's 128 query codes once, then the chunk's 128-row tiles, one
-//           128-byte K slice per stage, through a 6-stage mbarrier ring; plus
+//           128-byte K slice per stage, through a 7- or 8-stage mbarrier ring; plus
 //           a 1-D bulk copy of each tile's (s_j, n_j) pairs.
 //   warp 1  TMEM allocator and MMA issuer: tcgen05.mma (M = 128 queries,
-//           N = 128 rows, K = 16 BF16 / 32 FP8 per instruction) into two
-//           128-column FP32 accumulators in TMEM, alternating per tile;
+//           N = 128 rows, K = 16 BF16 / 32 FP8 per instruction) into four
+//           128-column FP32 accumulators in TMEM, in turn per tile (so the
+//           tensor core runs up to three tiles ahead of the epilogue);
 //           tcgen05.commit frees smem stages and publishes accumulators.
 //   warps 2-9 epilogue: two warps per TMEM lane quadrant, each taking half of
 //           a tile's 128 columns; thread = (query = its TMEM lane, column half);
-//           tcgen05.ld 32 columns at a time, the next load in flight while the
-//           current 32 are scored, score = fma(-2 s_q, s_j dot, n_j). What
+//           both 32-column tcgen05.ld of its 64 columns issued together, the
+//           accumulator released as soon as they land (scoring runs from
+//           registers), score = fma(-2 s_q, s_j dot, n_j). What
 //           happens to a score depends on the pass (per-thread lists cover the
 //           thread's column half and count as separate chunk lists):
 //     pilot  over every 64th database row (a copy built with the database):
@@ -47,6 +49,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -58,7 +61,8 @@ namespace {
 constexpr int kTile = 128;        // queries per CTA (UMMA M) and rows per tile (UMMA N)
 constexpr int kSliceBytes = 128;  // K bytes per smem row (one 128-byte swizzle atom)
 constexpr int kSliceTile = kTile * kSliceBytes;  // 16 KB per tile slice
-constexpr int kStages = 6;
+constexpr int kMaxStages = 8;     // operand ring depth: as many 16 KB slices as shared memory leaves room for
+constexpr int kAcc = 4;           // FP32 accumulators in TMEM (4 x 128 columns = all 512)
 constexpr int kSnSlots = 8;       // (s_j, n_j) tiles in flight: deeper than the operand ring, so never its limit
 constexpr int kBuf = 16;          // survivor buffer entries per epilogue thread
 constexpr int kHalves = 2;        // epilogue warps per TMEM lane quadrant (each takes a column range)
@@ -174,6 +178,7 @@ constexpr int kMergeWarps = 4;
 struct TcParams {
     int64_t n;
     int slices;          // D * elem / 128
+    int stages;          // operand ring depth, <= kMaxStages
     int chunk_rows;      // multiple of kTile
     int nchunks;
     const float2* sn;    // per row (s_j, n_j), padded
@@ -263,16 +268,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char* smem =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = smem;                                   // slices x 16 KB
-    unsigned char* sB = sA + (size_t)p.slices * kSliceTile;     // kStages x 16 KB
-    float2* sSN = reinterpret_cast<float2*>(sB + (size_t)kStages * kSliceTile);  // kSnSlots x 128
+    unsigned char* sB = sA + (size_t)p.slices * kSliceTile;     // p.stages x 16 KB
+    const int stages = p.stages;
+    float2* sSN = reinterpret_cast<float2*>(sB + (size_t)stages * kSliceTile);  // kSnSlots x 128
     u64* sBuf = reinterpret_cast<u64*>(sSN + kSnSlots * kTile);  // main / full: kBuf x kEpiThreads (slot-major)
     u64* bars = MODE != kModePilot ? sBuf + kBuf * kEpiThreads : sBuf;
     u64* full = bars;
-    u64* empty = full + kStages;
-    u64* a_full = empty + kStages;
+    u64* empty = full + kMaxStages;
+    u64* a_full = empty + kMaxStages;
     u64* acc_full = a_full + 1;
-    u64* acc_empty = acc_full + 2;
-    u64* sn_full = acc_empty + 2;
+    u64* acc_empty = acc_full + kAcc;
+    u64* sn_full = acc_empty + kAcc;
     u64* sn_empty = sn_full + kSnSlots;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sn_empty + kSnSlots);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
@@ -286,12 +292,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr uint32_t kIdesc = tc_idesc(kFp8);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < stages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         mbar_init(a_full, 1);
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kAcc; ++i) {
             mbar_init(&acc_full[i], 1);
             mbar_init(&acc_empty[i], kEpiWarps);
         }
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                     "r"(2 * kTile)
+                     "r"(kAcc * kTile)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -320,6 +326,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int s = 0; s < p.slices; ++s)
                 tma_load_2d(sA + (size_t)s * kSliceTile, &tmA, s * kElemPerSlice, qblock * kTile, a_full);
             int sn_issued = 0, b_issued = 0;
+            int st = 0;
+            uint32_t ph = 0;  // ring slot and its wrap parity
             for (int t = 0; t < ntiles && !*abort_flag; ++t) {
                 const int64_t r = row0 + (int64_t)t * kTile;
                 const int slot = t % kSnSlots;
@@ -334,9 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 bulk_g2s(sSN + slot * kTile, p.sn + r, snb, &sn_full[slot]);
                 ++sn_issued;
                 for (int s = 0; s < p.slices; ++s) {
-                    const int it = t * p.slices + s;
-                    const int st = it % kStages;
-                    if (!mbar_wait(&empty[st], (uint32_t)((it / kStages) & 1) ^ 1u, abort_flag)) {
+                    if (!mbar_wait(&empty[st], ph ^ 1u, abort_flag)) {
                         *abort_flag = 1;
                         record_error(p.err, kErrTimeout);
                         break;
@@ -344,6 +350,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mbar_arrive_expect_tx(&full[st], kSliceTile);
                     tma_load_2d(sB + (size_t)st * kSliceTile, &tmB, s * kElemPerSlice, (int)r, &full[st]);
                     ++b_issued;
+                    if (++st == stages) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
                 }
             }
             if (*abort_flag) {
@@ -351,26 +361,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_wait(a_full, 0u, nullptr);
                 for (int t = sn_issued > kSnSlots ? sn_issued - kSnSlots : 0; t < sn_issued; ++t)
                     mbar_wait(&sn_full[t % kSnSlots], (uint32_t)((t / kSnSlots) & 1), nullptr);
-                for (int it = b_issued > kStages ? b_issued - kStages : 0; it < b_issued; ++it)
-                    mbar_wait(&full[it % kStages], (uint32_t)((it / kStages) & 1), nullptr);
+                for (int it = b_issued > stages ? b_issued - stages : 0; it < b_issued; ++it)
+                    mbar_wait(&full[it % stages], (uint32_t)((it / stages) & 1), nullptr);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             bool ok = mbar_wait(a_full, 0u, abort_flag);
-            int t = 0;
-            for (; ok && t < ntiles; ++t) {
-                const int a = t & 1;
-                if (!mbar_wait(&acc_empty[a], (uint32_t)((t >> 1) & 1) ^ 1u, abort_flag)) {
+            int st = 0;
+            uint32_t ph = 0;
+            for (int t = 0; ok && t < ntiles; ++t) {
+                const int a = t % kAcc;
+                if (!mbar_wait(&acc_empty[a], (uint32_t)((t / kAcc) & 1) ^ 1u, abort_flag)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(a * kTile);
                 for (int s = 0; s < p.slices; ++s) {
-                    const int it = t * p.slices + s;
-                    const int st = it % kStages;
-                    if (!mbar_wait(&full[st], (uint32_t)((it / kStages) & 1), abort_flag)) {
+                    if (!mbar_wait(&full[st], ph, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -384,6 +393,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                                      (s | kk) != 0 ? 1u : 0u);
                     }
                     tc_commit(&empty[st]);
+                    if (++st == stages) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
                 }
                 if (!ok) break;
                 tc_commit(&acc_full[a]);
@@ -430,8 +443,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         int nb = 0;
         u64* buf = sBuf + ew * 32 + lane;
         for (int t = 0; t < ntiles; ++t) {
-            const int a = t & 1;
-            const uint32_t par = (uint32_t)((t >> 1) & 1);
+            const int a = t % kAcc;
+            const uint32_t par = (uint32_t)((t / kAcc) & 1);
             const int sl = t % kSnSlots;
             if (!mbar_wait(&acc_full[a], par, abort_flag) ||
                 !mbar_wait(&sn_full[sl], (uint32_t)((t / kSnSlots) & 1), abort_flag)) {
@@ -516,17 +529,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int cb = half * (kTile / kHalves);
             uint32_t va[32], vb[32];
             tmem_ld32_issue(tbase + (uint32_t)cb, va);
-            tmem_ld_wait(va);
             tmem_ld32_issue(tbase + (uint32_t)(cb + 32), vb);
-            score32(va, cb);
+            tmem_ld_wait(va);  // waits for both loads; the second wait only names vb's registers
             tmem_ld_wait(vb);
-            score32(vb, cb + 32);
+            // the accumulator is in registers: hand it back to the MMA issuer before scoring
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&acc_empty[a]);
-                mbar_arrive(&sn_empty[sl]);
-            }
+            if (lane == 0) mbar_arrive(&acc_empty[a]);
+            score32(va, cb);
+            score32(vb, cb + 32);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sn_empty[sl]);
         }
         if (MODE == kModePilot && qvalid) {
             u64* dst = p.partial + ((size_t)qi * p.nchunks * kHalves + lchunk) * kPilotR;
@@ -546,7 +559,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTile) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAcc * kTile) : "memory");
 }
 
 // Per query: per-vector scale s_q = amax / qmax, codes, and -2 s_q. Rows past
@@ -808,17 +821,29 @@ LowpPlan plan(const lhr_db* db, int nq, bool fp8, int W) {
     return pl;
 }
 
-size_t tc_smem(int slices, int mode) {
-    return 1024 + (size_t)slices * kSliceTile + (size_t)kStages * kSliceTile + kSnSlots * kTile * sizeof(float2) +
+constexpr size_t kSmemLimit = 227 * 1024;  // dynamic shared memory per CTA
+
+size_t tc_smem_fixed(int slices, int mode) {
+    return 1024 + (size_t)slices * kSliceTile + kSnSlots * kTile * sizeof(float2) +
            (mode != kModePilot ? (size_t)kBuf * kEpiThreads * sizeof(u64) : 0) +
-           (2 * kStages + 5 + 2 * kSnSlots) * sizeof(u64) + 16;
+           (2 * kMaxStages + 1 + 2 * kAcc + 2 * kSnSlots) * sizeof(u64) + 16;
 }
+
+// Ring depth: as many slices as fit beside the resident query codes (>= 2).
+int tc_stages(int slices, int mode) {
+    const size_t fixed = tc_smem_fixed(slices, mode);
+    const int fit = fixed < kSmemLimit ? (int)((kSmemLimit - fixed) / kSliceTile) : 0;
+    return std::min(kMaxStages, fit);
+}
+
+size_t tc_smem(int slices, int stages, int mode) { return tc_smem_fixed(slices, mode) + (size_t)stages * kSliceTile; }
 
 template <bool kFp8, int MODE, int WMAX>
 cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& tp, int qblocks,
                       cudaStream_t stream, const char* name) {
     auto kern = tc_kernel<kFp8, MODE, WMAX>;
-    const size_t sm = tc_smem(tp.slices, MODE);
+    if (tp.stages < 2 || tp.stages > kMaxStages) return cudaErrorInvalidValue;
+    const size_t sm = tc_smem(tp.slices, tp.stages, MODE);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     ProfScope ps(name, stream);
@@ -885,6 +910,7 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
         pp.nchunks = pl.pilot.nchunks;
         pp.sn = fp8 ? db->sn8_s : db->snb_s;
         pp.partial = pilot;
+        pp.stages = tc_stages(pp.slices, kModePilot);
         e = fp8 ? launch_tc<true, kModePilot, 32>(ma, ms, pp, pl.qblocks, stream, "tc_pilot_kernel_fp8")
                 : launch_tc<false, kModePilot, 32>(ma, ms, pp, pl.qblocks, stream, "tc_pilot_kernel_bf16");
         if (e != cudaSuccess) return e;
@@ -899,6 +925,7 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
         mp.pchunks = pl.pilot.nchunks;
         mp.cand = cand;
         mp.cnt = cnt;
+        mp.stages = tc_stages(mp.slices, kModeMain);
         e = fp8 ? launch_tc<true, kModeMain, 32>(ma, mb, mp, pl.qblocks, stream, "tc_main_kernel_fp8")
                 : launch_tc<false, kModeMain, 32>(ma, mb, mp, pl.qblocks, stream, "tc_main_kernel_bf16");
         if (e != cudaSuccess) return e;
@@ -911,6 +938,7 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
     fp.sn = fp8 ? db->sn8 : db->snb;
     fp.partial = partial;
     fp.cnt = pl.sampled ? cnt : nullptr;
+    fp.stages = tc_stages(fp.slices, kModeFull);
     e = fp8 ? launch_full<true>(pl.wmax, ma, mb, fp, pl.qblocks, stream)
             : launch_full<false>(pl.wmax, ma, mb, fp, pl.qblocks, stream);
     if (e != cudaSuccess) return e;
