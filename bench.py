@@ -503,7 +503,7 @@ def run_precision(args, rank, world, local):
     torch.cuda.synchronize()
     lhr.lhr_profile_enable(False)
     share = {}
-    for name in ("quantize", "tc_pilot", "tc_main", "tc_full", "merge_rerank"):
+    for name in ("quantize", "tc_pilot", "tau_kernel", "tc_main", "tc_full", "merge_rerank"):
         n_l, t_ms = lhr.lhr_profile_read(name, reset=True)
         if n_l:
             share[name] = (n_l, t_ms)
@@ -534,7 +534,8 @@ def run_precision(args, rank, world, local):
                      "algorithmic_flops_per_launch": flops,
                      "kernel_share": {n: round(v[1] / tot_all, 4) for n, v in share.items()}},
         "cpu_baseline": cpu,
-        "gpu_launches": 5 * args.steps,
+        # per batch: query scale, query codes, pilot, tau, main, fallback (exits at once), merge + re-rank
+        "gpu_launches": 7 * args.steps,
     }
     h.close()
     return out

@@ -4,40 +4,46 @@
 // features directly, §3.1; this form trades a widened shortlist for
 // tensor-core throughput when many query frames are batched).
 //
-// score(q, x_j) = n_j - 2 s_q s_j (q^ . x^_j)        (||q||^2 dropped: constant per query)
-//   q^, x^_j : quantised codes, s_q, s_j : per-vector scales,
-//   n_j = s_j^2 ||x^_j||^2 (built with the database).
+// score(q, x_j) = fma(m s_j, q^ . x^_j, n_j)       (||q||^2 dropped: constant per query)
+//   x^_j, s_j : database codes and per-row scale, n_j = s_j^2 ||x^_j||^2
+//               (built with the database);
+//   q^, s_Q   : query codes and the batch's shared power-of-two scale (the
+//               smallest 2^e >= max |q| / QMAX), m = -2 s_Q, so m s_j is exact.
 // Keys are (orderable score bits << 32 | row); the shortlist is the W
 // smallest keys, exactly.
 //
-// tc_kernel, one CTA per (128-query block, database chunk), 6 warps:
+// Both tensor-core kernels are warp-specialised, 10 warps, one CTA per
+// (128-query block, database chunk):
 //   warp 0  producer: TMA (cp.async.bulk.tensor.2d, 128-byte swizzle) of the
 //           block's 128 query codes once, then the chunk's 128-row tiles, one
-//           128-byte K slice per stage, through a 7- or 8-stage mbarrier ring; plus
-//           a 1-D bulk copy of each tile's (s_j, n_j) pairs.
-//   warp 1  TMEM allocator and MMA issuer: tcgen05.mma (M = 128 queries,
-//           N = 128 rows, K = 16 BF16 / 32 FP8 per instruction) into four
-//           128-column FP32 accumulators in TMEM, in turn per tile (so the
-//           tensor core runs up to three tiles ahead of the epilogue);
-//           tcgen05.commit frees smem stages and publishes accumulators.
-//   warps 2-9 epilogue: two warps per TMEM lane quadrant, each taking half of
-//           a tile's 128 columns; thread = (query = its TMEM lane, column half);
-//           both 32-column tcgen05.ld of its 64 columns issued together, the
-//           accumulator released as soon as they land (scoring runs from
-//           registers), score = fma(-2 s_q, s_j dot, n_j). What
-//           happens to a score depends on the pass (per-thread lists cover the
-//           thread's column half and count as separate chunk lists):
+//           128-byte K slice per stage, through a mbarrier ring as deep as
+//           shared memory allows (7-8 stages).
+//   warp 1  TMEM allocator and MMA issuer: tcgen05.mma (M = N = 128, K = 16
+//           BF16 / 32 FP8 per instruction) into four 128-column FP32
+//           accumulators in TMEM, in turn per tile (the tensor core runs up to
+//           three tiles ahead of the epilogue); tcgen05.commit frees ring
+//           stages and publishes accumulators.
+//   warps 2-9 epilogue: two warps per TMEM lane quadrant, each reading half of
+//           a tile's 128 columns with two 32-column tcgen05.ld.
+// tc_main_kernel (the main pass): the database tile is the MMA's A operand, so
+//   a TMEM lane -- an epilogue thread -- is a database row and a column is a
+//   query. The row's (m s_j, n_j) sit in two registers (loaded from global
+//   memory a tile ahead) and the thread's 64 queries' thresholds tau_q in 64
+//   more, so scoring reads no shared memory: per pair of columns one packed
+//   fma and one packed subtract (score - tau_q), then a minimum over 32
+//   columns. Keys <= tau_q (rare) go to the query's candidate buffer with one
+//   warp-aggregated atomic per column. tau_q is the 8th smallest sample key
+//   of the query (pilot pass), so at least 8 keys, about 8 x 64 in
+//   expectation, qualify.
+// tc_kernel (pilot and fallback passes): the query block is the A operand, a
+//   thread is a query and reads each column's (s_j, n_j) from shared memory
+//   (a 1-D bulk copy per tile):
 //     pilot  over every 64th database row (a copy built with the database):
 //            the thread keeps its query's 8 smallest sample keys in a static
 //            register network;
-//     main   over the database: the query's threshold key tau is the 8th
-//            smallest sample key (so at least 8 keys, about 8 x 64 in
-//            expectation, are <= tau); every key <= tau is appended to the
-//            query's candidate buffer (rare, one atomic each). Scores never
-//            leave the SM otherwise.
 //     full   (fallback, and the only pass for databases too small to sample):
 //            the thread keeps its query's exact top W of the chunk in local
-//            memory, filled through a 32-entry shared-memory survivor
+//            memory, filled through a 16-entry shared-memory survivor
 //            buffer. When run after a main pass it exits at once unless a
 //            query of its block collected fewer than W or more than kCap keys.
 // merge_rerank_kernel, one warp per query: the shortlist is the W smallest
@@ -128,18 +134,6 @@ __device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes, 8-row core groups 1024 bytes apart.
 __device__ __forceinline__ u64 sw128_desc(uint32_t saddr) {
@@ -170,7 +164,7 @@ __device__ __forceinline__ u64 score_key(float t, uint32_t row) {
 }
 
 
-enum { kModePilot = 0, kModeMain = 1, kModeFull = 2 };
+enum { kModePilot = 0, kModeFull = 2 };
 constexpr int kPilotR = 8;        // sample keys kept per query by the pilot pass
 constexpr int kCap = 2048;        // candidate keys kept per query by the main pass
 constexpr int kMergeWarps = 4;
@@ -182,14 +176,24 @@ struct TcParams {
     int chunk_rows;      // multiple of kTile
     int nchunks;
     const float2* sn;    // per row (s_j, n_j), padded
-    const float* qm;     // per padded query: -2 s_q (0 for padding)
+    const float* qs;     // [0] = s_Q, [1] = m = -2 s_Q
     int nq;
     int W;
     u64* partial;        // full: [query][chunk][W]; pilot: [query][chunk][kPilotR]
-    const u64* pilot;    // main: the pilot lists [query][pchunks][kPilotR]
-    int pchunks;
-    u64* cand;           // main: [query][kCap]
-    unsigned* cnt;       // main: keys seen per query; full: nullptr = always run
+    const unsigned* cnt; // full: keys the main pass saw per query; nullptr = always run
+    int* err;
+};
+
+struct MainParams {
+    int64_t n;
+    int slices, stages, chunk_rows, nchunks;
+    const float2* sn;     // per row (s_j, n_j), kSnPad rows of zero padding
+    const float* qs;      // [0] = s_Q, [1] = m = -2 s_Q
+    const float* tau_s;   // per padded query: threshold score (-inf for padding queries)
+    const u64* tau_key;   // per padded query: threshold key
+    u64* cand;            // [query][kCap]
+    unsigned* cnt;        // keys <= tau seen per query
+    int nq;
     int* err;
 };
 
@@ -237,13 +241,11 @@ __device__ __noinline__ void flush_buffer(u64* list, const u64* buf, int stride,
     for (int o = 0; o < W; ++o) list[o] = out[o];
 }
 
-// Main pass: moves a thread's buffered keys (shared memory, stride kTile) to its
-// query's candidate buffer with one atomic. Returns the new buffer fill (0).
-__device__ __noinline__ int append_candidates(const TcParams& p, int64_t qi, const u64* buf, int nb) {
-    const unsigned pos = atomicAdd(&p.cnt[qi], (unsigned)nb);
-    for (int i = 0; i < nb; ++i)
-        if (pos + i < (unsigned)kCap) p.cand[(size_t)qi * kCap + pos + i] = buf[i * kEpiThreads];
-    return 0;
+// Three-input minimum (one instruction on this architecture).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
 template <bool kFp8, int MODE, int WMAX>
@@ -271,8 +273,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char* sB = sA + (size_t)p.slices * kSliceTile;     // p.stages x 16 KB
     const int stages = p.stages;
     float2* sSN = reinterpret_cast<float2*>(sB + (size_t)stages * kSliceTile);  // kSnSlots x 128
-    u64* sBuf = reinterpret_cast<u64*>(sSN + kSnSlots * kTile);  // main / full: kBuf x kEpiThreads (slot-major)
-    u64* bars = MODE != kModePilot ? sBuf + kBuf * kEpiThreads : sBuf;
+    u64* sBuf = reinterpret_cast<u64*>(sSN + kSnSlots * kTile);  // full: kBuf x kEpiThreads (slot-major)
+    u64* bars = MODE == kModeFull ? sBuf + kBuf * kEpiThreads : sBuf;
     u64* full = bars;
     u64* empty = full + kMaxStages;
     u64* a_full = empty + kMaxStages;
@@ -415,27 +417,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int lchunk = chunk * kHalves + half; // this thread's list slot among the chunk lists
         const int64_t qi = (int64_t)qblock * kTile + qrow;
         const bool qvalid = qi < p.nq;
-        const float m = qvalid ? p.qm[qi] : 0.f;
-        // pilot: the sample keys; main: tau from the pilot lists; full: exact top W
+        const float m = qvalid ? __ldg(p.qs + 1) : 0.f;
+        // pilot: the sample keys; full: exact top W
         u64 net[kPilotR];
 #pragma unroll
         for (int i = 0; i < kPilotR; ++i) net[i] = kKeyEmpty;
-        u64 tau = kKeyEmpty;
-        float tau_score = __int_as_float(0x7f800000);
-        if (MODE == kModeMain && qvalid) {
-            // tau = the kPilotR-th smallest pilot key; one pilot chunk's list per
-            // pass, its loads issued together
-            const u64* pl = p.pilot + (size_t)qi * p.pchunks * kHalves * kPilotR;
-            for (int c = 0; c < p.pchunks * kHalves; ++c) {
-                u64 kk[kPilotR];
-#pragma unroll
-                for (int i = 0; i < kPilotR; ++i) kk[i] = __ldcg(pl + (size_t)c * kPilotR + i);
-#pragma unroll
-                for (int i = 0; i < kPilotR; ++i) net_insert(net, kk[i]);
-            }
-            tau = net[kPilotR - 1];
-            tau_score = tau == kKeyEmpty ? __int_as_float(0x7f800000) : key_score(tau);
-        }
         u64 list[MODE == kModeFull ? WMAX : 1];
         if (MODE == kModeFull)
             for (int i = 0; i < WMAX; ++i) list[i] = kKeyEmpty;
@@ -460,54 +446,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float2* snt = sSN + sl * kTile;
             // 32 columns at a time; the second load is in flight while the first is scored
             auto score32 = [&](const uint32_t(&v)[32], const int c0) {
-                if (MODE == kModeMain && qvalid) {
-                    // scores of 32 columns (packed pairs), then their minimum by a
-                    // balanced tree (one min per score, short dependency chains);
-                    // the rare block whose minimum is <= tau gets its survivor
-                    // mask and appends
-                    float sc[32];
-#pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
-                        const float4 s4 = *reinterpret_cast<const float4*>(snt + c0 + j);  // s_j n_j s_j+1 n_j+1
-                        const float2 prod = __fmul2_rn(make_float2(s4.x, s4.z),
-                                                       make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])));
-                        const float2 s2 = __ffma2_rn(make_float2(m, m), prod, make_float2(s4.y, s4.w));
-                        sc[j] = s2.x;
-                        sc[j + 1] = s2.y;
-                    }
-                    float mn[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) mn[j] = fminf(sc[2 * j], sc[2 * j + 1]);
-#pragma unroll
-                    for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-                        for (int j = 0; j < w; ++j) mn[j] = fminf(mn[j], mn[j + w]);
-                    unsigned mask = 0u;
-                    if (mn[0] <= tau_score) {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) mask |= (sc[j] <= tau_score ? 1u : 0u) << j;
-                        const int valid = nr - c0;
-                        if (valid < 32) mask &= valid > 0 ? ((1u << valid) - 1u) : 0u;
-                    }
-                    if (mask) {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            if ((mask >> j) & 1u) {
-                                const u64 key = score_key(sc[j], (uint32_t)(r + c0 + j));
-                                if (key <= tau) {
-                                    buf[nb * kEpiThreads] = key;
-                                    if (++nb == kBuf) nb = append_candidates(p, qi, buf, nb);
-                                }
-                            }
-                        }
-                    }
-                }
-                if (MODE != kModeMain && qvalid) {
+                if (qvalid) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int col = c0 + j;
                         const float2 sn = snt[col];
-                        const float score = fmaf(m, sn.x * __uint_as_float(v[j]), sn.y);
+                        const float score = fmaf(m * sn.x, __uint_as_float(v[j]), sn.y);
                         if (MODE == kModePilot) {
                             if (col < nr) net_insert(net, score_key(score, (uint32_t)(r + col)));
                         } else {
@@ -546,7 +490,6 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int i = 0; i < kPilotR; ++i) dst[i] = net[i];
         }
-        if (MODE == kModeMain && nb) append_candidates(p, qi, buf, nb);
         if (MODE == kModeFull) {
             if (nb) flush_buffer<WMAX>(list, buf, kEpiThreads, nb, p.W);
             if (qvalid) {
@@ -562,29 +505,233 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAcc * kTile) : "memory");
 }
 
-// Per query: per-vector scale s_q = amax / qmax, codes, and -2 s_q. Rows past
-// nq (padding to the 128-query block) get zero codes.
-template <bool kFp8>
-__global__ void quantize_queries_kernel(const float* Q, int nq, int nq_pad, int D, void* codes, float* qm) {
-    const int lane = threadIdx.x & 31;
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w >= nq_pad) return;
-    const float qmax = kFp8 ? 448.0f : 1.0f;
-    float amax = 0.f;
-    if (w < nq)
-        for (int j = lane; j < D; j += 32) amax = fmaxf(amax, fabsf(Q[(size_t)w * D + j]));
+// Main pass, a rare run of columns C0..C1-1 of group G in which this thread's
+// row has a key <= the query's tau: such keys go to the query's candidate
+// buffer, one atomic each. score < tau_s decides without the key; on an exact
+// score tie the row index decides against the threshold key.
+template <int G, int C0, int C1>
+__device__ __forceinline__ void main_survivors(const MainParams& p, const uint32_t (&v)[32], const float2 (&ntau)[32],
+                                               float A, float B, uint32_t row, int64_t q0) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(kFull, amax, o));
-    const float s = amax > 0.f ? __fdiv_rn(amax, qmax) : 1.0f;
-    for (int j = lane; j < D; j += 32) {
-        const float v = w < nq ? __fdiv_rn(Q[(size_t)w * D + j], s) : 0.f;
-        if (kFp8)
-            reinterpret_cast<__nv_fp8_storage_t*>(codes)[(size_t)w * D + j] =
-                __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
-        else
-            reinterpret_cast<__nv_bfloat16*>(codes)[(size_t)w * D + j] = __float2bfloat16_rn(v);
+    for (int j = C0; j < C1; ++j) {
+        const float2 nt = ntau[G * 16 + j / 2];
+        const float tau_s = -((j & 1) ? nt.y : nt.x);
+        const float score = fmaf(B, __uint_as_float(v[j]), A);
+        if (score <= tau_s) {
+            const int64_t qi = q0 + G * 32 + j;
+            const u64 key = score_key(score, row);
+            if (qi < p.nq && (score < tau_s || key <= __ldg(p.tau_key + qi))) {
+                const unsigned pos = atomicAdd(p.cnt + qi, 1u);
+                if (pos < (unsigned)kCap) p.cand[(size_t)qi * kCap + pos] = key;
+            }
+        }
     }
-    if (lane == 0) qm[w] = w < nq ? -2.0f * s : 0.f;
+}
+
+// Minima of score - tau_q over the four column runs 0-8, 9-17, 18-26, 27-31 of
+// group G, score = fma(B, dot, A) in packed pairs (exact sign: the difference
+// of two floats is <= 0 iff score <= tau_q).
+template <int G>
+__device__ __forceinline__ float4 main_group_min(const uint32_t (&v)[32], const float2 (&ntau)[32], float2 A2,
+                                                 float2 B2) {
+    float d[32];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float2 sc = __ffma2_rn(B2, make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])), A2);
+        const float2 df = __fadd2_rn(sc, ntau[G * 16 + i]);
+        d[2 * i] = df.x;
+        d[2 * i + 1] = df.y;
+    }
+    float t[11];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) t[i] = fmin3(d[3 * i], d[3 * i + 1], d[3 * i + 2]);
+    t[10] = fminf(d[30], d[31]);
+    return make_float4(fmin3(t[0], t[1], t[2]), fmin3(t[3], t[4], t[5]), fmin3(t[6], t[7], t[8]), fminf(t[9], t[10]));
+}
+
+template <int G>
+__device__ __forceinline__ void main_group(const MainParams& p, const uint32_t (&v)[32], const float2 (&ntau)[32],
+                                           float A, float B, bool rowvalid, uint32_t row, int64_t q0) {
+    const float4 mn = main_group_min<G>(v, ntau, make_float2(A, A), make_float2(B, B));
+    if (rowvalid && fminf(fmin3(mn.x, mn.y, mn.z), mn.w) <= 0.f) {
+        if (mn.x <= 0.f) main_survivors<G, 0, 9>(p, v, ntau, A, B, row, q0);
+        if (mn.y <= 0.f) main_survivors<G, 9, 18>(p, v, ntau, A, B, row, q0);
+        if (mn.z <= 0.f) main_survivors<G, 18, 27>(p, v, ntau, A, B, row, q0);
+        if (mn.w <= 0.f) main_survivors<G, 27, 32>(p, v, ntau, A, B, row, q0);
+    }
+}
+
+// Main pass: every key <= tau_q of the chunk into query q's candidate buffer.
+template <bool kFp8>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_main_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmX, const MainParams p) {
+    extern __shared__ unsigned char smem_raw[];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int chunk = blockIdx.x, qblock = blockIdx.y;
+    unsigned char* smem =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int stages = p.stages;
+    unsigned char* sQ = smem;                                   // slices x 16 KB: the block's query codes
+    unsigned char* sX = sQ + (size_t)p.slices * kSliceTile;     // stages x 16 KB: database slices
+    u64* full = reinterpret_cast<u64*>(sX + (size_t)stages * kSliceTile);
+    u64* empty = full + kMaxStages;
+    u64* q_full = empty + kMaxStages;
+    u64* acc_full = q_full + 1;
+    u64* acc_empty = acc_full + kAcc;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + kAcc);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+    const int64_t row0 = (int64_t)chunk * p.chunk_rows;
+    const int64_t row1 = min(p.n, row0 + p.chunk_rows);
+    const int ntiles = row1 > row0 ? (int)((row1 - row0 + kTile - 1) / kTile) : 0;
+    constexpr int kElemPerSlice = kFp8 ? 128 : 64;
+    constexpr int kMmaK = kFp8 ? 32 : 16;
+    constexpr int kMmaPerSlice = kElemPerSlice / kMmaK;
+    constexpr uint32_t kIdesc = tc_idesc(kFp8);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(q_full, 1);
+        for (int i = 0; i < kAcc; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], kEpiWarps);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(kAcc * kTile)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(q_full, (uint32_t)p.slices * kSliceTile);
+            for (int s = 0; s < p.slices; ++s)
+                tma_load_2d(sQ + (size_t)s * kSliceTile, &tmQ, s * kElemPerSlice, qblock * kTile, q_full);
+            int b_issued = 0, st = 0;
+            uint32_t ph = 0;
+            for (int t = 0; t < ntiles && !*abort_flag; ++t) {
+                const int r = (int)(row0 + (int64_t)t * kTile);
+                for (int s = 0; s < p.slices; ++s) {
+                    if (!mbar_wait(&empty[st], ph ^ 1u, abort_flag)) {
+                        *abort_flag = 1;
+                        record_error(p.err, kErrTimeout);
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[st], kSliceTile);
+                    tma_load_2d(sX + (size_t)st * kSliceTile, &tmX, s * kElemPerSlice, r, &full[st]);
+                    ++b_issued;
+                    if (++st == stages) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            if (*abort_flag) {
+                // let this thread's copies still in flight land before the CTA exits (bounded waits)
+                mbar_wait(q_full, 0u, nullptr);
+                for (int it = b_issued > stages ? b_issued - stages : 0; it < b_issued; ++it)
+                    mbar_wait(&full[it % stages], (uint32_t)((it / stages) & 1), nullptr);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = mbar_wait(q_full, 0u, abort_flag);
+            int st = 0;
+            uint32_t ph = 0;
+            for (int t = 0; ok && t < ntiles; ++t) {
+                const int a = t % kAcc;
+                if (!mbar_wait(&acc_empty[a], (uint32_t)((t / kAcc) & 1) ^ 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(a * kTile);
+                for (int s = 0; s < p.slices; ++s) {
+                    if (!mbar_wait(&full[st], ph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t x_base = smem_u32(sX + (size_t)st * kSliceTile);
+                    const uint32_t q_base = smem_u32(sQ + (size_t)s * kSliceTile);
+#pragma unroll
+                    for (int kk = 0; kk < kMmaPerSlice; ++kk) {
+                        const uint32_t off = (uint32_t)(kk * kMmaK * (kFp8 ? 1 : 2));
+                        tc_mma<kFp8>(d_tmem, sw128_desc(x_base + off), sw128_desc(q_base + off), kIdesc,
+                                     (s | kk) != 0 ? 1u : 0u);
+                    }
+                    tc_commit(&empty[st]);
+                    if (++st == stages) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                tc_commit(&acc_full[a]);
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                record_error(p.err, kErrTimeout);
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue: thread = database row
+        const int quad = warp & 3;                     // TMEM lane quadrant this warp may access
+        const int rl = quad * 32 + lane;               // row within the tile
+        const int half = (warp - 2) / 4;               // column (query) half this warp scores
+        const int cb = half * (kTile / kHalves);
+        const int64_t q0 = (int64_t)qblock * kTile + cb;  // the thread's first query
+        static_assert(kTile / kHalves == 64, "two 32-column loads per warp and tile");
+        float2 ntau[32];                               // -tau of queries q0 + 2i, q0 + 2i + 1
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            ntau[i] = make_float2(-__ldg(p.tau_s + q0 + 2 * i), -__ldg(p.tau_s + q0 + 2 * i + 1));
+        const float m = __ldg(p.qs + 1);
+        float2 sn_next = ntiles > 0 ? __ldg(p.sn + row0 + rl) : make_float2(0.f, 0.f);
+        for (int t = 0; t < ntiles; ++t) {
+            const int a = t % kAcc;
+            const int64_t r = row0 + (int64_t)t * kTile;
+            const float2 sn = sn_next;  // rows past the database read its zero padding
+            if (t + 1 < ntiles) sn_next = __ldg(p.sn + r + kTile + rl);
+            if (!mbar_wait(&acc_full[a], (uint32_t)((t / kAcc) & 1), abort_flag)) {
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    record_error(p.err, kErrTimeout);
+                }
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kTile + cb);
+            uint32_t va[32], vb[32];
+            tmem_ld32_issue(tbase, va);
+            tmem_ld32_issue(tbase + 32u, vb);
+            tmem_ld_wait(va);  // waits for both loads; the second wait only names vb's registers
+            tmem_ld_wait(vb);
+            const float B = m * sn.x, A = sn.y;
+            const bool rowvalid = r + rl < row1;
+            main_group<0>(p, va, ntau, A, B, rowvalid, (uint32_t)(r + rl), q0);
+            main_group<1>(p, vb, ntau, A, B, rowvalid, (uint32_t)(r + rl), q0);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[a]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAcc * kTile) : "memory");
 }
 
 __device__ __forceinline__ u64 warp_min_u64(u64 v) {
@@ -595,6 +742,96 @@ __device__ __forceinline__ u64 warp_min_u64(u64 v) {
     }
     return v;
 }
+
+// Per query (one warp): tau = the kPilotR-th smallest of its pilot keys (key
+// and score); each lane keeps the kPilotR smallest of every 32nd list, then
+// kPilotR rounds of a warp minimum pop the overall smallest. Padding queries
+// get a score threshold of -inf, so nothing passes.
+__global__ void tau_kernel(const u64* __restrict__ pilot, int lists, int nq, int nq_pad, u64* __restrict__ tau_key,
+                           float* __restrict__ tau_s) {
+    const int lane = threadIdx.x & 31;
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= nq_pad) return;
+    if (q >= nq) {
+        if (lane == 0) {
+            tau_key[q] = 0;
+            tau_s[q] = -__int_as_float(0x7f800000);
+        }
+        return;
+    }
+    u64 net[kPilotR];
+#pragma unroll
+    for (int i = 0; i < kPilotR; ++i) net[i] = kKeyEmpty;
+    const u64* pl = pilot + (size_t)q * lists * kPilotR;
+    for (int c = lane; c < lists; c += 32) {
+        u64 kk[kPilotR];
+#pragma unroll
+        for (int i = 0; i < kPilotR; ++i) kk[i] = __ldcg(pl + (size_t)c * kPilotR + i);
+#pragma unroll
+        for (int i = 0; i < kPilotR; ++i) net_insert(net, kk[i]);
+    }
+    u64 tau = kKeyEmpty;
+    for (int r = 0; r < kPilotR; ++r) {
+        const u64 head = net[0];
+        tau = warp_min_u64(head);
+        if (head == tau && tau != kKeyEmpty) {
+            // the lane holding it (ties: keys are unique, (score, row)) pops its head
+#pragma unroll
+            for (int i = 0; i < kPilotR - 1; ++i) net[i] = net[i + 1];
+            net[kPilotR - 1] = kKeyEmpty;
+        }
+    }
+    if (lane == 0) {
+        tau_key[q] = tau;
+        tau_s[q] = tau == kKeyEmpty ? __int_as_float(0x7f800000) : key_score(tau);
+    }
+}
+
+// max |q| over the batch into *amax_bits (the bits of a non-negative float
+// order like unsigned integers; *amax_bits zeroed before the launch).
+__global__ void query_amax_kernel(const float* __restrict__ Q, int64_t count, unsigned* __restrict__ amax_bits) {
+    float amax = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        amax = fmaxf(amax, fabsf(__ldg(Q + i)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(kFull, amax, o));
+    if ((threadIdx.x & 31) == 0 && amax > 0.f) atomicMax(amax_bits, __float_as_uint(amax));
+}
+
+// The batch's shared query scale from max |q|: s_Q = the smallest power of two
+// >= max |q| / qmax (the divide in binary32; at least 2^-126; 1 for an
+// all-zero batch).
+__device__ __forceinline__ float query_scale(float amax, float qmax) {
+    if (!(amax > 0.f)) return 1.0f;
+    const float x = fmaxf(__fdiv_rn(amax, qmax), 1.17549435e-38f);  // 2^-126
+    const uint32_t b = __float_as_uint(x);
+    return (b & 0x7fffffu) == 0u ? x : __uint_as_float((b & 0x7f800000u) + 0x00800000u);
+}
+
+// Query codes q / s_Q (exact: s_Q is a power of two) rounded to the format;
+// rows past nq (padding to the 128-query block) get zero codes. Also writes
+// qs[0] = s_Q, qs[1] = m = -2 s_Q.
+template <bool kFp8>
+__global__ void quantize_queries_kernel(const float* Q, int nq, int nq_pad, int D, const unsigned* amax_bits,
+                                        float qmax, float* qs, void* codes) {
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= nq_pad) return;
+    const float s = query_scale(__uint_as_float(*amax_bits), qmax);
+    if (w == 0 && lane == 0) {
+        qs[0] = s;
+        qs[1] = -2.0f * s;
+    }
+    for (int j = lane; j < D; j += 32) {
+        const float v = w < nq ? __fdiv_rn(Q[(size_t)w * D + j], s) : 0.f;
+        if (kFp8)
+            reinterpret_cast<__nv_fp8_storage_t*>(codes)[(size_t)w * D + j] =
+                __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+        else
+            reinterpret_cast<__nv_bfloat16*>(codes)[(size_t)w * D + j] = __float2bfloat16_rn(v);
+    }
+}
+
 
 // Warp bitonic sort of n (power of two) keys in shared memory, ascending.
 __device__ void warp_sort(u64* a, int n, int lane) {
@@ -800,7 +1037,7 @@ struct LowpPlan {
     int nq_pad, qblocks, wmax;
     bool sampled;
     Chunking main, pilot;
-    size_t codes_bytes, qm_bytes, pilot_bytes, cnt_bytes, cand_bytes, partial_bytes;
+    size_t codes_bytes, qs_bytes, pilot_bytes, tau_bytes, cnt_bytes, cand_bytes, partial_bytes;
 };
 
 LowpPlan plan(const lhr_db* db, int nq, bool fp8, int W) {
@@ -813,8 +1050,9 @@ LowpPlan plan(const lhr_db* db, int nq, bool fp8, int W) {
     pl.pilot = chunking(std::max<int64_t>(db->n_sample, 1), pl.qblocks, db->sms);
     const int elem = fp8 ? 1 : 2;
     pl.codes_bytes = a256((size_t)pl.nq_pad * db->dim * elem);
-    pl.qm_bytes = a256((size_t)pl.nq_pad * sizeof(float));
+    pl.qs_bytes = a256(4 * sizeof(float));  // s_Q, m, max |q| bits
     pl.pilot_bytes = pl.sampled ? a256((size_t)nq * pl.pilot.nchunks * kHalves * kPilotR * sizeof(u64)) : 0;
+    pl.tau_bytes = pl.sampled ? a256((size_t)pl.nq_pad * sizeof(u64)) + a256((size_t)pl.nq_pad * sizeof(float)) : 0;
     pl.cnt_bytes = pl.sampled ? a256((size_t)nq * sizeof(unsigned)) : 0;
     pl.cand_bytes = pl.sampled ? a256((size_t)nq * kCap * sizeof(u64)) : 0;
     pl.partial_bytes = a256((size_t)nq * pl.main.nchunks * kHalves * W * sizeof(u64));
@@ -837,6 +1075,29 @@ int tc_stages(int slices, int mode) {
 }
 
 size_t tc_smem(int slices, int stages, int mode) { return tc_smem_fixed(slices, mode) + (size_t)stages * kSliceTile; }
+
+size_t main_smem(int slices, int stages) {
+    return 1024 + (size_t)(slices + stages) * kSliceTile + (2 * kMaxStages + 1 + 2 * kAcc) * sizeof(u64) + 16;
+}
+
+int main_stages(int slices) {
+    const size_t fixed = main_smem(slices, 0);
+    const int fit = fixed < kSmemLimit ? (int)((kSmemLimit - fixed) / kSliceTile) : 0;
+    return std::min(kMaxStages, fit);
+}
+
+template <bool kFp8>
+cudaError_t launch_main(const CUtensorMap& mq, const CUtensorMap& mx, const MainParams& mp, int qblocks,
+                        cudaStream_t stream) {
+    auto kern = tc_main_kernel<kFp8>;
+    if (mp.stages < 2 || mp.stages > kMaxStages) return cudaErrorInvalidValue;
+    const size_t sm = main_smem(mp.slices, mp.stages);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    ProfScope ps(kFp8 ? "tc_main_kernel_fp8" : "tc_main_kernel_bf16", stream);
+    kern<<<dim3(mp.nchunks, qblocks), kThreads, sm, stream>>>(mq, mx, mp);
+    return cudaGetLastError();
+}
 
 template <bool kFp8, int MODE, int WMAX>
 cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& tp, int qblocks,
@@ -864,7 +1125,8 @@ cudaError_t launch_full(int wmax, const CUtensorMap& ma, const CUtensorMap& mb, 
 
 size_t lowp_scratch_bytes(const lhr_db* db, int nq, bool fp8, int W) {
     const LowpPlan pl = plan(db, nq, fp8, W);
-    return pl.codes_bytes + pl.qm_bytes + pl.pilot_bytes + pl.cnt_bytes + pl.cand_bytes + pl.partial_bytes;
+    return pl.codes_bytes + pl.qs_bytes + pl.pilot_bytes + pl.tau_bytes + pl.cnt_bytes + pl.cand_bytes +
+           pl.partial_bytes;
 }
 
 cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int W, int k, int64_t* idx, float* dist,
@@ -873,10 +1135,13 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
     unsigned char* base = reinterpret_cast<unsigned char*>(scratch);
     void* codes = base;
     base += pl.codes_bytes;
-    float* qm = reinterpret_cast<float*>(base);
-    base += pl.qm_bytes;
+    float* qs = reinterpret_cast<float*>(base);
+    base += pl.qs_bytes;
     u64* pilot = reinterpret_cast<u64*>(base);
     base += pl.pilot_bytes;
+    u64* tau_key = reinterpret_cast<u64*>(base);
+    float* tau_s = reinterpret_cast<float*>(base + a256((size_t)pl.nq_pad * sizeof(u64)));
+    base += pl.tau_bytes;
     unsigned* cnt = reinterpret_cast<unsigned*>(base);
     base += pl.cnt_bytes;
     u64* cand = reinterpret_cast<u64*>(base);
@@ -885,11 +1150,18 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
     cudaError_t e;
     {
         ProfScope ps("quantize_queries_kernel", stream);
+        unsigned* amax_bits = reinterpret_cast<unsigned*>(qs + 2);
+        if ((e = cudaMemsetAsync(amax_bits, 0, sizeof(unsigned), stream)) != cudaSuccess) return e;
+        const int64_t count = (int64_t)nq * db->dim;
+        const int ablocks = (int)std::min<int64_t>(std::max<int64_t>((count + 1023) / 1024, 1), db->sms);
+        query_amax_kernel<<<ablocks, 256, 0, stream>>>(q, count, amax_bits);
+        const float qmax = fp8 ? 448.0f : 1.0f;
         const int blocks = (pl.nq_pad * 32 + 255) / 256;
         if (fp8)
-            quantize_queries_kernel<true><<<blocks, 256, 0, stream>>>(q, nq, pl.nq_pad, db->dim, codes, qm);
+            quantize_queries_kernel<true><<<blocks, 256, 0, stream>>>(q, nq, pl.nq_pad, db->dim, amax_bits, qmax, qs, codes);
         else
-            quantize_queries_kernel<false><<<blocks, 256, 0, stream>>>(q, nq, pl.nq_pad, db->dim, codes, qm);
+            quantize_queries_kernel<false><<<blocks, 256, 0, stream>>>(q, nq, pl.nq_pad, db->dim, amax_bits, qmax, qs,
+                                                                       codes);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     CUtensorMap ma, mb, ms;
@@ -897,7 +1169,7 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
         return cudaErrorInvalidValue;
     TcParams tp{};
     tp.slices = db->dim * (fp8 ? 1 : 2) / kSliceBytes;
-    tp.qm = qm;
+    tp.qs = qs;
     tp.nq = nq;
     tp.W = W;
     tp.err = db->err;
@@ -914,20 +1186,29 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
         e = fp8 ? launch_tc<true, kModePilot, 32>(ma, ms, pp, pl.qblocks, stream, "tc_pilot_kernel_fp8")
                 : launch_tc<false, kModePilot, 32>(ma, ms, pp, pl.qblocks, stream, "tc_pilot_kernel_bf16");
         if (e != cudaSuccess) return e;
+        {
+            ProfScope ps("tau_kernel", stream);
+            tau_kernel<<<(pl.nq_pad + 7) / 8, 256, 0, stream>>>(pilot, pl.pilot.nchunks * kHalves, nq, pl.nq_pad,
+                                                                 tau_key, tau_s);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         // main pass: every key <= tau into the candidate buffers
         if ((e = cudaMemsetAsync(cnt, 0, (size_t)nq * sizeof(unsigned), stream)) != cudaSuccess) return e;
-        TcParams mp = tp;
+        MainParams mp{};
         mp.n = db->n;
+        mp.slices = tp.slices;
+        mp.stages = main_stages(tp.slices);
         mp.chunk_rows = pl.main.chunk_rows;
         mp.nchunks = pl.main.nchunks;
         mp.sn = fp8 ? db->sn8 : db->snb;
-        mp.pilot = pilot;
-        mp.pchunks = pl.pilot.nchunks;
+        mp.qs = qs;
+        mp.tau_s = tau_s;
+        mp.tau_key = tau_key;
         mp.cand = cand;
         mp.cnt = cnt;
-        mp.stages = tc_stages(mp.slices, kModeMain);
-        e = fp8 ? launch_tc<true, kModeMain, 32>(ma, mb, mp, pl.qblocks, stream, "tc_main_kernel_fp8")
-                : launch_tc<false, kModeMain, 32>(ma, mb, mp, pl.qblocks, stream, "tc_main_kernel_bf16");
+        mp.nq = nq;
+        mp.err = db->err;
+        e = fp8 ? launch_main<true>(ma, mb, mp, pl.qblocks, stream) : launch_main<false>(ma, mb, mp, pl.qblocks, stream);
         if (e != cudaSuccess) return e;
     }
     // full pass: always without a sample, otherwise only where a main pass fell short

@@ -62,7 +62,7 @@ def main(argv=None):
         torch.cuda.synchronize()
         lhr.lhr_profile_enable(False)
         for name in ("hier_fused", "scan_pilot", "wnorm", "scan_topk", "small_topk", "coarse_kernel", "collect", "shortlist",
-                     "aggregate", "quantize", "tc_pilot", "tc_main", "tc_full", "merge_rerank"):
+                     "aggregate", "quantize", "tc_pilot", "tau_kernel", "tc_main", "tc_full", "merge_rerank"):
             n, ms = lhr.lhr_profile_read(name)
             if n:
                 print(f"{a.case} {name}: {n} launches, mean {ms / n * 1e3:.1f} us")

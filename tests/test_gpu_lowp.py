@@ -22,12 +22,12 @@ def lhr():
     return m
 
 
-def _shortlist_separated(q, X, fmt, W, s_rows, codes):
+def _shortlist_separated(q, X, fmt, W, s_rows, codes, s_Q):
     """The oracle's W-th and (W+1)-th scores differ by more than the FP32
     accumulation error of the tensor-core score (so both sides shortlist the
-    same rows)."""
-    s_q, qc = olowp.quantize_rows(q[None], fmt)
-    sc = np.sort(olowp.lowp_scores(q, s_q[0], qc[0], s_rows, codes))
+    same rows). s_Q: the shared scale of the batch the query was served in."""
+    _, qc = olowp.quantize_queries(q[None], fmt, s_Q)
+    sc = np.sort(olowp.lowp_scores(q, s_Q, qc[0], s_rows, codes))
     if W >= sc.size:
         return True
     scale = float(q.astype(np.float64) @ q) + float(np.max(s_rows.astype(np.float64) ** 2 * (codes.astype(np.float64) ** 2).sum(1)))
@@ -52,10 +52,11 @@ def test_against_oracle(lhr, fmt_name, n, dim, nq, W, k):
     assert lhr.lhr_db_error(db) == 0
     gi, gd = idx.cpu().numpy()[:, 0], dist.cpu().numpy()[:, 0]
     s_rows, codes = olowp.quantize_rows(X, fmt)
+    s_Q = olowp.batch_scale(Q, fmt)
     o_idx, o_dist, _ = olowp.lowp_topk(Q, X, fmt, W, min(k + 1, W), codes=codes, s_rows=s_rows)
     checked = 0
     for qi in range(nq):
-        if not _shortlist_separated(Q[qi], X, fmt, W, s_rows, codes):
+        if not _shortlist_separated(Q[qi], X, fmt, W, s_rows, codes, s_Q):
             continue
         check_list(Q[qi], X, gi[qi], gd[qi], o_idx[qi], o_dist[qi], k, where=f"{fmt_name} q{qi}")
         checked += 1
@@ -83,11 +84,13 @@ def test_sampled_threshold_path_against_oracle(lhr, fmt_name):
     assert lhr.lhr_db_error(db) == 0
     gi, gd = idx.cpu().numpy()[:, 0], dist.cpu().numpy()[:, 0]
     s_rows, codes = olowp.quantize_rows(X, fmt)
+    s_Q = olowp.batch_scale(Q, fmt)
     sample = np.random.default_rng(32).choice(np.arange(1, nq), size=24, replace=False)
     for qi in [0] + sample.tolist():
-        if qi and not _shortlist_separated(Q[qi], X, fmt, W, s_rows, codes):
+        if qi and not _shortlist_separated(Q[qi], X, fmt, W, s_rows, codes, s_Q):
             continue
-        o_idx, o_dist, _ = olowp.lowp_topk(Q[qi:qi + 1], X, fmt, W, k + 1, codes=codes, s_rows=s_rows)
+        o_idx, o_dist, _ = olowp.lowp_topk(Q[qi:qi + 1], X, fmt, W, k + 1, codes=codes, s_rows=s_rows,
+                                           q_scale=s_Q)
         check_list(Q[qi], X, gi[qi], gd[qi], o_idx[0], o_dist[0], k, where=f"{fmt_name} q{qi}")
     # query 0: exact copies at distance 0, lowest rows first
     assert gi[0, 0] == 5 and np.all(gd[0] == 0.0)

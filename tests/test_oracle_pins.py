@@ -289,10 +289,44 @@ def test_lowp_score_equals_distance_on_exact_codes():
     X = np.array([[448.0, -224.0, 0.0, 8.0], [1.0, 2.0, -4.0, 448.0]], dtype=np.float32)
     q = np.array([[448.0, 0.0, 0.0, 0.0]], dtype=np.float32)
     s, c = lowp.quantize_rows(X, "e4m3")
-    sq, cq = lowp.quantize_rows(q, "e4m3")
+    sq, cq = lowp.quantize_queries(q, "e4m3")
     assert np.array_equal(c * s[:, None], X)
-    sc = lowp.lowp_scores(q[0], sq[0], cq[0], s, c)
+    sc = lowp.lowp_scores(q[0], sq, cq[0], s, c)
     assert np.allclose(sc, retrieval.sq_dist(q[0], X), rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_batch_scale_is_the_smallest_power_of_two_above_the_ratio(fmt):
+    qmax = lowp.QMAX[fmt]
+    rng = np.random.default_rng(23)
+    for _ in range(200):
+        Q = (rng.standard_normal((3, 8)) * 10.0 ** rng.uniform(-3, 3)).astype(np.float32)
+        s = float(lowp.batch_scale(Q, fmt))
+        ratio = float(np.float32(np.abs(Q).max()) / np.float32(qmax))
+        f, _ = np.frexp(s)
+        assert f == 0.5                        # a power of two
+        assert s / 2 < ratio <= s              # the smallest one >= the ratio
+    # ratio exactly a power of two: s equals it; an all-zero batch: 1; tiny: 2^-126
+    assert lowp.batch_scale(np.array([[qmax * 0.25, -1e-3]], np.float32), fmt) == np.float32(0.25)
+    assert lowp.batch_scale(np.zeros((2, 4), np.float32), fmt) == np.float32(1.0)
+    assert lowp.batch_scale(np.array([[1e-40]], np.float32), fmt) == np.float32(2.0 ** -126)
+    # the batch maximum, not each query's own, sets the scale
+    Q = np.array([[qmax, 0.0], [1.0, 0.0]], np.float32)
+    s, c = lowp.quantize_queries(Q, fmt)
+    assert s == np.float32(1.0) and c[1, 0] == 1.0
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_query_codes_do_not_depend_on_the_batch_power_of_two(fmt):
+    # With a power-of-two scale, s_Q q^ is the same whichever batch the query is
+    # in (values away from the format's subnormal range).
+    rng = np.random.default_rng(24)
+    q = (rng.uniform(0.5, 2.0, (1, 16)) * rng.choice([-1.0, 1.0], (1, 16))).astype(np.float32)
+    big = np.full((1, 16), 7.5, np.float32)
+    s1, c1 = lowp.quantize_queries(q, fmt)
+    s2, c2 = lowp.quantize_queries(np.concatenate([q, big]), fmt)
+    assert s2 > s1
+    assert np.array_equal(c1[0] * s1, c2[0] * s2)
 
 
 # ---------------------------------------------------------------- soft retrieval
