@@ -505,35 +505,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAcc * kTile) : "memory");
 }
 
-// Main pass, a rare run of columns C0..C1-1 of group G in which this thread's
-// row has a key <= the query's tau: such keys go to the query's candidate
-// buffer, one atomic each. score < tau_s decides without the key; on an exact
-// score tie the row index decides against the threshold key.
-template <int G, int C0, int C1>
-__device__ __forceinline__ void main_survivors(const MainParams& p, const uint32_t (&v)[32], const float2 (&ntau)[32],
-                                               float A, float B, uint32_t row, int64_t q0) {
-#pragma unroll
-    for (int j = C0; j < C1; ++j) {
-        const float2 nt = ntau[G * 16 + j / 2];
-        const float tau_s = -((j & 1) ? nt.y : nt.x);
-        const float score = fmaf(B, __uint_as_float(v[j]), A);
-        if (score <= tau_s) {
-            const int64_t qi = q0 + G * 32 + j;
-            const u64 key = score_key(score, row);
-            if (qi < p.nq && (score < tau_s || key <= __ldg(p.tau_key + qi))) {
-                const unsigned pos = atomicAdd(p.cnt + qi, 1u);
-                if (pos < (unsigned)kCap) p.cand[(size_t)qi * kCap + pos] = key;
-            }
-        }
-    }
-}
-
-// Minima of score - tau_q over the four column runs 0-8, 9-17, 18-26, 27-31 of
-// group G, score = fma(B, dot, A) in packed pairs (exact sign: the difference
-// of two floats is <= 0 iff score <= tau_q).
+// Minimum over the 32 columns of group G of score - tau_q, score =
+// fma(B, dot, A) in packed pairs (exact sign: the difference of two floats is
+// <= 0 iff score <= tau_q).
 template <int G>
-__device__ __forceinline__ float4 main_group_min(const uint32_t (&v)[32], const float2 (&ntau)[32], float2 A2,
-                                                 float2 B2) {
+__device__ __forceinline__ float main_group_min(const uint32_t (&v)[32], const float2 (&ntau)[32], float2 A2, float2 B2) {
     float d[32];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
@@ -546,18 +522,59 @@ __device__ __forceinline__ float4 main_group_min(const uint32_t (&v)[32], const 
 #pragma unroll
     for (int i = 0; i < 10; ++i) t[i] = fmin3(d[3 * i], d[3 * i + 1], d[3 * i + 2]);
     t[10] = fminf(d[30], d[31]);
-    return make_float4(fmin3(t[0], t[1], t[2]), fmin3(t[3], t[4], t[5]), fmin3(t[6], t[7], t[8]), fminf(t[9], t[10]));
+    const float u0 = fmin3(t[0], t[1], t[2]), u1 = fmin3(t[3], t[4], t[5]), u2 = fmin3(t[6], t[7], t[8]);
+    return fminf(fmin3(u0, u1, u2), fminf(t[9], t[10]));
 }
 
+// Survivors of the main pass. Lane l of an epilogue warp owns column l of each
+// of its two 32-column groups (one query each) and stages that query's keys in
+// kOwnSlots shared-memory slots; a full stage goes to the query's candidate
+// buffer with one atomic.
+constexpr int kOwnSlots = 8;
+
+struct Owner {
+    u64* slot;        // slot i of group g at slot[(g * kOwnSlots + i) * kEpiThreads]
+    float tau_s[2];   // thresholds of the two owned queries (-inf when past nq)
+    int64_t q[2];     // the owned queries
+    int n[2];         // keys staged per owned query
+};
+
+__device__ __noinline__ void flush_owner(const MainParams& p, Owner& o, int g) {
+    const int n = o.n[g];
+    const unsigned pos = atomicAdd(p.cnt + o.q[g], (unsigned)n);
+    for (int i = 0; i < n; ++i)
+        if (pos + i < (unsigned)kCap)
+            p.cand[(size_t)o.q[g] * kCap + pos + i] = o.slot[(g * kOwnSlots + i) * kEpiThreads];
+    o.n[g] = 0;
+}
+
+// Group G of a tile in which some lane's row has a key <= its query's tau (the
+// warp's ballot `ev`): for each such row in turn the warp moves the row's 32
+// dot products across the lanes (lane l gets column l), and every lane checks
+// its own query. score < tau_s decides without the key; on an exact score tie
+// the row index decides against the threshold key.
 template <int G>
-__device__ __forceinline__ void main_group(const MainParams& p, const uint32_t (&v)[32], const float2 (&ntau)[32],
-                                           float A, float B, bool rowvalid, uint32_t row, int64_t q0) {
-    const float4 mn = main_group_min<G>(v, ntau, make_float2(A, A), make_float2(B, B));
-    if (rowvalid && fminf(fmin3(mn.x, mn.y, mn.z), mn.w) <= 0.f) {
-        if (mn.x <= 0.f) main_survivors<G, 0, 9>(p, v, ntau, A, B, row, q0);
-        if (mn.y <= 0.f) main_survivors<G, 9, 18>(p, v, ntau, A, B, row, q0);
-        if (mn.z <= 0.f) main_survivors<G, 18, 27>(p, v, ntau, A, B, row, q0);
-        if (mn.w <= 0.f) main_survivors<G, 27, 32>(p, v, ntau, A, B, row, q0);
+__device__ __forceinline__ void main_survivors(const MainParams& p, const uint32_t (&v)[32], float A, float B,
+                                               uint32_t row, unsigned ev, int lane, Owner& o) {
+    while (ev) {
+        const int e = __ffs(ev) - 1;
+        ev &= ev - 1;
+        const float Be = __shfl_sync(kFull, B, e), Ae = __shfl_sync(kFull, A, e);
+        const uint32_t rowe = __shfl_sync(kFull, row, e);
+        uint32_t x = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t t = __shfl_sync(kFull, v[j], e);
+            x = lane == j ? t : x;
+        }
+        const float score = fmaf(Be, __uint_as_float(x), Ae);
+        if (score <= o.tau_s[G]) {
+            const u64 key = score_key(score, rowe);
+            if (score < o.tau_s[G] || key <= __ldg(p.tau_key + o.q[G])) {
+                o.slot[(G * kOwnSlots + o.n[G]) * kEpiThreads] = key;
+                if (++o.n[G] == kOwnSlots) flush_owner(p, o, G);
+            }
+        }
     }
 }
 
@@ -573,7 +590,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int stages = p.stages;
     unsigned char* sQ = smem;                                   // slices x 16 KB: the block's query codes
     unsigned char* sX = sQ + (size_t)p.slices * kSliceTile;     // stages x 16 KB: database slices
-    u64* full = reinterpret_cast<u64*>(sX + (size_t)stages * kSliceTile);
+    u64* own_slot = reinterpret_cast<u64*>(sX + (size_t)stages * kSliceTile);  // 2 kOwnSlots x kEpiThreads
+    u64* full = own_slot + 2 * kOwnSlots * kEpiThreads;
     u64* empty = full + kMaxStages;
     u64* q_full = empty + kMaxStages;
     u64* acc_full = q_full + 1;
@@ -698,6 +716,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = 0; i < 32; ++i)
             ntau[i] = make_float2(-__ldg(p.tau_s + q0 + 2 * i), -__ldg(p.tau_s + q0 + 2 * i + 1));
         const float m = __ldg(p.qs + 1);
+        Owner o;
+        o.slot = own_slot + (threadIdx.x - 64);
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            o.q[g] = q0 + 32 * g + lane;
+            o.tau_s[g] = o.q[g] < p.nq ? __ldg(p.tau_s + o.q[g]) : -__int_as_float(0x7f800000);
+            o.n[g] = 0;
+        }
         float2 sn_next = ntiles > 0 ? __ldg(p.sn + row0 + rl) : make_float2(0.f, 0.f);
         for (int t = 0; t < ntiles; ++t) {
             const int a = t % kAcc;
@@ -720,12 +746,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_ld_wait(vb);
             const float B = m * sn.x, A = sn.y;
             const bool rowvalid = r + rl < row1;
-            main_group<0>(p, va, ntau, A, B, rowvalid, (uint32_t)(r + rl), q0);
-            main_group<1>(p, vb, ntau, A, B, rowvalid, (uint32_t)(r + rl), q0);
+            const float2 A2 = make_float2(A, A), B2 = make_float2(B, B);
+            const unsigned eva = __ballot_sync(kFull, rowvalid && main_group_min<0>(va, ntau, A2, B2) <= 0.f);
+            const unsigned evb = __ballot_sync(kFull, rowvalid && main_group_min<1>(vb, ntau, A2, B2) <= 0.f);
+            if (eva) main_survivors<0>(p, va, A, B, (uint32_t)(r + rl), eva, lane, o);
+            if (evb) main_survivors<1>(p, vb, A, B, (uint32_t)(r + rl), evb, lane, o);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[a]);
         }
+        for (int g = 0; g < 2; ++g)
+            if (o.n[g]) flush_owner(p, o, g);
     }
     tc_fence_before();
     __syncthreads();
@@ -1077,7 +1108,8 @@ int tc_stages(int slices, int mode) {
 size_t tc_smem(int slices, int stages, int mode) { return tc_smem_fixed(slices, mode) + (size_t)stages * kSliceTile; }
 
 size_t main_smem(int slices, int stages) {
-    return 1024 + (size_t)(slices + stages) * kSliceTile + (2 * kMaxStages + 1 + 2 * kAcc) * sizeof(u64) + 16;
+    return 1024 + (size_t)(slices + stages) * kSliceTile + (size_t)2 * kOwnSlots * kEpiThreads * sizeof(u64) +
+           (2 * kMaxStages + 1 + 2 * kAcc) * sizeof(u64) + 16;
 }
 
 int main_stages(int slices) {
