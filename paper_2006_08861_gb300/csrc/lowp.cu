@@ -883,6 +883,52 @@ __device__ void warp_sort(u64* a, int n, int lane) {
     }
 }
 
+// 64 keys of a warp, element e * 32 + lane in v[e], sorted ascending (bitonic).
+__device__ __forceinline__ void warp_sort64(u64 (&v)[2], int lane) {
+#pragma unroll
+    for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride == 32) {
+                const u64 lo = v[0] < v[1] ? v[0] : v[1], hi = v[0] < v[1] ? v[1] : v[0];
+                v[0] = lo;
+                v[1] = hi;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const u64 o = __shfl_xor_sync(kFull, v[e], stride);
+                    const bool asc = ((e * 32 + lane) & size) == 0;
+                    const bool keep_min = ((lane & stride) == 0) == asc;
+                    v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
+                }
+            }
+        }
+    }
+}
+
+// best (64 sorted keys, layout of warp_sort64) becomes the 64 smallest of best
+// and c (also sorted): min(best_i, c_{63-i}) is a bitonic sequence holding
+// them, which a half-cleaner cascade sorts.
+__device__ __forceinline__ void warp_merge64(u64 (&best)[2], const u64 (&c)[2], int lane) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const u64 r = __shfl_sync(kFull, c[1 - e], 31 - lane);
+        best[e] = best[e] < r ? best[e] : r;
+    }
+    const u64 lo = best[0] < best[1] ? best[0] : best[1], hi = best[0] < best[1] ? best[1] : best[0];
+    best[0] = lo;
+    best[1] = hi;
+#pragma unroll
+    for (int stride = 16; stride > 0; stride >>= 1) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const u64 o = __shfl_xor_sync(kFull, best[e], stride);
+            const bool keep_min = (lane & stride) == 0;
+            best[e] = keep_min ? (o < best[e] ? o : best[e]) : (o > best[e] ? o : best[e]);
+        }
+    }
+}
+
 // Number of keys <= x among the query's per-chunk lists.
 __device__ int count_le(const u64* P, int total, u64 x, int lane) {
     int c = 0;
@@ -907,7 +953,34 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_rerank_kernel(
     u64* cw = cand_sm + (size_t)warp * kCap;
     const unsigned c = cand != nullptr ? cnt[qi] : 0u;
     int n = 0;
-    if (cand != nullptr && c >= (unsigned)W && c <= (unsigned)kCap) {
+    bool sorted = false;
+    if (cand != nullptr && c >= (unsigned)W && c <= (unsigned)kCap && W <= 64) {
+        // the main pass collected every key <= tau, and there are W..kCap of
+        // them: a running 64 smallest in registers, one 64-key chunk at a time
+        // (the next chunk's loads in flight; chunks with nothing below the
+        // current 64th key skipped)
+        const int nc = (int)c;
+        const u64* cq = cand + (size_t)qi * kCap;
+        u64 best[2] = {kKeyEmpty, kKeyEmpty}, nxt[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) nxt[e] = e * 32 + lane < nc ? __ldcg(cq + e * 32 + lane) : kKeyEmpty;
+        for (int base = 0; base < nc; base += 64) {
+            u64 cur[2] = {nxt[0], nxt[1]};
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int i = base + 64 + e * 32 + lane;
+                nxt[e] = i < nc ? __ldcg(cq + i) : kKeyEmpty;
+            }
+            const u64 worst = __shfl_sync(kFull, best[1], 31);
+            if (!__any_sync(kFull, cur[0] < worst || cur[1] < worst)) continue;
+            warp_sort64(cur, lane);
+            warp_merge64(best, cur, lane);
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) cw[e * 32 + lane] = best[e];
+        n = W;
+        sorted = true;
+    } else if (cand != nullptr && c >= (unsigned)W && c <= (unsigned)kCap) {
         // the main pass collected every key <= tau, and there are W..kCap of them
         n = (int)c;
         for (int i = lane; i < n; i += 32) cw[i] = __ldcg(cand + (size_t)qi * kCap + i);
@@ -944,12 +1017,14 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_rerank_kernel(
         }
         n = min(n, kCap);
     }
-    int p2 = 32;
-    while (p2 < n) p2 <<= 1;
     __syncwarp();
-    for (int i = n + lane; i < p2; i += 32) cw[i] = kKeyEmpty;
-    __syncwarp();
-    warp_sort(cw, p2, lane);
+    if (!sorted) {
+        int p2 = 32;
+        while (p2 < n) p2 <<= 1;
+        for (int i = n + lane; i < p2; i += 32) cw[i] = kKeyEmpty;
+        __syncwarp();
+        warp_sort(cw, p2, lane);
+    }
     const int take = min(n, W);
     // FP32 direct re-rank of the shortlist, four rows in flight
     const int D4 = D / 4;
