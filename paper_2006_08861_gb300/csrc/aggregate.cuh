@@ -85,6 +85,51 @@ __device__ __noinline__ void warp_sort_smem(u64* keys, int n, int lane) {
     for (int e = 0; e < E; ++e) keys[e * 32 + lane] = v[e];
 }
 
+// Initialization and binning of a window of at most 32 E candidate slots in
+// registers: every slot's row, distance and tile key loaded in one round,
+// rows and distances compacted (padding rows skipped) into cand_rows /
+// cand_d, and the tile keys sorted in registers with the padding slots' empty
+// keys last, written to keys[0, 32 E). Returns the candidate count C.
+template <int E>
+__device__ __forceinline__ int init_sorted(const AggParams& p, long long b0, long long total, u64* keys,
+                                           int* cand_rows, float* cand_d, int lane, bool sort) {
+    const AggArgs& a = p.a;
+    const unsigned below = (1u << lane) - 1u;
+    int64_t r[E];
+    float d[E];
+    u64 v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const long long i = e * 32 + lane;
+        r[e] = i < total ? __ldcg(a.idx + b0 + i) : -1;  // may come from another CTA of the launch
+        d[e] = (i < total && a.dist != nullptr) ? __ldcg(a.dist + b0 + i) : 0.f;
+        v[e] = (i < total && p.tile_keys != nullptr) ? __ldcg(p.tile_keys + b0 + i) : kKeyEmpty;
+    }
+    int C = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const bool bad = r[e] >= p.n;
+        if (bad) record_error(p.err, kErrInvalidArg);
+        const bool take = r[e] >= 0 && !bad;
+        const unsigned m = __ballot_sync(kFull, take);
+        const int pos = C + __popc(m & below);
+        if (take) {
+            cand_rows[pos] = (int)r[e];
+            cand_d[pos] = d[e];
+            if (p.tile_keys == nullptr) v[e] = tile_key(p.tile[2 * r[e]], p.tile[2 * r[e] + 1]);
+        } else {
+            v[e] = kKeyEmpty;
+        }
+        C += __popc(m);
+    }
+    if (sort) {
+        warp_sort_regs<E>(v, lane);
+#pragma unroll
+        for (int e = 0; e < E; ++e) keys[e * 32 + lane] = v[e];
+    }
+    return C;
+}
+
 // Algorithm 2 for one window of at most kWarpCand candidate slots, by a single
 // warp: the same steps, tie rules and integer tests as the block path of
 // aggregate.cu, with warp shuffles in place of block barriers.
@@ -93,9 +138,21 @@ __device__ inline void aggregate_warp(const AggParams& p, int w, long long b0, l
     const AggArgs& a = p.a;
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
-    // initialization: rows -> tiles, padding rows skipped, compacted in order
+    // initialization: rows -> tiles, padding rows skipped, compacted in order;
+    // up to 128 slots in registers, sorted there for the binning below
     int C = 0;
-    for (long long base = 0; base < total; base += 32) {
+    bool sorted = false;
+    if (total <= 32) {
+        C = init_sorted<1>(p, b0, total, keys, cand_rows, cand_d, lane, a.mode != 2);
+        sorted = true;
+    } else if (total <= 64) {
+        C = init_sorted<2>(p, b0, total, keys, cand_rows, cand_d, lane, a.mode != 2);
+        sorted = true;
+    } else if (total <= 128) {
+        C = init_sorted<4>(p, b0, total, keys, cand_rows, cand_d, lane, a.mode != 2);
+        sorted = true;
+    }
+    for (long long base = 0; !sorted && base < total; base += 32) {
         const long long i = base + lane;
         const int64_t r = i < total ? __ldcg(a.idx + b0 + i) : -1;  // may come from another CTA of the launch
         const bool bad = r >= p.n;
@@ -121,7 +178,9 @@ __device__ inline void aggregate_warp(const AggParams& p, int w, long long b0, l
     if (a.mode != 2) {
         // step 2: binning = sort the tile keys (in registers), count runs
         static_assert(kWarpCand == 32 * 32, "sort widths below cover kWarpCand");
-        if (C <= 32) warp_sort_smem<1>(keys, C, lane);
+        if (sorted) {
+            // keys[0, C) hold the candidates' sorted keys (the empty keys follow)
+        } else if (C <= 32) warp_sort_smem<1>(keys, C, lane);
         else if (C <= 64) warp_sort_smem<2>(keys, C, lane);
         else if (C <= 128) warp_sort_smem<4>(keys, C, lane);
         else if (C <= 256) warp_sort_smem<8>(keys, C, lane);

@@ -214,9 +214,65 @@ __device__ void write_topk(const HierParams& p, int f, const u64* fk, unsigned t
     __syncthreads();
 }
 
+// Top k (k <= 32) of at most kHT distinct keys, by warps: each warp sorts
+// its 32 keys (one per lane, a bitonic network), then four levels of
+// pairwise merges keep the 32 smallest -- warp w takes its list and warp w +
+// h's reversed, the elementwise minima (a bitonic sequence holding the 32
+// smallest) sorted by a half-cleaner cascade -- and warp 0 writes the first k.
+// `lists` holds kHW x 32 keys.
+__device__ void select_topk_small(const HierParams& p, int f, const u64* fk, unsigned total, u64* lists,
+                                  unsigned* res) {
+    const int t = threadIdx.x, warp = t / 32, lane = t % 32;
+    u64 v = (unsigned)t < total ? fk[t] : kKeyEmpty;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const u64 o = __shfl_xor_sync(kFull, v, stride);
+            const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
+            v = keep_min ? (o < v ? o : v) : (o > v ? o : v);
+        }
+    }
+    lists[warp * 32 + lane] = v;
+    __syncthreads();
+#pragma unroll
+    for (int h = kHW / 2; h >= 1; h >>= 1) {
+        if (warp < h) {
+            const u64 a = lists[warp * 32 + lane], b = lists[(warp + h) * 32 + (31 - lane)];
+            u64 m = a < b ? a : b;
+#pragma unroll
+            for (int stride = 16; stride > 0; stride >>= 1) {
+                const u64 o = __shfl_xor_sync(kFull, m, stride);
+                m = (lane & stride) == 0 ? (o < m ? o : m) : (o > m ? o : m);
+            }
+            lists[warp * 32 + lane] = m;  // warp w's own slot: no other warp reads it at this level
+        }
+        __syncthreads();
+    }
+    if (warp == 0 && lane < p.k) {
+        const u64 r0 = lists[lane];
+        const size_t o = (size_t)f * p.k + lane;
+        if (r0 == kKeyEmpty) {
+            p.idx[o] = -1;
+            p.dist[o] = __int_as_float(0x7f800000);
+        } else {
+            const uint32_t r = key_row(r0);
+            p.idx[o] = (int64_t)r;
+            p.dist[o] = key_dist(r0);
+            if (p.ctk != nullptr) p.ctk[o] = agg::tile_key(__ldg(p.ap.tile + 2 * r), __ldg(p.ap.tile + 2 * r + 1));
+        }
+    }
+    __syncthreads();
+}
+
 // Top k of fk[0, total) (distinct keys) written as frame f's result.
 __device__ void select_topk(const HierParams& p, int f, const u64* fk, unsigned total, unsigned* hs, u64* outk,
                             unsigned* res, unsigned* tmp) {
+    static_assert(kHW * 32 * sizeof(u64) <= kBins * sizeof(unsigned), "the warp lists fit the histogram space");
+    if (total <= (unsigned)kHT && p.k <= 32) {
+        select_topk_small(p, f, fk, total, reinterpret_cast<u64*>(hs), res);
+        return;
+    }
     u64 kth = ~0ull;
     if (total > (unsigned)p.k) {
         // the keys' range first, so the radix passes split it from the start
