@@ -30,11 +30,17 @@
 //   query. The row's (m s_j, n_j) sit in two registers (loaded from global
 //   memory a tile ahead) and the thread's 64 queries' thresholds tau_q in 64
 //   more, so scoring reads no shared memory: per pair of columns one packed
-//   fma and one packed subtract (score - tau_q), then a minimum over 32
-//   columns. Keys <= tau_q (rare) go to the query's candidate buffer with one
-//   warp-aggregated atomic per column. tau_q is the 8th smallest sample key
-//   of the query (pilot pass), so at least 8 keys, about 8 x 64 in
-//   expectation, qualify.
+//   fma and one packed add (score - tau_q), then a minimum over 32 columns.
+//   A row with a key <= tau_q (rare; a warp ballot) is moved across the warp
+//   with shuffles so that lane l checks the query it owns (column l), and
+//   stages the key in shared memory; eight staged keys of a query go to its
+//   candidate buffer with one atomic. tau_q is the 8th smallest sample key of
+//   the query (pilot pass, then tau_kernel), so at least 8 keys, about 8 x 64
+//   in expectation, qualify.
+//   Under the tensor core's and TMA's shared-memory traffic a shared or local
+//   load in the epilogue waits about a microsecond; the scoring loop issues
+//   none, and the rare path is kept small (it runs from the instruction cache
+//   beside the scoring loop).
 // tc_kernel (pilot and fallback passes): the query block is the A operand, a
 //   thread is a query and reads each column's (s_j, n_j) from shared memory
 //   (a 1-D bulk copy per tile):
@@ -47,9 +53,11 @@
 //            buffer. When run after a main pass it exits at once unless a
 //            query of its block collected fewer than W or more than kCap keys.
 // merge_rerank_kernel, one warp per query: the shortlist is the W smallest
-//   keys of the query's candidate buffer (or, after the full pass, of its
-//   per-chunk lists cut at the smallest chunk's W-th key); its rows are
-//   re-scored with the exact FP32 direct form and the top k kept.
+//   keys of the query's candidate buffer (for W <= 64 a running 64 smallest in
+//   registers over 64-key chunks; else, and after the full pass, a sort of the
+//   candidates or of the per-chunk lists cut at the smallest chunk's W-th
+//   key); its rows are re-scored with the exact FP32 direct form and the top
+//   k kept.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
