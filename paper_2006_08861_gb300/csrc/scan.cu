@@ -7,7 +7,10 @@
 // kept small.
 //   * One CTA per (row chunk, block of QB query frames). A row chunk is a
 //     contiguous range of one subspace; the chunk table is built with the
-//     database.
+//     database. The frame block is the grid's fastest index, so the CTAs
+//     resident together share chunks: with many frame blocks a chunk comes
+//     from DRAM once and from L2 for the other blocks (chunk-fastest order
+//     would stream the whole database from DRAM once per frame block).
 //   * A producer thread streams the chunk through shared memory with 1-D bulk
 //     copies (cp.async.bulk, 16 rows per stage) into an mbarrier ring; consumer
 //     warp w owns the stages s with s % warps == w, so its parity waits always
@@ -143,8 +146,8 @@ __global__ void __launch_bounds__((kMaxWarps + 1) * 32, 1) scan_topk_kernel(cons
     int* flags = reinterpret_cast<int*>(thr_sh + QB);
     volatile int* abort_flag = flags;
 
-    const int chunk = blockIdx.x;
-    const int qblock = blockIdx.y;
+    const int qblock = blockIdx.x;
+    const int chunk = blockIdx.y;
     const int4 ch = p.chunks[chunk];
     const int row0 = ch.x, row1 = ch.y;
     const int iters = (row1 - row0 + kRPS - 1) / kRPS;
@@ -765,7 +768,8 @@ cudaError_t launch_t(const ScanConfig& c, const ScanParams& p, int nqb, const ch
     auto kern = scan_topk_kernel<QB, CPL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(p.nchunks, nqb);
+    if (p.nchunks > 65535) return cudaErrorInvalidValue;
+    dim3 grid(nqb, p.nchunks);
     ProfScope ps(label, stream);
     kern<<<grid, (c.warps + 1) * 32, c.smem, stream>>>(p);
     return cudaGetLastError();
