@@ -81,6 +81,31 @@ def test_random_windows_against_oracle(lhr, mode):
     assert np.max(np.abs(gxy - oxy)) <= tol
 
 
+@pytest.mark.parametrize("mode", ["tile", "centroid", "softmax"])
+def test_small_windows_against_oracle(lhr, mode):
+    # windows of 1..128 slots (the register path: 32, 64 and 128 slots per
+    # warp), with padding rows and repeated rows
+    rng = np.random.default_rng(13)
+    n = 400
+    xy = rng.uniform(0, 20, size=(n, 2))
+    xy[:40] = rng.uniform(5, 6, size=(40, 2))
+    db = _db_for_xy(lhr, xy)
+    cands, dists = [], []
+    for size in [1, 2, 31, 32, 33, 63, 64, 65, 100, 127, 128, 129]:
+        c = rng.integers(0, n, size=size)
+        if size > 2:
+            c[::4] = rng.integers(0, 40, size=len(c[::4]))
+            c[1::7] = -1
+        cands.append(c)
+        dists.append(rng.uniform(0.1, 5.0, size=size).astype(np.float32))
+    gxy, gst = _agg(lhr, db, cands, mode, dists=dists if mode == "softmax" else None, tau=0.7)
+    oxy, ost = oagg.aggregate_windows(cands, xy, dists=dists if mode == "softmax" else None, mode=mode,
+                                      tau=float(np.float32(0.7)))
+    assert np.array_equal(gst, ost)
+    tol = 0.0 if mode == "tile" else 1e-9
+    assert np.max(np.abs(gxy - oxy)) <= tol
+
+
 def test_parameters_top_c_radius_toler(lhr):
     rng = np.random.default_rng(12)
     xy = rng.uniform(0, 8, size=(300, 2))

@@ -42,6 +42,8 @@ def test_full_shortlist_equals_exhaustive(lhr):
     (9_001, 128, 32, 100, 20, 3),
     (3_000, 36, 4, 64, 7, 9),      # prefix of one float4, more than 8 frames
     (5_000, 256, 128, 4096, 32, 2),  # widest prefix, largest shortlist
+    (8_000, 128, 64, 500, 32, 6),    # fused path: k = 32 of a 500-row shortlist (warp merges)
+    (7_000, 64, 16, 33, 32, 4),      # fused path: shortlist just above k
 ])
 def test_against_oracle(lhr, n, dim, dc, S, k, nq):
     rng = np.random.default_rng(n + S)
