@@ -604,11 +604,14 @@ def run_differentiation(args, rank, world, local):
     torch.cuda.synchronize()
     lhr.lhr_profile_enable(False)
     share = {}
-    for name in ("wnorm_kernel", "scan_pilot", "scan_topk_kernel", "soft_forward_kernel", "soft_backward_kernel"):
+    for name in ("wnorm_kernel", "scan_pilot", "scan_topk_kernel", "many_bound_kernel", "many_kernel",
+                 "many_select_kernel", "soft_forward_kernel", "soft_backward_kernel"):
         n_l, t_ms = lhr.lhr_profile_read(name, reset=True)
         if n_l:
             share[name] = (n_l, t_ms)
-    n_scan, t_scan = share.get("scan_topk_kernel", (1, float("nan")))
+    # the selection's main kernel: the many-frame pass (>= 64 frames) or the streaming scan
+    sel = "many_kernel" if "many_kernel" in share else "scan_topk_kernel"
+    n_scan, t_scan = share.get(sel, (1, float("nan")))
     # the selection is FP32 SIMT arithmetic: 3 flops per (frame, row, dim) (sub, fma)
     flops = 3.0 * B * m * c["n"] * c["dim"]
     alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock (GHz), TFLOP/s
@@ -638,7 +641,7 @@ def run_differentiation(args, rank, world, local):
         "config": {"workload": "differentiation", "desc": "N=200000 D=256, B=256 windows of m=5, k=32, w=1, "
                                                           "tau=0.1: soft retrieval forward + location loss + backward",
                    "l2": "flushed before every timed step", "launch": "eager (autograd)"},
-        "roofline": {"bound": "alu", "kernel": "scan_topk_kernel (weighted selection)",
+        "roofline": {"bound": "alu", "kernel": f"{sel} (weighted selection)",
                      "achieved": round(achieved, 2), "peak": round(alu_peak, 1),
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (derived)", "unit": "TFLOP/s",
                      "frac": round(achieved / alu_peak, 4), "traffic": None,

@@ -61,6 +61,52 @@ __device__ __forceinline__ void list_merge_keys(u64& L, const u64* keys, int n, 
 }
 
 // ---------------------------------------------------------------- PTX wrappers
+// 64 keys of a warp, element e * 32 + lane in v[e], sorted ascending (bitonic).
+__device__ __forceinline__ void warp_sort64(u64 (&v)[2], int lane) {
+#pragma unroll
+    for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride == 32) {
+                const u64 lo = v[0] < v[1] ? v[0] : v[1], hi = v[0] < v[1] ? v[1] : v[0];
+                v[0] = lo;
+                v[1] = hi;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const u64 o = __shfl_xor_sync(kFull, v[e], stride);
+                    const bool asc = ((e * 32 + lane) & size) == 0;
+                    const bool keep_min = ((lane & stride) == 0) == asc;
+                    v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
+                }
+            }
+        }
+    }
+}
+
+// best (64 sorted keys, layout of warp_sort64) becomes the 64 smallest of best
+// and c (also sorted): min(best_i, c_{63-i}) is a bitonic sequence holding
+// them, which a half-cleaner cascade sorts.
+__device__ __forceinline__ void warp_merge64(u64 (&best)[2], const u64 (&c)[2], int lane) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const u64 r = __shfl_sync(kFull, c[1 - e], 31 - lane);
+        best[e] = best[e] < r ? best[e] : r;
+    }
+    const u64 lo = best[0] < best[1] ? best[0] : best[1], hi = best[0] < best[1] ? best[1] : best[0];
+    best[0] = lo;
+    best[1] = hi;
+#pragma unroll
+    for (int stride = 16; stride > 0; stride >>= 1) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const u64 o = __shfl_xor_sync(kFull, best[e], stride);
+            const bool keep_min = (lane & stride) == 0;
+            best[e] = keep_min ? (o < best[e] ? o : best[e]) : (o > best[e] ? o : best[e]);
+        }
+    }
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }

@@ -102,6 +102,14 @@ struct ProfScope {
 // `pilot`: seed the scan's thresholds from the pilot sample when the database
 // has one (same results, fewer exact recomputes; more scratch).
 size_t scan_scratch_bytes(const lhr_db* db, int nq, int k, bool pilot);
+// many.cu: exhaustive top k for many frames at once (register-tiled expanded
+// form over the pilot's bound, exact re-score of the candidates)
+bool many_eligible(const lhr_db* db, int nq, int k);
+size_t many_scratch_bytes(int nq);
+cudaError_t launch_many(const lhr_db* db, const float* q, int nq, int k, const float* w, const float* xn,
+                        const float* xmax_w, const unsigned* bmin, float margin_scale, int64_t* idx, float* dist,
+                        void* scratch, cudaStream_t stream);
+
 cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t* idx, float* dist,
                         void* scratch, bool pilot, cudaStream_t stream);
 // Weighted exhaustive scan: d_w = sum_j w_j (q_j - x_j)^2, w device (D), >= 0.

@@ -791,6 +791,16 @@ struct ScanSrc {
     const int32_t* perm;  // nullable
 };
 
+// 2 (gamma_{D+4} + 3u) with u = 2^-24 and gamma_m = m u / (1 - m u), slightly
+// rounded up (the weighted form rounds w q and w (q - x) once more): times
+// (max ||x|| + ||q||)^2, it bounds the difference between the expanded-form
+// distance and the exact direct form.
+float scan_margin_scale(int dim) {
+    const double u = 1.0 / 16777216.0;
+    const double gamma = (dim + 4) * u / (1.0 - (dim + 4) * u);
+    return (float)(2.0 * (gamma + 3.0 * u) * 1.0001);
+}
+
 size_t pass_bytes(const ScanConfig& c, int nchunks, int n_sub, int nq, int k) {
     const size_t nqb = (nq + c.qb - 1) / c.qb;
     return align256(nqb * c.qb * (size_t)nchunks * k * sizeof(u64)) + align256(nqb * sizeof(unsigned)) +
@@ -855,11 +865,7 @@ cudaError_t scan_pass(const lhr_db* db, const ScanSrc& src, const char* label, c
         p.xnorm = wt->xnw;
         p.xmax_w = wt->xmax_w;
     }
-    // 2 (gamma_{D+4} + 3u) with u = 2^-24 and gamma_m = m u / (1 - m u), slightly
-    // rounded up (the weighted form rounds w q and w (q - x) once more)
-    const double u = 1.0 / 16777216.0;
-    const double gamma = (db->dim + 4) * u / (1.0 - (db->dim + 4) * u);
-    p.margin_scale = (float)(2.0 * (gamma + 3.0 * u) * 1.0001);
+    p.margin_scale = scan_margin_scale(db->dim);
     // max ||x|| over the whole database bounds the sample's too
     p.xmax = (float)(sqrt((double)db->xnorm_max) * 1.0001);
     p.partial = reinterpret_cast<u64*>(scratch);
@@ -888,6 +894,7 @@ cudaError_t scan_pass(const lhr_db* db, const ScanSrc& src, const char* label, c
 }  // namespace
 
 size_t scan_scratch_bytes(const lhr_db* db, int nq, int k, bool pilot) {
+    if (pilot && use_pilot(db, nq) && many_eligible(db, nq, k)) return pilot_bytes(db, nq) + many_scratch_bytes(nq);
     const ScanConfig c = choose_config(db, nq);
     const size_t main = pass_bytes(c, db->nchunks, db->n_sub, nq, k);
     return pilot && use_pilot(db, nq) ? main + pilot_bytes(db, nq) : main;
@@ -904,6 +911,14 @@ cudaError_t scan_with_pilot(const lhr_db* db, const float* q, int nq, int k, con
                             float* dist, void* scratch, bool pilot, cudaStream_t stream) {
     const ScanSrc full{db->X, db->xnorm, db->chunks, db->nchunks, db->chunk_off, db->perm};
     unsigned* bmin = nullptr;
+    if (pilot && use_pilot(db, nq) && many_eligible(db, nq, k)) {
+        // many frames: the pilot's bound, then the register-tiled pass (many.cu)
+        cudaError_t e = launch_pilot(db, q, nq, wt ? wt->w : nullptr, scratch, &bmin, stream);
+        if (e != cudaSuccess) return e;
+        void* ms = reinterpret_cast<unsigned char*>(scratch) + pilot_bytes(db, nq);
+        return launch_many(db, q, nq, k, wt ? wt->w : nullptr, wt ? wt->xnw : db->xnorm, wt ? wt->xmax_w : nullptr,
+                           bmin, scan_margin_scale(db->dim), idx, dist, ms, stream);
+    }
     if (pilot && use_pilot(db, nq)) {
         const ScanConfig c = choose_config(db, nq);
         unsigned char* ps = reinterpret_cast<unsigned char*>(scratch) + pass_bytes(c, db->nchunks, db->n_sub, nq, k);

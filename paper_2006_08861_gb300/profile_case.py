@@ -61,7 +61,8 @@ def main(argv=None):
             call()
         torch.cuda.synchronize()
         lhr.lhr_profile_enable(False)
-        for name in ("hier_fused", "scan_pilot", "wnorm", "scan_topk", "small_topk", "coarse_kernel", "collect", "shortlist",
+        for name in ("hier_fused", "scan_pilot", "wnorm", "scan_topk", "many_bound", "many_kernel", "many_select",
+                     "small_topk", "coarse_kernel", "collect", "shortlist",
                      "aggregate", "quantize", "tc_pilot", "tau_kernel", "tc_main", "tc_full", "merge_rerank"):
             n, ms = lhr.lhr_profile_read(name)
             if n:

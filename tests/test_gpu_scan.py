@@ -215,6 +215,30 @@ def test_pilot_exact_ties(lhr):
     assert np.array_equal(gd.astype(np.float64), o_dist)
 
 
+def test_many_frames_match_oracle(lhr):
+    # >= 64 frames over a sampled database take the register-tiled many-frame
+    # pass: three frame blocks (the last ragged), k = 20
+    rng = np.random.default_rng(45)
+    n, dim, nq, k = 70_003, 128, 150, 20
+    X = rng.standard_normal((n, dim)).astype(np.float32)
+    Q = (X[rng.integers(0, n, nq)] + 0.3 * rng.standard_normal((nq, dim))).astype(np.float32)
+    _, gi, gd = _run(lhr, X, Q, k)
+    _compare(X, Q, k, gi, gd)
+
+
+def test_many_frames_exact_ties(lhr):
+    # integer rows with many exact duplicates through the many-frame pass:
+    # equal to the oracle bit for bit (ties by lower row)
+    rng = np.random.default_rng(46)
+    base = rng.integers(-2, 3, size=(60, 64)).astype(np.float32)
+    X = base[rng.integers(0, 60, size=80_000)]
+    Q = rng.integers(-2, 3, size=(70, 64)).astype(np.float32)
+    _, gi, gd = _run(lhr, X, Q, 30)
+    o_idx, o_dist = oret.exhaustive_topk(Q, X, 30)
+    assert np.array_equal(gi, o_idx)
+    assert np.array_equal(gd.astype(np.float64), o_dist)
+
+
 def test_pilot_and_plain_scan_agree(lhr):
     # lhr_query seeds from the pilot; lhr_query_static never does
     rng = np.random.default_rng(44)

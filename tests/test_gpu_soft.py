@@ -31,6 +31,7 @@ def _weights(rng, dim):
     (3001, 64, 7, 16, None),      # ragged, no pilot
     (70_003, 32, 9, 32, None),    # pilot sample, two query blocks
     (80_000, 128, 5, 20, 3),      # pilot with subspaces
+    (70_003, 128, 130, 32, None), # many frames: the register-tiled pass
 ])
 def test_weighted_selection_matches_oracle(lhr, n, dim, nq, k, subs):
     rng = np.random.default_rng(n + dim)
