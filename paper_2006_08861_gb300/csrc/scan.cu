@@ -510,6 +510,9 @@ ScanConfig choose_config(const lhr_db* db, int nq) {
 // bmin[(f * n_sub + sub_p[j]) * 128 + j % 128] (float bits, preset to ~0u).
 // A warp takes 4 rows and 8 frames per round: 32 partial sums per lane, one
 // butterfly transpose-reduce, and lane l then holds (row l / 8, frame l % 8).
+// With many frames the grid's y splits them into slices of kPilotFrameSlice.
+constexpr int kPilotFrameSlice = 64;
+
 template <int CPL>
 __global__ void __launch_bounds__(256) pilot_kernel(const float* Xp, const int32_t* sub_p, int64_t np, int D,
                                                     const float* Q, int nq, int n_sub, const float* w,
@@ -538,7 +541,10 @@ __global__ void __launch_bounds__(256) pilot_kernel(const float* Xp, const int32
             wv[j] = (w != nullptr && c < D4) ? __ldg(reinterpret_cast<const float4*>(w) + c)
                                              : make_float4(1.f, 1.f, 1.f, 1.f);
         }
-        for (int f0 = 0; f0 < nq; f0 += 8) {
+        // this CTA's frames: a slice of kPilotFrameSlice (grid y), all of them
+        // when the grid has one slice
+        const int fb0 = blockIdx.y * kPilotFrameSlice, fb1 = gridDim.y == 1 ? nq : min(nq, fb0 + kPilotFrameSlice);
+        for (int f0 = fb0; f0 < fb1; f0 += 8) {
             float part[32];
 #pragma unroll
             for (int f = 0; f < 8; ++f) {
@@ -573,7 +579,7 @@ __global__ void __launch_bounds__(256) pilot_kernel(const float* Xp, const int32
                 }
             }
             const int f = f0 + lane % 8;
-            if (r < np && f < nq)
+            if (r < np && f < fb1)
                 atomicMin(bmin + ((size_t)f * n_sub + sub) * kPilotBuckets + (r % kPilotBuckets),
                           __float_as_uint(part[0]));
         }
@@ -820,7 +826,8 @@ cudaError_t launch_pilot(const lhr_db* db, const float* q, int nq, const float* 
     if (e != cudaSuccess) return e;
     const int d4 = db->dim / 4;
     const int cpl = d4 <= 32 ? 1 : (d4 <= 64 ? 2 : 4);
-    const int grid = (int)std::min<int64_t>((db->n_pilot + 31) / 32, (int64_t)db->sms * 8);
+    const int slices = nq > 2 * kPilotFrameSlice ? (nq + kPilotFrameSlice - 1) / kPilotFrameSlice : 1;
+    const dim3 grid((unsigned)std::min<int64_t>((db->n_pilot + 31) / 32, (int64_t)db->sms * 8), (unsigned)slices);
     {
         ProfScope ps("scan_pilot", stream);
         if (cpl == 1)
