@@ -5,8 +5,9 @@
 // With F frames the streaming scan reduces every (row, frame) distance across
 // the 32 lanes of a warp; with hundreds of frames that reduction costs as much
 // as the multiply-adds. Here a CTA holds 64 frames (w * q, in shared memory)
-// and streams its row chunk in 128-row tiles, K-chunked by 64 dimensions
-// (double-buffered cp.async); each thread owns an 8-frame x 4-row register
+// and streams its row chunk in 128-row tiles, K-chunked by 128 dimensions (64
+// when D is not a multiple of 128; double-buffered cp.async); each thread
+// owns an 8-frame x 4-row register
 // tile of the expanded form
 //     e(f, r) = ||x_r||_w^2 + ||q_f||_w^2 - 2 (w q_f) . x_r,
 // so no cross-lane reduction is needed. A pair is a candidate when
@@ -33,12 +34,10 @@ namespace {
 
 constexpr int kMF = 64;        // frames per CTA
 constexpr int kMRows = 128;    // rows per tile
-constexpr int kMK = 64;        // dimensions per K-chunk
 constexpr int kMThreads = 256; // 8 frame groups x 32 row groups
 constexpr int kMStage = 32;    // staged candidates per frame in shared memory
 constexpr int kMCap = 8192;    // candidates per frame in global memory (about 64 k expected)
 constexpr int kMBuckets = 128; // pilot bucket minima per frame
-constexpr int kXPitch = kMK + 4;  // padded row pitch of a K-chunk of rows (floats)
 
 struct ManyParams {
     const float* X;       // n x D, internal row order
@@ -119,9 +118,12 @@ __global__ void many_bound_kernel(ManyParams p) {
     }
 }
 
-// Stage one K-chunk (kMRows rows x kMK dims) of rows [r0, r0 + kMRows) into xs
-// with 16-byte cp.async copies (rows past r1 are zero-filled).
+// Stage one K-chunk (kMRows rows x KC dims) of rows [r0, r0 + kMRows) into xs
+// (row pitch KC + 4 floats) with 16-byte cp.async copies (rows past r1 are
+// zero-filled).
+template <int KC>
 __device__ __forceinline__ void load_chunk(const ManyParams& p, float* xs, int64_t r0, int64_t r1, int d0) {
+    constexpr int kMK = KC, kXPitch = KC + 4;
     constexpr int kVec = kMRows * kMK / 4;  // float4 per chunk
     for (int i = threadIdx.x; i < kVec; i += kMThreads) {
         const int r = i / (kMK / 4), c = i % (kMK / 4);
@@ -152,8 +154,11 @@ __device__ __forceinline__ void flush_stage(const ManyParams& p, int f0, unsigne
     __syncthreads();
 }
 
-template <bool kWeighted>
+// KC: dimensions per K-chunk (128 when D allows: half the chunk steps and
+// their barriers of 64).
+template <bool kWeighted, int KC>
 __global__ void __launch_bounds__(kMThreads, 1) many_kernel(ManyParams p) {
+    constexpr int kMK = KC, kXPitch = KC + 4;
     extern __shared__ __align__(16) float msm[];
     const int D = p.D;
     const int wpitch = D + 4;
@@ -191,7 +196,7 @@ __global__ void __launch_bounds__(kMThreads, 1) many_kernel(ManyParams p) {
     const int nk = D / kMK;
     const int64_t ntiles = row1 > row0 ? (row1 - row0 + kMRows - 1) / kMRows : 0;
     const int64_t nsteps = ntiles * nk;
-    if (nsteps > 0) load_chunk(p, xs0, row0, row1, 0);
+    if (nsteps > 0) load_chunk<KC>(p, xs0, row0, row1, 0);
     float2 acc[8][4];
     for (int64_t s = 0; s < nsteps; ++s) {
         const int64_t tile = s / nk;
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(kMThreads, 1) many_kernel(ManyParams p) {
         float* xs = (s & 1) ? xs1 : xs0;
         if (s + 1 < nsteps) {
             const int64_t tn = (s + 1) / nk;
-            load_chunk(p, (s & 1) ? xs0 : xs1, row0 + tn * kMRows, row1, (int)((s + 1) % nk) * kMK);
+            load_chunk<KC>(p, (s & 1) ? xs0 : xs1, row0 + tn * kMRows, row1, (int)((s + 1) % nk) * kMK);
             __pipeline_wait_prior(1);
         } else {
             __pipeline_wait_prior(0);
@@ -367,8 +372,8 @@ __global__ void many_select_kernel(ManyParams p) {
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-size_t many_smem(int D) {
-    return (size_t)kMF * (D + 4) * sizeof(float) + 2 * (size_t)kMRows * kXPitch * sizeof(float) +
+size_t many_smem(int D, int kc) {
+    return (size_t)kMF * (D + 4) * sizeof(float) + 2 * (size_t)kMRows * (kc + 4) * sizeof(float) +
            (size_t)kMF * kMStage * sizeof(u64) + 3 * (size_t)kMF * sizeof(float);
 }
 
@@ -380,7 +385,7 @@ size_t many_smem(int D) {
 // here); over 2,000,000 rows x 1,024 frames the streaming scan is faster
 // (39 ms vs 52 ms).
 bool many_eligible(const lhr_db* db, int nq, int k) {
-    return db->n_sub == 1 && db->Xp != nullptr && nq >= kMF && k >= 1 && k <= 32 && db->dim % kMK == 0 &&
+    return db->n_sub == 1 && db->Xp != nullptr && nq >= kMF && k >= 1 && k <= 32 && db->dim % 64 == 0 &&
            db->dim <= 256 && db->n < 1000000;
 }
 
@@ -430,9 +435,11 @@ cudaError_t launch_many(const lhr_db* db, const float* q, int nq, int k, const f
         many_bound_kernel<<<(nq + 7) / 8, 256, 0, stream>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const size_t sm = many_smem(db->dim);
+    const int kc = db->dim % 128 == 0 ? 128 : 64;
+    const size_t sm = many_smem(db->dim, kc);
     {
-        auto kern = w ? many_kernel<true> : many_kernel<false>;
+        auto kern = kc == 128 ? (w ? many_kernel<true, 128> : many_kernel<false, 128>)
+                              : (w ? many_kernel<true, 64> : many_kernel<false, 64>);
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
             return e;
         ProfScope ps("many_kernel", stream);
