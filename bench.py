@@ -39,10 +39,10 @@ METRIC = "queries/s and % of HBM/TC roofline, low-precision vs FP32 at recall@kâ
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each workload's dominant
 # kernel, from one ncu capture of the current kernel: hier_fused_kernel on this very workload;
-# scan_topk_kernel on 500,000 x 256 rows (518.9 MB), scaled by rows to the 2,000,000-row launch;
+# scan_topk_kernel on 500,000 x 256 rows (517.4 MB), scaled by rows to the 2,000,000-row launch;
 # tc_main_kernel (FP8) at the full 2,000,000 rows (single metrics: one pass).
 # Re-measure (or set None) whenever the kernel changes.
-TRAFFIC = {"hierarchical": ("hier_fused_kernel", 14.02e6), "hbm_scan": ("scan_topk_kernel", 4 * 518.9e6),
+TRAFFIC = {"hierarchical": ("hier_fused_kernel", 14.02e6), "hbm_scan": ("scan_topk_kernel", 4 * 517.4e6),
            "precision": ("tc_main_kernel", 531.3e6 + 5.8e6)}
 
 
