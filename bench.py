@@ -536,6 +536,7 @@ def run_precision(args, rank, world, local):
                      "algorithmic_flops_per_launch": flops,
                      "kernel_share": {n: round(v[1] / tot_all, 4) for n, v in share.items()}},
         "cpu_baseline": cpu,
+        "clocks": forms[best].get("clocks"),  # sampled during the reported form's timed batches
         # per batch: query scale, query codes, pilot, tau, main, fallback (exits at once), merge + re-rank
         "gpu_launches": 7 * args.steps,
     }
