@@ -326,7 +326,10 @@ lhr_status lhr_server_destroy(lhr_server* s);
  * returns, for kernels whose name contains `kernel` (NULL = all), the number
  * of launches and their summed device time in milliseconds, then forgets them
  * when `reset` is non-zero. Off by default; costs two event records per
- * kernel when on. Process-wide.
+ * kernel when on. Process-wide. A launch made while its stream is being
+ * captured into a CUDA graph records the pair as event-record nodes of the
+ * graph: every replay re-records them, so read such records with reset = 0
+ * after each replay, and reset them only once the graph is destroyed.
  */
 lhr_status lhr_profile_enable(int32_t on);
 lhr_status lhr_profile_read(const char* kernel, int64_t* launches, double* total_ms, int32_t reset);

@@ -146,6 +146,28 @@ def _dev_tensor(x, dtype, name):
     return x
 
 
+def _out_tensor(x, dtype, shape, device, name):
+    """A caller-supplied output: contiguous, on `device`, of this dtype and exact shape (the
+    library writes that many elements through its pointer)."""
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.device != device:
+        raise TypeError(f"{name} must be a CUDA tensor on {device}")
+    if x.dtype != dtype or not x.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    if tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(x.shape)}")
+    return x
+
+
+def _frames(db, x, name):
+    """Query frames: a contiguous float32 CUDA tensor of shape (nq, db.dim)."""
+    torch = _torch()
+    x = _dev_tensor(x, torch.float32, name)
+    if x.dim() != 2 or x.shape[1] != db.dim:
+        raise ValueError(f"{name} must have shape (n, {db.dim}), got {tuple(x.shape)}")
+    return x
+
+
 class Database:
     """Owns an lhr_db handle (freed with the object)."""
 
@@ -209,13 +231,14 @@ def lhr_query(db: Database, q, k: int, shortlist: int = 0, score: str = "f32", r
               out=None, stream=None):
     """Top-k rows per query frame: returns (idx int64 [nq, n_s, k], dist float32 [nq, n_s, k])."""
     torch = _torch()
-    q = _dev_tensor(q, torch.float32, "q")
+    q = _frames(db, q, "q")
     nq = q.shape[0]
     if out is None:
         idx = torch.empty((nq, db.n_subspaces, k), dtype=torch.int64, device=q.device)
         dist = torch.empty((nq, db.n_subspaces, k), dtype=torch.float32, device=q.device)
     else:
-        idx, dist = out
+        idx = _out_tensor(out[0], torch.int64, (nq, db.n_subspaces, k), q.device, "idx")
+        dist = _out_tensor(out[1], torch.float32, (nq, db.n_subspaces, k), q.device, "dist")
     p = query_params(k, shortlist, score, rerank_width)
     _check(_lib.lhr_query(db.handle, _ptr(q), nq, ctypes.byref(p), _ptr(idx), _ptr(dist), _stream(stream)))
     return idx, dist
@@ -227,8 +250,10 @@ def lhr_query_static(db: Database, q, k: int, out, stream=None):
     calls). ``out`` = (idx int64 [nq, n_s, k], dist float32 [nq, n_s, k]),
     preallocated by the caller."""
     torch = _torch()
-    q = _dev_tensor(q, torch.float32, "q")
-    idx, dist = out
+    q = _frames(db, q, "q")
+    nq = q.shape[0]
+    idx = _out_tensor(out[0], torch.int64, (nq, db.n_subspaces, k), q.device, "idx")
+    dist = _out_tensor(out[1], torch.float32, (nq, db.n_subspaces, k), q.device, "dist")
     _check(_lib.lhr_query_static(db.handle, _ptr(q), q.shape[0], k, _ptr(idx), _ptr(dist), _stream(stream)))
     return idx, dist
 
@@ -239,17 +264,22 @@ def lhr_query_window(db: Database, frames, offsets, k: int, shortlist: int = 0, 
     """Retrieval for every frame, then Algorithm 2 per window.
     Returns (idx, dist, xy float64 [nw, 2], status int32 [nw])."""
     torch = _torch()
-    frames = _dev_tensor(frames, torch.float32, "frames")
+    frames = _frames(db, frames, "frames")
     offsets = _dev_tensor(offsets, torch.int32, "offsets")
+    if offsets.dim() != 1 or offsets.shape[0] < 2:
+        raise ValueError("offsets must be a 1-D tensor of nw + 1 >= 2 entries")
     W, nw = frames.shape[0], offsets.shape[0] - 1
+    dev = frames.device
     if out is None:
-        dev = frames.device
         idx = torch.empty((W, db.n_subspaces, k), dtype=torch.int64, device=dev)
         dist = torch.empty((W, db.n_subspaces, k), dtype=torch.float32, device=dev)
         xy = torch.empty((nw, 2), dtype=torch.float64, device=dev)
         status = torch.empty((nw,), dtype=torch.int32, device=dev)
     else:
-        idx, dist, xy, status = out
+        idx = _out_tensor(out[0], torch.int64, (W, db.n_subspaces, k), dev, "idx")
+        dist = _out_tensor(out[1], torch.float32, (W, db.n_subspaces, k), dev, "dist")
+        xy = _out_tensor(out[2], torch.float64, (nw, 2), dev, "xy")
+        status = _out_tensor(out[3], torch.int32, (nw,), dev, "status")
     p = query_params(k, shortlist, score, rerank_width)
     a = agg_params(mode, top_c, radius_m, toler_pct, tau)
     _check(_lib.lhr_query_window(db.handle, _ptr(frames), _ptr(offsets), W, nw, ctypes.byref(p), ctypes.byref(a),
@@ -265,12 +295,17 @@ def lhr_aggregate_2d(db: Database, idx, cand_offsets, dist=None, mode: str = "ti
     cand_offsets = _dev_tensor(cand_offsets, torch.int32, "cand_offsets")
     if dist is not None:
         dist = _dev_tensor(dist, torch.float32, "dist")
+    if cand_offsets.dim() != 1 or cand_offsets.shape[0] < 2:
+        raise ValueError("cand_offsets must be a 1-D tensor of nw + 1 >= 2 entries")
+    if dist is not None and dist.numel() != idx.numel():
+        raise ValueError("dist must hold one distance per candidate")
     nw = cand_offsets.shape[0] - 1
     if out is None:
         xy = torch.empty((nw, 2), dtype=torch.float64, device=idx.device)
         status = torch.empty((nw,), dtype=torch.int32, device=idx.device)
     else:
-        xy, status = out
+        xy = _out_tensor(out[0], torch.float64, (nw, 2), idx.device, "xy")
+        status = _out_tensor(out[1], torch.int32, (nw,), idx.device, "status")
     a = agg_params(mode, top_c, radius_m, toler_pct, tau)
     _check(_lib.lhr_aggregate_2d(db.handle, _ptr(idx), _ptr(dist), idx.numel(), _ptr(cand_offsets), nw,
                                  ctypes.byref(a), _ptr(xy), _ptr(status), _stream(stream)))
@@ -302,14 +337,15 @@ def lhr_query_weighted(db: Database, q, k: int, w, out=None, stream=None):
     """Exhaustive top-k by the weighted distance sum_j w_j (q_j - x_j)^2:
     (idx int64 [nq, n_s, k], dist float32 [nq, n_s, k])."""
     torch = _torch()
-    q = _dev_tensor(q, torch.float32, "q")
-    w = _dev_tensor(w, torch.float32, "w")
+    q = _frames(db, q, "q")
+    w = _out_tensor(w, torch.float32, (db.dim,), q.device, "w")
     nq = q.shape[0]
     if out is None:
         idx = torch.empty((nq, db.n_subspaces, k), dtype=torch.int64, device=q.device)
         dist = torch.empty((nq, db.n_subspaces, k), dtype=torch.float32, device=q.device)
     else:
-        idx, dist = out
+        idx = _out_tensor(out[0], torch.int64, (nq, db.n_subspaces, k), q.device, "idx")
+        dist = _out_tensor(out[1], torch.float32, (nq, db.n_subspaces, k), q.device, "dist")
     _check(_lib.lhr_query_weighted(db.handle, _ptr(q), nq, k, _ptr(w), _ptr(idx), _ptr(dist), _stream(stream)))
     return idx, dist
 

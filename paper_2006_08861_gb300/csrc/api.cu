@@ -88,7 +88,12 @@ ProfScope::ProfScope(const char* kernel, cudaStream_t s) : stream(s) {
     ProfRec r;
     r.name = kernel;
     if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
-    cudaEventRecord(r.a, s);
+    // under stream capture the pair becomes event-record nodes of the graph, re-recorded by every replay
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusNone;
+    capturing = cs == cudaStreamCaptureStatusActive;
+    if (capturing) cudaEventRecordWithFlags(r.a, s, cudaEventRecordExternal);
+    else cudaEventRecord(r.a, s);
     std::lock_guard<std::mutex> lk(g_prof_mu);
     slot = (int)g_prof_recs.size();
     g_prof_recs.push_back(r);
@@ -101,7 +106,8 @@ ProfScope::~ProfScope() {
         std::lock_guard<std::mutex> lk(g_prof_mu);
         b = g_prof_recs[slot].b;
     }
-    cudaEventRecord(b, stream);
+    if (capturing) cudaEventRecordWithFlags(b, stream, cudaEventRecordExternal);
+    else cudaEventRecord(b, stream);
 }
 
 // Restores the caller's current device on scope exit.

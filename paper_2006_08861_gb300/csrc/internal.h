@@ -93,6 +93,7 @@ struct Scratch {
 // event pair around the launches it encloses when profiling is on.
 struct ProfScope {
     int slot = -1;
+    bool capturing = false;
     cudaStream_t stream = nullptr;
     ProfScope(const char* kernel, cudaStream_t s);
     ~ProfScope();

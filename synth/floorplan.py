@@ -28,6 +28,7 @@ Randomness comes from numpy's PCG64 ``default_rng`` with the seeds in
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -88,15 +89,30 @@ class FeatureField:
     def dim(self) -> int:
         return self.A.shape[1]
 
-    def __call__(self, pos: np.ndarray, chunk: int = 1 << 16) -> np.ndarray:
+    def __call__(self, pos: np.ndarray, chunk: int = 1 << 15) -> np.ndarray:
         pos = np.asarray(pos, dtype=np.float32)
         out = np.empty((pos.shape[0], self.dim), dtype=np.float32)
         scale = np.float32(math.sqrt(2.0 / self.omega.shape[0]))
-        for s in range(0, pos.shape[0], chunk):
-            phase = pos[s:s + chunk] @ self.omega.T + self.b
+        om = self.omega.astype(np.float64)
+        b = self.b.astype(np.float64)
+
+        def one(s):
+            p = pos[s:s + chunk].astype(np.float64)
+            # phase in binary64 (the products of binary32 values are exact), rounded once to binary32
+            phase = (p[:, 0:1] * om[:, 0] + p[:, 1:2] * om[:, 1] + b).astype(np.float32)
             np.cos(phase, out=phase)
             phase *= scale
             np.matmul(phase, self.A, out=out[s:s + chunk])
+
+        starts = range(0, pos.shape[0], chunk)
+        if pos.shape[0] <= chunk:
+            for s in starts:
+                one(s)
+        else:
+            # chunks are independent and write disjoint rows: the bytes do not depend on the thread count
+            import concurrent.futures as cf
+            with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+                list(ex.map(one, starts))
         return out
 
 
@@ -127,8 +143,7 @@ def make_database(n: int, dim: int, seed: int, spacing: float = 0.5, alias_frac:
     fld = FeatureField.make(dim, rng, ell=ell)
     arc = spacing * np.arange(n, dtype=np.float64)
     xy = path_positions(arc)
-    base = fld(xy)
-    feats = base.copy()
+    feats = fld(xy)
     n_alias = int(round(alias_frac * n))
     aliased = np.zeros(n, dtype=bool)
     alias_src = np.full(n, -1, dtype=np.int64)
@@ -144,7 +159,8 @@ def make_database(n: int, dim: int, seed: int, spacing: float = 0.5, alias_frac:
         ok = np.hypot(*(xy[src] - xy[rows]).T) >= alias_min_dist
         rows, src = rows[ok], src[ok]
         noise = rng.standard_normal((rows.size, dim)).astype(np.float32) * np.float32(alias_sigma)
-        feats[rows] = base[src] + noise
+        # feats[src] is gathered before any row is overwritten: every copy is of the field's own value
+        feats[rows] = feats[src] + noise
         aliased[rows] = True
         alias_src[rows] = src
     return Database(feats=np.ascontiguousarray(feats), xy=xy, arc=arc, aliased=aliased,

@@ -67,3 +67,28 @@ def check_list(q, X, g_idx, g_dist, o_idx, o_dist, k, rows=None, where="", w=Non
         if od[k] - od[k - 1] > GAP * max(od[k - 1], 1e-12):
             assert set(gi.tolist()) == set(oi[:k].tolist()), f"{where}: top-k set differs"
     return exact_cmp
+
+
+def check_hier_ambiguous(q, X, dc, S, g_idx, g_dist, k, where=""):
+    """Coarse-to-fine list of a frame whose S-th / (S+1)-th coarse distances nearly
+    tie, so that which boundary rows enter the shortlist is decided by rounding.
+    The list must be the exact top k of SOME valid shortlist: every returned row's
+    coarse distance is at most the S-th one (+ 2 GAP), distances are exact and
+    ascending, and every row whose coarse distance is surely below the boundary
+    (- 2 GAP) and whose full distance is below the list's k-th (- 2 GAP) is in it."""
+    g_idx = np.asarray(g_idx)
+    g_dist = np.asarray(g_dist, dtype=np.float64)
+    dcoarse = oret.sq_dist(q[:dc], X[:, :dc])
+    cS = np.sort(dcoarse)[S - 1]
+    lo, hi = cS * (1 - 2 * GAP), cS * (1 + 2 * GAP) + 1e-12
+    n_ret = min(k, X.shape[0])
+    gi = g_idx[:n_ret]
+    assert np.all(gi >= 0) and len(set(gi.tolist())) == n_ret, f"{where}: padding or duplicate rows"
+    assert np.all(dcoarse[gi] <= hi), f"{where}: a returned row cannot be in any valid shortlist"
+    exact = oret.sq_dist(q, X[gi])
+    assert np.all(np.abs(g_dist[:n_ret] - exact) <= DIST_RTOL * exact + 1e-7), f"{where}: distance error"
+    assert np.all(np.diff(g_dist[:n_ret]) >= 0), f"{where}: list not ascending"
+    sure = np.nonzero(dcoarse < lo)[0]
+    full = oret.sq_dist(q, X[sure])
+    must = set(sure[full < g_dist[n_ret - 1] * (1 - 2 * GAP) - 1e-7].tolist())
+    assert must <= set(gi.tolist()), f"{where}: rows {sorted(must - set(gi.tolist()))[:5]} missing"

@@ -6,7 +6,7 @@ import pytest
 import synth
 from oracle import aggregate as oagg
 from oracle import retrieval as oret
-from tests.parity import GAP, XY_ATOL, check_list
+from tests.parity import GAP, XY_ATOL, check_hier_ambiguous, check_list
 
 pytestmark = pytest.mark.gpu
 
@@ -126,9 +126,17 @@ def test_hierarchical_configuration_windows(lhr):
     gi, gd = idx.cpu().numpy()[:, 0], dist.cpu().numpy()[:, 0]
     o_idx, o_dist, _ = oret.hierarchical_topk(win.frames, db.feats, cfg["coarse_dim"], cfg["shortlist"],
                                               cfg["k"] + 1)
+    strict = 0
     for f in range(win.frames.shape[0]):
         if _shortlist_separated(win.frames[f], db.feats, cfg["coarse_dim"], cfg["shortlist"]):
             check_list(win.frames[f], db.feats, gi[f], gd[f], o_idx[f], o_dist[f], cfg["k"], where=f"f{f}")
+            strict += 1
+        else:
+            # the shortlist boundary nearly ties (about a third of the frames at S = 512 of 100,000):
+            # the list must still be the exact top k of a valid shortlist
+            check_hier_ambiguous(win.frames[f], db.feats, cfg["coarse_dim"], cfg["shortlist"], gi[f], gd[f],
+                                 cfg["k"], where=f"f{f}")
+    assert strict >= win.frames.shape[0] // 2, strict
     # Algorithm 2 on the GPU's candidates equals the oracle's on the same candidates
     cands = oret.window_candidates(gi, win.offsets)
     o_xy, o_st = oagg.aggregate_windows(cands, db.xy, mode="tile")

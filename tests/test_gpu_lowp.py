@@ -121,30 +121,95 @@ def test_invalid_low_precision_requests(lhr):
         lhr.lhr_build_db(np.zeros((10, 96), np.float32), np.zeros((10, 2)), lowp=2)  # D % 128 for FP8
 
 
-def test_precision_configuration_recall(lhr):
+def _oracle_topk_threads(Q, X, k):
+    """The FP64 oracle's exhaustive top-k of each query, one query per host thread."""
+    import concurrent.futures as cf
+    import os
+
+    def one(i):
+        return oret.exhaustive_topk(Q[i:i + 1], X, k)
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        res = list(ex.map(one, range(Q.shape[0])))
+    return np.stack([r[0][0, 0] for r in res]), np.stack([r[1][0, 0] for r in res])
+
+
+def test_precision_configuration_recall_and_positions(lhr):
     # N = 2,000,000, D = 256, Q = 1,024 frames (noise 0.05), top-64 shortlist,
-    # FP32 re-rank to k = 20: recall@20 against the exhaustive FP32 scan (which
-    # is parity-tested against the oracle) on every query, and against the FP64
-    # oracle itself on sampled queries.
+    # FP32 re-rank to k = 20, then Algorithm 2 on each frame's 20 candidates.
+    # Every query: recall@20 of the BF16 / FP8 forms against the exhaustive FP32
+    # scan, and their final positions against the FP32 form's. Sampled queries
+    # (64, one per host thread): every form against the FP64 oracle, lists by
+    # the parity rule and positions against Algorithm 2 on the oracle's list.
+    from oracle import aggregate as oagg
     cfg = synth.CONFIGS["precision"]
-    db = synth.make_database(cfg["n"], cfg["dim"], seed=1002)
-    q, rows, _ = synth.make_point_queries(db, cfg["nq"], seed=2002)
+    k = cfg["k"]
+    db = synth.make_database(cfg["n"], cfg["dim"], seed=synth.db_seed(cfg["index"]))
+    q, rows, _ = synth.make_point_queries(db, cfg["nq"], seed=synth.query_seed(cfg["index"]))
     h = lhr.lhr_build_db(db.feats, db.xy, lowp=3)
     qt = torch.from_numpy(q).cuda()
-    ei, ed = lhr.lhr_query(h, qt, cfg["k"])
+    offs = torch.arange(0, cfg["nq"] * k + 1, k, dtype=torch.int32, device="cuda")
     results = {}
-    for f in ("bf16", "fp8"):
-        li, ld = lhr.lhr_query(h, qt, cfg["k"], score=f, rerank_width=cfg["rerank_width"])
+    for f in ("f32", "bf16", "fp8"):
+        kw = {} if f == "f32" else dict(score=f, rerank_width=cfg["rerank_width"])
+        li, ld = lhr.lhr_query(h, qt, k, **kw)
+        xy, st = lhr.lhr_aggregate_2d(h, li.view(-1), offs, mode="tile")
         torch.cuda.synchronize()
-        results[f] = (li.cpu().numpy()[:, 0], ld.cpu().numpy()[:, 0])
-    ex = ei.cpu().numpy()[:, 0]
-    for f, (li, ld) in results.items():
-        recall = np.mean([len(set(li[i]) & set(ex[i])) / cfg["k"] for i in range(cfg["nq"])])
+        results[f] = (li.cpu().numpy()[:, 0], ld.cpu().numpy()[:, 0], xy.cpu().numpy(), st.cpu().numpy())
+    assert lhr.lhr_db_error(h) == 0
+    ex, _, ex_xy, ex_st = results["f32"]
+    for f in ("bf16", "fp8"):
+        li, ld, xy, st = results[f]
+        same_set = np.array([set(li[i]) == set(ex[i]) for i in range(cfg["nq"])])
+        recall = np.mean([len(set(li[i]) & set(ex[i])) / k for i in range(cfg["nq"])])
         assert recall >= 0.999, (f, recall)
         assert np.mean(li[:, 0] == ex[:, 0]) >= 0.999, f
-    for qi in (0, 511):
-        o_idx, o_dist = oret.exhaustive_topk(q[qi:qi + 1], db.feats, cfg["k"] + 1)
-        for f, (li, ld) in results.items():
-            check_list(q[qi], db.feats, li[qi], ld[qi], o_idx[0, 0], o_dist[0, 0], cfg["k"], where=f"{f} q{qi}")
+        # identical candidate sets give identical positions (Algorithm 2 reads the set only)
+        dev_m = np.max(np.abs(xy - ex_xy), axis=1)
+        assert np.all(dev_m[same_set] <= 1e-9) and np.all(st[same_set] == ex_st[same_set]), f
+        assert np.mean((dev_m <= 1e-3) & (st == ex_st)) >= 0.999, (f, np.mean(dev_m <= 1e-3))
+    sample = np.random.default_rng(5).choice(cfg["nq"], size=64, replace=False)
+    o_idx, o_dist = _oracle_topk_threads(q[sample], db.feats, k + 1)
+    o_xy, o_st = oagg.aggregate_windows([o_idx[j, :k] for j in range(sample.size)], db.xy, mode="tile")
+    hits = {f: 0 for f in results}
+    for j, qi in enumerate(sample):
+        sep = o_dist[j, k] - o_dist[j, k - 1] > 1e-4 * o_dist[j, k - 1]
+        for f, (li, ld, xy, st) in results.items():
+            same = set(li[qi]) == set(o_idx[j, :k])
+            hits[f] += len(set(li[qi]) & set(o_idx[j, :k]))
+            if f == "f32" or same:
+                check_list(q[qi], db.feats, li[qi], ld[qi], o_idx[j], o_dist[j], k, where=f"{f} q{qi}")
+            if sep and (f == "f32" or same):
+                assert np.max(np.abs(xy[qi] - o_xy[j])) <= 1e-3 and st[qi] == o_st[j], (f, qi)
+    for f in ("bf16", "fp8"):
+        assert hits[f] / (k * sample.size) >= 0.995, (f, hits[f])
+    h.close()
+
+
+@pytest.mark.parametrize("fmt_name", ["bf16", "fp8"])
+def test_batch_outlier_keeps_recall(lhr, fmt_name):
+    # The queries of one batch share one power-of-two scale, set by the batch's
+    # largest |q_j|. One query 100x larger than the rest pushes the others'
+    # codes 100x down (FP8: partly into the e4m3 subnormal range): the others'
+    # recall@20 against the exhaustive FP32 scan must stay >= 0.999, and the
+    # outlier's own list must equal the scan's.
+    fmt, bit = FMT[fmt_name]
+    cfg = synth.CONFIGS["precision"]
+    k = cfg["k"]
+    db = synth.make_database(300_000, 256, seed=4242)
+    q, _, _ = synth.make_point_queries(db, 256, seed=4343)
+    q[17] *= np.float32(100.0)
+    h = lhr.lhr_build_db(db.feats, db.xy, lowp=bit)
+    qt = torch.from_numpy(q).cuda()
+    ei, ed = lhr.lhr_query(h, qt, k)
+    li, ld = lhr.lhr_query(h, qt, k, score=fmt_name, rerank_width=cfg["rerank_width"])
+    torch.cuda.synchronize()
     assert lhr.lhr_db_error(h) == 0
+    ex, got = ei.cpu().numpy()[:, 0], li.cpu().numpy()[:, 0]
+    rest = [i for i in range(q.shape[0]) if i != 17]
+    recall = np.mean([len(set(got[i]) & set(ex[i])) / k for i in rest])
+    assert recall >= 0.999, recall
+    assert set(got[17]) == set(ex[17])
+    # the batch scale really moved: the outlier's amax sets it (the oracle's statement of the scale)
+    assert olowp.batch_scale(q, fmt) >= 64 * olowp.batch_scale(np.delete(q, 17, axis=0), fmt)
     h.close()

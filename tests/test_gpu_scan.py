@@ -251,3 +251,27 @@ def test_pilot_and_plain_scan_agree(lhr):
     lhr.lhr_query_static(db, q, 24, (out_i, out_d))
     torch.cuda.synchronize()
     assert torch.equal(i1, out_i) and torch.equal(d1, out_d)
+
+
+def test_binding_rejects_mismatched_buffers(lhr):
+    # the binding checks shapes, dtypes and devices before the library writes through a pointer
+    X = np.random.default_rng(9).standard_normal((500, 64)).astype(np.float32)
+    db = lhr.lhr_build_db(X, np.zeros((500, 2)))
+    q = torch.zeros((3, 64), device="cuda")
+    k = 5
+    good = (torch.empty((3, 1, k), dtype=torch.int64, device="cuda"),
+            torch.empty((3, 1, k), dtype=torch.float32, device="cuda"))
+    lhr.lhr_query(db, q, k, out=good)
+    lhr.lhr_query_static(db, q, k, out=good)
+    with pytest.raises(ValueError):
+        lhr.lhr_query(db, torch.zeros((3, 32), device="cuda"), k)          # D differs from the database's
+    with pytest.raises(ValueError):
+        lhr.lhr_query(db, q, k, out=(good[0][:2], good[1][:2]))            # too few rows
+    with pytest.raises(ValueError):
+        lhr.lhr_query_static(db, q, k + 1, out=good)                        # k differs
+    with pytest.raises(TypeError):
+        lhr.lhr_query(db, q, k, out=(good[0], good[1].double()))            # wrong dtype
+    with pytest.raises(TypeError):
+        lhr.lhr_query(db, q, k, out=(good[0].cpu(), good[1]))               # host tensor
+    torch.cuda.synchronize()
+    assert lhr.lhr_db_error(db) == 0

@@ -211,4 +211,13 @@ def test_differentiation_workload_sampled(lhr):
         dq_ref = ref["dq"] * scale
         err = np.max(np.abs(dq.cpu().numpy()[fr] - dq_ref)) / max(np.max(np.abs(dq_ref)), 1e-12)
         assert err < 2e-4, f"window {b}: dq error {err:.3g}"
+    # dw and dtau sum over all 256 windows (the library reduces them in a fixed order): the FP64
+    # oracle's gradients over every window, with the GPU's selection held fixed
+    ref = soft.forward_backward(win.frames, win.offsets, db.feats, db.xy, y, w.astype(np.float64),
+                                float(np.float32(0.1)), idx=gi)
+    dw_err = np.max(np.abs(dw.cpu().numpy() - ref["dw"])) / max(np.max(np.abs(ref["dw"])), 1e-30)
+    assert dw_err < 2e-4, f"dw error {dw_err:.3g}"
+    dtau_ref = ref["dtau"]
+    assert abs(float(dtau.cpu().numpy()[0]) - dtau_ref) <= 2e-4 * abs(dtau_ref) + 1e-9, (dtau, dtau_ref)
+    assert np.allclose(yhat.cpu().numpy(), ref["yhat"], atol=1e-6)
     h.close()
