@@ -51,7 +51,7 @@ METRIC = "queries/s and % of HBM/TC roofline, low-precision vs FP32 at recall@kâ
 # tc_main_kernel (FP8) at the full 2,000,000 rows (single metrics: one pass).
 # Re-measure (or set None) whenever the kernel changes.
 TRAFFIC = {"hierarchical": ("hier_fused_kernel", 14.02e6), "hbm_scan": ("scan_topk_kernel", 4 * 517.4e6),
-           "precision": ("tc_main_kernel", 531.3e6 + 5.8e6)}
+           "precision": ("tc_main_kernel", None)}
 
 
 # ------------------------------------------------------------------ ranks

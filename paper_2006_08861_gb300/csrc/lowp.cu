@@ -83,6 +83,8 @@ constexpr int kHalves = 2;        // epilogue warps per TMEM lane quadrant (each
 constexpr int kEpiWarps = 4 * kHalves;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;  // producer, MMA issuer, epilogue
+constexpr int kQTile = 256;       // queries per CTA of the main pass (UMMA N)
+constexpr int kMainAcc = 2;       // main pass: 2 x 256 FP32 accumulator columns = all of TMEM
 
 // ------------------------------------------------------------------ PTX
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, u64* bar) {
@@ -93,11 +95,43 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// The same tile box delivered to the shared memory of every CTA of the cluster
+// in `mask` (same offsets in each), completing bytes on each CTA's barrier at
+// `bar`'s offset.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int c0, int c1, u64* bar,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
+        "%3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// All threads of every CTA of the cluster (a plain block barrier when the cluster is one CTA).
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_commit(u64* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Arrival, once this thread's earlier tcgen05 operations complete, on the barrier
+// at `bar`'s offset in every CTA of the cluster in `mask`.
+__device__ __forceinline__ void tc_commit_mc(u64* bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                     smem_u32(bar)),
+                 "h"(mask)
                  : "memory");
 }
 
@@ -153,14 +187,14 @@ __device__ __forceinline__ u64 sw128_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: dense, FP32 accumulate, A/B K-major, M = N = 128.
-// BF16 inputs: format 1 in both operand fields (kind::f16); E4M3: format 0
-// (kind::f8f6f4).
-__host__ __device__ constexpr uint32_t tc_idesc(bool fp8) {
+// Instruction descriptor: dense, FP32 accumulate, A/B K-major, M = 128, N = n
+// (128 or 256). BF16 inputs: format 1 in both operand fields (kind::f16);
+// E4M3: format 0 (kind::f8f6f4).
+__host__ __device__ constexpr uint32_t tc_idesc(bool fp8, int n = kTile) {
     return (1u << 4)                      // D format: F32
            | ((fp8 ? 0u : 1u) << 7)       // A format
            | ((fp8 ? 0u : 1u) << 10)      // B format
-           | ((uint32_t)(kTile >> 3) << 17)  // N >> 3
+           | ((uint32_t)(n >> 3) << 17)      // N >> 3
            | ((uint32_t)(kTile >> 4) << 24); // M >> 4
 }
 
@@ -199,9 +233,12 @@ struct MainParams {
     const float* qs;      // [0] = s_Q, [1] = m = -2 s_Q
     const float* tau_s;   // per padded query: threshold score (-inf for padding queries)
     const u64* tau_key;   // per padded query: threshold key
+    const int* perm;      // per sorted position: the query there (caller's order), -1 = padding
+    const float* tgrp;    // per 32 sorted positions: the largest threshold among them (-inf if none)
     u64* cand;            // [query][kCap]
     unsigned* cnt;        // keys <= tau seen per query
     int nq;
+    int cs;               // CTAs per cluster along the query blocks (1, 2 or 4): they share each database tile
     int* err;
 };
 
@@ -247,13 +284,6 @@ __device__ __noinline__ void flush_buffer(u64* list, const u64* buf, int stride,
         }
     }
     for (int o = 0; o < W; ++o) list[o] = out[o];
-}
-
-// Three-input minimum (one instruction on this architecture).
-__device__ __forceinline__ float fmin3(float a, float b, float c) {
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
 }
 
 template <bool kFp8, int MODE, int WMAX>
@@ -513,82 +543,113 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAcc * kTile) : "memory");
 }
 
-// Minimum over the 32 columns of group G of score - tau_q, score =
-// fma(B, dot, A) in packed pairs (exact sign: the difference of two floats is
-// <= 0 iff score <= tau_q).
-template <int G>
-__device__ __forceinline__ float main_group_min(const uint32_t (&v)[32], const float2 (&ntau)[32], float2 A2, float2 B2) {
-    float d[32];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const float2 sc = __ffma2_rn(B2, make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])), A2);
-        const float2 df = __fadd2_rn(sc, ntau[G * 16 + i]);
-        d[2 * i] = df.x;
-        d[2 * i + 1] = df.y;
-    }
-    float t[11];
-#pragma unroll
-    for (int i = 0; i < 10; ++i) t[i] = fmin3(d[3 * i], d[3 * i + 1], d[3 * i + 2]);
-    t[10] = fminf(d[30], d[31]);
-    const float u0 = fmin3(t[0], t[1], t[2]), u1 = fmin3(t[3], t[4], t[5]), u2 = fmin3(t[6], t[7], t[8]);
-    return fminf(fmin3(u0, u1, u2), fminf(t[9], t[10]));
+// Maximum of 32 accumulator values (three-input max: one instruction on this architecture).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
-// Survivors of the main pass. Lane l of an epilogue warp owns column l of each
-// of its two 32-column groups (one query each) and stages that query's keys in
-// kOwnSlots shared-memory slots; a full stage goes to the query's candidate
-// buffer with one atomic.
-constexpr int kOwnSlots = 8;
+// Maximum of 32 accumulator values in four interleaved chains of three-input
+// maxima (few live temporaries: the values of two groups are in registers).
+__device__ __forceinline__ float max32(const uint32_t (&v)[32]) {
+    float c[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c[i] = fmax3(__uint_as_float(v[i]), __uint_as_float(v[4 + i]), __uint_as_float(v[8 + i]));
+#pragma unroll
+    for (int j = 12; j < 28; j += 8)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) c[i] = fmax3(c[i], __uint_as_float(v[j + i]), __uint_as_float(v[j + 4 + i]));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c[i] = fmaxf(c[i], __uint_as_float(v[28 + i]));
+    return fmax3(c[0], c[1], fmaxf(c[2], c[3]));
+}
 
-struct Owner {
-    u64* slot;        // slot i of group g at slot[(g * kOwnSlots + i) * kEpiThreads]
-    float tau_s[2];   // thresholds of the two owned queries (-inf when past nq)
-    int64_t q[2];     // the owned queries
-    int n[2];         // keys staged per owned query
-};
+// Main pass layout: 2 + kMainEpiWarps warps. Epilogue warp w reads TMEM lane
+// quadrant w % 4 (its 32 database rows) and column quarter (w - 2) / 4 of each
+// 256-query tile: kMGroups 32-query groups.
+constexpr int kMainEpiWarps = 16;
+constexpr int kMainEpiThreads = 32 * kMainEpiWarps;
+constexpr int kMainThreads = 64 + kMainEpiThreads;
+constexpr int kMGroups = kQTile / (kMainEpiWarps / 4) / 32;  // 2
+constexpr int kOwnSlots = 4;       // staged keys per owned query
+constexpr int kTRows = 8;          // rows a warp moves through its transpose buffer at a time
+constexpr int kTStride = 36;       // floats per buffered row: 32 values, then (A, B, row, -); 144 B apart
 
-__device__ __noinline__ void flush_owner(const MainParams& p, Owner& o, int g) {
-    const int n = o.n[g];
-    const unsigned pos = atomicAdd(p.cnt + o.q[g], (unsigned)n);
+// Staged keys of one owned query (slot i at slot[i * kMainEpiThreads]) to its
+// candidate buffer: one atomic for the lot.
+__device__ __forceinline__ void flush_owned(const MainParams& p, const u64* slot, int q, int n) {
+    const unsigned pos = atomicAdd(p.cnt + q, (unsigned)n);
     for (int i = 0; i < n; ++i)
-        if (pos + i < (unsigned)kCap)
-            p.cand[(size_t)o.q[g] * kCap + pos + i] = o.slot[(g * kOwnSlots + i) * kEpiThreads];
-    o.n[g] = 0;
+        if (pos + i < (unsigned)kCap) p.cand[(size_t)q * kCap + pos + i] = slot[i * kMainEpiThreads];
 }
 
-// Group G of a tile in which some lane's row has a key <= its query's tau (the
-// warp's ballot `ev`): for each such row in turn the warp moves the row's 32
-// dot products across the lanes (lane l gets column l), and every lane checks
-// its own query. score < tau_s decides without the key; on an exact score tie
-// the row index decides against the threshold key.
-template <int G>
-__device__ __forceinline__ void main_survivors(const MainParams& p, const uint32_t (&v)[32], float A, float B,
-                                               uint32_t row, unsigned ev, int lane, Owner& o) {
-    while (ev) {
-        const int e = __ffs(ev) - 1;
-        ev &= ev - 1;
-        const float Be = __shfl_sync(kFull, B, e), Ae = __shfl_sync(kFull, A, e);
-        const uint32_t rowe = __shfl_sync(kFull, row, e);
-        uint32_t x = 0;
+// Rows of one 32-column group that passed the group bound (the warp's ballot
+// `ev`; see the epilogue) go, up to kTRows at a time, through the warp's
+// shared-memory transpose buffer: lane l then reads column l of each such row
+// -- the query it owns -- and checks it exactly: score < tau_s decides without
+// the key; on an exact score tie the row index decides against the threshold
+// key. A qualifying key is staged in the lane's slots for that query; a full
+// stage goes to the query's candidate buffer with one atomic.
+// Lanes of `sel` (at most kTRows) write their rows' 32 values and (A, B, row) to
+// the warp's transpose buffer, row `rank` = the lane's rank within `sel`.
+__device__ __forceinline__ void stage_rows(const uint32_t (&v)[32], float A, float B, uint32_t row, unsigned sel,
+                                           int lane, float* tbuf) {
+    if ((sel >> lane) & 1u) {
+        float4* dst = reinterpret_cast<float4*>(tbuf + __popc(sel & ((1u << lane) - 1u)) * kTStride);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const uint32_t t = __shfl_sync(kFull, v[j], e);
-            x = lane == j ? t : x;
-        }
-        const float score = fmaf(Be, __uint_as_float(x), Ae);
-        if (score <= o.tau_s[G]) {
-            const u64 key = score_key(score, rowe);
-            if (score < o.tau_s[G] || key <= __ldg(p.tau_key + o.q[G])) {
-                o.slot[(G * kOwnSlots + o.n[G]) * kEpiThreads] = key;
-                if (++o.n[G] == kOwnSlots) flush_owner(p, o, G);
+        for (int j = 0; j < 8; ++j)
+            dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]), __uint_as_float(v[4 * j + 2]),
+                                 __uint_as_float(v[4 * j + 3]));
+        dst[8] = make_float4(A, B, __uint_as_float(row), 0.f);
+    }
+}
+
+// Lane l checks column l -- the query it owns -- of the nsel buffered rows.
+__device__ __forceinline__ void check_rows(const MainParams& p, const float* tbuf, int nsel, int lane, u64* slot,
+                                           const int* own_q, const float* own_tau, int& n_own) {
+    const float tau_own = *own_tau;
+    for (int r = 0; r < nsel; ++r) {
+        const float x = tbuf[r * kTStride + lane];
+        const float4 mt = *reinterpret_cast<const float4*>(tbuf + r * kTStride + 32);
+        const float score = fmaf(mt.y, x, mt.x);
+        if (score <= tau_own) {
+            const int q_own = *own_q;
+            const u64 key = score_key(score, __float_as_uint(mt.z));
+            if (score < tau_own || key <= __ldg(p.tau_key + q_own)) {
+                slot[n_own * kMainEpiThreads] = key;
+                if (++n_own == kOwnSlots) {
+                    flush_owned(p, slot, q_own, n_own);
+                    n_own = 0;
+                }
             }
         }
     }
 }
 
+// All rows of `ev`, kTRows at a time.
+__device__ __forceinline__ void main_survivors(const MainParams& p, const uint32_t (&v)[32], float A, float B,
+                                               unsigned ev, uint32_t row, int lane, float* tbuf, u64* slot,
+                                               const int* own_q, const float* own_tau, int& n_own) {
+    const unsigned lt = (1u << lane) - 1u;
+    while (ev) {
+        const unsigned sel = __ballot_sync(kFull, ((ev >> lane) & 1u) && __popc(ev & lt) < kTRows);
+        stage_rows(v, A, B, row, sel, lane, tbuf);
+        __syncwarp();
+        check_rows(p, tbuf, __popc(sel), lane, slot, own_q, own_tau, n_own);
+        __syncwarp();
+        ev &= ~sel;
+    }
+}
+
 // Main pass: every key <= tau_q of the chunk into query q's candidate buffer.
+// The query block is kQTile = 256 queries in ascending-threshold order (the MMA's
+// B operand, resident in shared memory); the database tile is the A operand,
+// so a TMEM lane -- an epilogue thread -- is a database row and a column is a
+// query. Two 256-column FP32 accumulators fill TMEM; the tensor core works on
+// one tile while the epilogue reads the other.
 template <bool kFp8>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kMainThreads, 1)
     tc_main_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmX, const MainParams p) {
     extern __shared__ unsigned char smem_raw[];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -596,15 +657,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char* smem =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int stages = p.stages;
-    unsigned char* sQ = smem;                                   // slices x 16 KB: the block's query codes
-    unsigned char* sX = sQ + (size_t)p.slices * kSliceTile;     // stages x 16 KB: database slices
-    u64* own_slot = reinterpret_cast<u64*>(sX + (size_t)stages * kSliceTile);  // 2 kOwnSlots x kEpiThreads
-    u64* full = own_slot + 2 * kOwnSlots * kEpiThreads;
+    constexpr int kQSlice = kQTile * kSliceBytes;               // 32 KB: one K slice of the query block
+    unsigned char* sQ = smem;                                   // slices x 32 KB: the block's query codes
+    unsigned char* sX = sQ + (size_t)p.slices * kQSlice;        // stages x 16 KB: database slices
+    u64* own_slot = reinterpret_cast<u64*>(sX + (size_t)stages * kSliceTile);  // kMGroups kOwnSlots x threads
+    float* tbuf_all = reinterpret_cast<float*>(own_slot + kMGroups * kOwnSlots * kMainEpiThreads);
+    int* own_q_all = reinterpret_cast<int*>(tbuf_all + kMainEpiWarps * kTRows * kTStride);
+    float* own_tau_all = reinterpret_cast<float*>(own_q_all + kMGroups * kMainEpiThreads);  // kMGroups x threads
+    u64* full = reinterpret_cast<u64*>(own_tau_all + kMGroups * kMainEpiThreads);  // after the buffers below
     u64* empty = full + kMaxStages;
     u64* q_full = empty + kMaxStages;
     u64* acc_full = q_full + 1;
-    u64* acc_empty = acc_full + kAcc;
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + kAcc);
+    u64* acc_empty = acc_full + kMainAcc;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + kMainAcc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
     const int64_t row0 = (int64_t)chunk * p.chunk_rows;
@@ -613,37 +678,49 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int kElemPerSlice = kFp8 ? 128 : 64;
     constexpr int kMmaK = kFp8 ? 32 : 16;
     constexpr int kMmaPerSlice = kElemPerSlice / kMmaK;
-    constexpr uint32_t kIdesc = tc_idesc(kFp8);
+    constexpr uint32_t kIdesc = tc_idesc(kFp8, kQTile);
 
+    // The cs CTAs of a cluster work on the same chunk for cs query blocks: each loads 1/cs of every
+    // database slice and multicasts it to all of them, so a slot is free again once every CTA's
+    // tensor core has read it (empty: one multicast commit from each CTA).
+    const int cs = p.cs;
+    const uint16_t cmask = (uint16_t)((1u << cs) - 1u);
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], (uint32_t)cs);
         }
         mbar_init(q_full, 1);
-        for (int i = 0; i < kAcc; ++i) {
+        for (int i = 0; i < kMainAcc; ++i) {
             mbar_init(&acc_full[i], 1);
-            mbar_init(&acc_empty[i], kEpiWarps);
+            mbar_init(&acc_empty[i], kMainEpiWarps);
         }
         *abort_flag = 0;
         fence_mbar_init();
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                     "r"(kAcc * kTile)
+                     "r"(kMainAcc * kQTile)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
-    __syncthreads();
+    if (cs > 1) cluster_sync();  // every CTA's barriers exist before any multicast reaches them
+    else __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
 
     if (warp == 0) {
         if (lane == 0) {
-            mbar_arrive_expect_tx(q_full, (uint32_t)p.slices * kSliceTile);
+            // the query block: per K slice two 128-row boxes, rows 0-127 and 128-255 of the slice
+            mbar_arrive_expect_tx(q_full, (uint32_t)p.slices * kQSlice);
             for (int s = 0; s < p.slices; ++s)
-                tma_load_2d(sQ + (size_t)s * kSliceTile, &tmQ, s * kElemPerSlice, qblock * kTile, q_full);
+                for (int hq = 0; hq < kQTile / kTile; ++hq)
+                    tma_load_2d(sQ + (size_t)s * kQSlice + (size_t)hq * kSliceTile, &tmQ, s * kElemPerSlice,
+                                qblock * kQTile + hq * kTile, q_full);
+            const int rank = cs > 1 ? (int)cluster_ctarank() : 0;
+            const int piece_rows = kTile / cs;
+            const uint32_t piece_off = (uint32_t)(rank * piece_rows * kSliceBytes);
             int b_issued = 0, st = 0;
             uint32_t ph = 0;
             for (int t = 0; t < ntiles && !*abort_flag; ++t) {
@@ -655,7 +732,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     mbar_arrive_expect_tx(&full[st], kSliceTile);
-                    tma_load_2d(sX + (size_t)st * kSliceTile, &tmX, s * kElemPerSlice, r, &full[st]);
+                    if (cs > 1)
+                        tma_load_2d_mc(sX + (size_t)st * kSliceTile + piece_off, &tmX, s * kElemPerSlice,
+                                       r + rank * piece_rows, &full[st], cmask);
+                    else
+                        tma_load_2d(sX + (size_t)st * kSliceTile, &tmX, s * kElemPerSlice, r, &full[st]);
                     ++b_issued;
                     if (++st == stages) {
                         st = 0;
@@ -669,6 +750,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int it = b_issued > stages ? b_issued - stages : 0; it < b_issued; ++it)
                     mbar_wait(&full[it % stages], (uint32_t)((it / stages) & 1), nullptr);
             }
+            if (cs > 1) {
+                // every CTA's release of the last slots has reached this CTA's barriers (bounded waits)
+                for (int it = b_issued > stages ? b_issued - stages : 0; it < b_issued; ++it)
+                    mbar_wait(&empty[it % stages], (uint32_t)((it / stages) & 1), nullptr);
+            }
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -676,13 +762,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             int st = 0;
             uint32_t ph = 0;
             for (int t = 0; ok && t < ntiles; ++t) {
-                const int a = t % kAcc;
-                if (!mbar_wait(&acc_empty[a], (uint32_t)((t / kAcc) & 1) ^ 1u, abort_flag)) {
+                const int a = t % kMainAcc;
+                if (!mbar_wait(&acc_empty[a], (uint32_t)((t / kMainAcc) & 1) ^ 1u, abort_flag)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(a * kTile);
+                const uint32_t d_tmem = tmem + (uint32_t)(a * kQTile);
                 for (int s = 0; s < p.slices; ++s) {
                     if (!mbar_wait(&full[st], ph, abort_flag)) {
                         ok = false;
@@ -690,14 +776,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tc_fence_after();
                     const uint32_t x_base = smem_u32(sX + (size_t)st * kSliceTile);
-                    const uint32_t q_base = smem_u32(sQ + (size_t)s * kSliceTile);
+                    const uint32_t q_base = smem_u32(sQ + (size_t)s * kQSlice);
 #pragma unroll
                     for (int kk = 0; kk < kMmaPerSlice; ++kk) {
                         const uint32_t off = (uint32_t)(kk * kMmaK * (kFp8 ? 1 : 2));
                         tc_mma<kFp8>(d_tmem, sw128_desc(x_base + off), sw128_desc(q_base + off), kIdesc,
                                      (s | kk) != 0 ? 1u : 0u);
                     }
-                    tc_commit(&empty[st]);
+                    if (cs > 1) tc_commit_mc(&empty[st], cmask);
+                    else tc_commit(&empty[st]);
                     if (++st == stages) {
                         st = 0;
                         ph ^= 1u;
@@ -713,32 +800,36 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------------ epilogue: thread = database row
-        const int quad = warp & 3;                     // TMEM lane quadrant this warp may access
-        const int rl = quad * 32 + lane;               // row within the tile
-        const int half = (warp - 2) / 4;               // column (query) half this warp scores
-        const int cb = half * (kTile / kHalves);
-        const int64_t q0 = (int64_t)qblock * kTile + cb;  // the thread's first query
-        static_assert(kTile / kHalves == 64, "two 32-column loads per warp and tile");
-        float2 ntau[32];                               // -tau of queries q0 + 2i, q0 + 2i + 1
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-            ntau[i] = make_float2(-__ldg(p.tau_s + q0 + 2 * i), -__ldg(p.tau_s + q0 + 2 * i + 1));
-        const float m = __ldg(p.qs + 1);
-        Owner o;
-        o.slot = own_slot + (threadIdx.x - 64);
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-            o.q[g] = q0 + 32 * g + lane;
-            o.tau_s[g] = o.q[g] < p.nq ? __ldg(p.tau_s + o.q[g]) : -__int_as_float(0x7f800000);
-            o.n[g] = 0;
+        const int ew = warp - 2;                        // epilogue warp 0 .. kMainEpiWarps - 1
+        const int quad = warp & 3;                      // TMEM lane quadrant this warp may access
+        const int rl = quad * 32 + lane;                // row within the tile
+        const int cb = (ew / 4) * (32 * kMGroups);      // first column (query) of this warp's quarter
+        const int64_t p0 = (int64_t)qblock * kQTile + cb;  // sorted position of that query
+        float* tbuf = tbuf_all + ew * kTRows * kTStride;
+        const int et = threadIdx.x - 64;                // epilogue thread 0 .. kMainEpiThreads - 1
+        u64* slot0 = own_slot + et;
+        u64* slot1 = slot0 + kOwnSlots * kMainEpiThreads;
+        const float T0 = __ldg(p.tgrp + p0 / 32), T1 = __ldg(p.tgrp + p0 / 32 + 1);
+        {
+            // the queries this lane owns (column lane of each group) and their thresholds, read only
+            // on the rare survivor path: kept in shared memory, not registers
+            const float ninf = -__int_as_float(0x7f800000);
+            for (int g = 0; g < kMGroups; ++g) {
+                const int q = __ldg(p.perm + p0 + 32 * g + lane);
+                own_q_all[g * kMainEpiThreads + et] = q;
+                own_tau_all[g * kMainEpiThreads + et] = q >= 0 ? __ldg(p.tau_s + q) : ninf;
+            }
         }
-        float2 sn_next = ntiles > 0 ? __ldg(p.sn + row0 + rl) : make_float2(0.f, 0.f);
+        int n0 = 0, n1 = 0;
+        const float m = __ldg(p.qs + 1);
+        const int rows_left = (int)(row1 - row0);       // rows of this chunk (< 2^31)
+        const float2* snp = p.sn + row0 + rl;
+        float2 sn_next = ntiles > 0 ? __ldg(snp) : make_float2(0.f, 0.f);
         for (int t = 0; t < ntiles; ++t) {
-            const int a = t % kAcc;
-            const int64_t r = row0 + (int64_t)t * kTile;
+            const int a = t % kMainAcc;
             const float2 sn = sn_next;  // rows past the database read its zero padding
-            if (t + 1 < ntiles) sn_next = __ldg(p.sn + r + kTile + rl);
-            if (!mbar_wait(&acc_full[a], (uint32_t)((t / kAcc) & 1), abort_flag)) {
+            if (t + 1 < ntiles) sn_next = __ldg(snp + (t + 1) * kTile);
+            if (!mbar_wait(&acc_full[a], (uint32_t)((t / kMainAcc) & 1), abort_flag)) {
                 if (lane == 0) {
                     *abort_flag = 1;
                     record_error(p.err, kErrTimeout);
@@ -746,31 +837,42 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             tc_fence_after();
-            const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kTile + cb);
-            uint32_t va[32], vb[32];
-            tmem_ld32_issue(tbase, va);
-            tmem_ld32_issue(tbase + 32u, vb);
-            tmem_ld_wait(va);  // waits for both loads; the second wait only names vb's registers
-            tmem_ld_wait(vb);
+            const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kQTile + cb);
             const float B = m * sn.x, A = sn.y;
-            const bool rowvalid = r + rl < row1;
-            const float2 A2 = make_float2(A, A), B2 = make_float2(B, B);
-            const unsigned eva = __ballot_sync(kFull, rowvalid && main_group_min<0>(va, ntau, A2, B2) <= 0.f);
-            const unsigned evb = __ballot_sync(kFull, rowvalid && main_group_min<1>(vb, ntau, A2, B2) <= 0.f);
-            if (eva) main_survivors<0>(p, va, A, B, (uint32_t)(r + rl), eva, lane, o);
-            if (evb) main_survivors<1>(p, vb, A, B, (uint32_t)(r + rl), evb, lane, o);
+            const int rr = t * kTile + rl;                 // row within the chunk
+            const bool rowvalid = rr < rows_left;
+            const uint32_t row = (uint32_t)(row0 + rr);
+            // per group: the row's smallest score over the group's queries is fma(B, max dot, A)
+            // (B = m s_j <= 0, and a correctly rounded fma is monotone in each operand), tested
+            // against the group's largest threshold. One group in registers at a time: 18 warps
+            // leave 96 registers per thread.
+            // one 32-column group in registers at a time: 18 warps leave 96 registers per thread
+            uint32_t v[32];
+            tmem_ld32_issue(tbase, v);
+            tmem_ld_wait(v);
+            const unsigned ev0 = __ballot_sync(kFull, rowvalid && fmaf(B, max32(v), A) <= T0);
+            if (ev0) main_survivors(p, v, A, B, ev0, row, lane, tbuf, slot0, own_q_all + et, own_tau_all + et, n0);
+            tmem_ld32_issue(tbase + 32u, v);
+            tmem_ld_wait(v);
+            // the accumulator is in registers: hand it back to the MMA issuer before scoring
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[a]);
+            const unsigned ev1 = __ballot_sync(kFull, rowvalid && fmaf(B, max32(v), A) <= T1);
+            if (ev1)
+                main_survivors(p, v, A, B, ev1, row, lane, tbuf, slot1, own_q_all + kMainEpiThreads + et,
+                               own_tau_all + kMainEpiThreads + et, n1);
         }
-        for (int g = 0; g < 2; ++g)
-            if (o.n[g]) flush_owner(p, o, g);
+        if (n0) flush_owned(p, slot0, own_q_all[et], n0);
+        if (n1) flush_owned(p, slot1, own_q_all[kMainEpiThreads + et], n1);
     }
     tc_fence_before();
-    __syncthreads();
+    if (cs > 1) cluster_sync();  // no CTA leaves while another may still deliver to its shared memory
+    else __syncthreads();
     tc_fence_after();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAcc * kTile) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMainAcc * kQTile)
+                     : "memory");
 }
 
 __device__ __forceinline__ u64 warp_min_u64(u64 v) {
@@ -823,6 +925,77 @@ __global__ void tau_kernel(const u64* __restrict__ pilot, int lists, int nq, int
     if (lane == 0) {
         tau_key[q] = tau;
         tau_s[q] = tau == kKeyEmpty ? __int_as_float(0x7f800000) : key_score(tau);
+    }
+}
+
+// Orders the batch's queries by threshold score for the main pass (CTA b
+// writes sorted positions [256 b, 256 b + 256)): every CTA sorts all
+// (threshold score, query) keys in shared memory with a bitonic network
+// (batches of more than kSortMax queries keep their order), then writes, for
+// its positions, the query there (perm, -1 = padding), its codes (a zero row
+// for padding), and per 32 positions the largest threshold among their
+// queries (tgrp). Adjacent thresholds make the main pass's per-group bound
+// tight.
+constexpr int kSortMax = 16384;
+constexpr int kSortThreads = 512;
+
+__global__ void __launch_bounds__(kSortThreads) sort_queries_kernel(const float* __restrict__ tau_s, int nq,
+                                                                    int n_sorted, const uint4* __restrict__ codes,
+                                                                    int row_chunks, uint4* __restrict__ codes_s,
+                                                                    int* __restrict__ perm, float* __restrict__ tgrp) {
+    extern __shared__ u64 keys[];  // n2 >= n_sorted (a power of two), when sorting
+    __shared__ int spos[kQTile];
+    const int tid = threadIdx.x;
+    const int base = blockIdx.x * kQTile;
+    if (n_sorted <= kSortMax) {
+        int n2 = 1;
+        while (n2 < n_sorted) n2 <<= 1;
+        for (int i = tid; i < n2; i += blockDim.x) {
+            uint32_t u = 0xffffffffu;  // padding positions sort last, in index order
+            if (i < nq) {
+                u = __float_as_uint(tau_s[i]);
+                u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+                u = min(u, 0xfffffffeu);
+            }
+            keys[i] = ((u64)u << 32) | (uint32_t)i;
+        }
+        __syncthreads();
+        for (int size = 2; size <= n2; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = tid; i < n2 / 2; i += blockDim.x) {
+                    const int lo = 2 * i - (i & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const u64 x = keys[lo], y = keys[hi];
+                    if ((x > y) == up) {
+                        keys[lo] = y;
+                        keys[hi] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = tid; i < kQTile; i += blockDim.x) {
+            const int q = (int)(uint32_t)keys[base + i];
+            spos[i] = q < nq ? q : -1;
+        }
+    } else {
+        for (int i = tid; i < kQTile; i += blockDim.x) spos[i] = base + i < nq ? base + i : -1;
+    }
+    __syncthreads();
+    for (int i = tid; i < kQTile; i += blockDim.x) perm[base + i] = spos[i];
+    const int warp = tid / 32, lane = tid % 32;
+    for (int g = warp; g < kQTile / 32; g += blockDim.x / 32) {
+        const int q = spos[g * 32 + lane];
+        float t = q >= 0 ? tau_s[q] : -__int_as_float(0x7f800000);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(kFull, t, o));
+        if (lane == 0) tgrp[(base >> 5) + g] = t;
+    }
+    for (int i = tid; i < kQTile * row_chunks; i += blockDim.x) {
+        const int r = i / row_chunks, c = i % row_chunks;
+        const int q = spos[r];
+        codes_s[(size_t)(base + r) * row_chunks + c] = q >= 0 ? codes[(size_t)q * row_chunks + c] : make_uint4(0, 0, 0, 0);
     }
 }
 
@@ -1069,13 +1242,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 2-D map over a row-major rows x D array of 1- or 2-byte codes; box = 128
 // bytes of K by 128 rows, 128-byte swizzle, zero fill past the last row.
-bool make_map(CUtensorMap* map, const void* base, int64_t rows, int D, bool fp8) {
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int D, bool fp8, int box_rows = kTile) {
     auto fn = encode_fn();
     if (!fn) return false;
     const int elem = fp8 ? 1 : 2;
     cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)D * elem};
-    cuuint32_t box[2] = {(cuuint32_t)(kSliceBytes / elem), (cuuint32_t)kTile};
+    cuuint32_t box[2] = {(cuuint32_t)(kSliceBytes / elem), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     const CUresult r = fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                           const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -1103,15 +1276,18 @@ Chunking chunking(int64_t rows, int qblocks, int sms) {
 
 struct LowpPlan {
     int nq_pad, qblocks, wmax;
+    int nq_sorted, qblocks_main;  // main pass: 256-query blocks of threshold-sorted queries
     bool sampled;
     Chunking main, pilot;
-    size_t codes_bytes, qs_bytes, pilot_bytes, tau_bytes, cnt_bytes, cand_bytes, partial_bytes;
+    size_t codes_bytes, qs_bytes, pilot_bytes, tau_bytes, cnt_bytes, cand_bytes, partial_bytes, sort_bytes;
 };
 
 LowpPlan plan(const lhr_db* db, int nq, bool fp8, int W) {
     LowpPlan pl{};
     pl.nq_pad = (nq + kTile - 1) / kTile * kTile;
     pl.qblocks = pl.nq_pad / kTile;
+    pl.nq_sorted = (nq + kQTile - 1) / kQTile * kQTile;
+    pl.qblocks_main = pl.nq_sorted / kQTile;
     pl.wmax = W <= 32 ? 32 : (W <= 64 ? 64 : 128);
     pl.sampled = (fp8 ? db->X8_s : db->Xb_s) != nullptr;
     pl.main = chunking(db->n, pl.qblocks, db->sms);
@@ -1124,6 +1300,10 @@ LowpPlan plan(const lhr_db* db, int nq, bool fp8, int W) {
     pl.cnt_bytes = pl.sampled ? a256((size_t)nq * sizeof(unsigned)) : 0;
     pl.cand_bytes = pl.sampled ? a256((size_t)nq * kCap * sizeof(u64)) : 0;
     pl.partial_bytes = a256((size_t)nq * pl.main.nchunks * kHalves * W * sizeof(u64));
+    // sorted codes, perm, group thresholds
+    pl.sort_bytes = pl.sampled ? a256((size_t)pl.nq_sorted * db->dim * elem) + a256((size_t)pl.nq_sorted * sizeof(int)) +
+                                     a256((size_t)pl.nq_sorted / 32 * sizeof(float))
+                               : 0;
     return pl;
 }
 
@@ -1145,8 +1325,10 @@ int tc_stages(int slices, int mode) {
 size_t tc_smem(int slices, int stages, int mode) { return tc_smem_fixed(slices, mode) + (size_t)stages * kSliceTile; }
 
 size_t main_smem(int slices, int stages) {
-    return 1024 + (size_t)(slices + stages) * kSliceTile + (size_t)2 * kOwnSlots * kEpiThreads * sizeof(u64) +
-           (2 * kMaxStages + 1 + 2 * kAcc) * sizeof(u64) + 16;
+    return 1024 + (size_t)slices * kQTile * kSliceBytes + (size_t)stages * kSliceTile +
+           (size_t)kMGroups * kOwnSlots * kMainEpiThreads * sizeof(u64) +
+           (size_t)kMainEpiWarps * kTRows * kTStride * sizeof(float) + (size_t)2 * kMGroups * kMainEpiThreads * 4 +
+           (2 * kMaxStages + 1 + 2 * kMainAcc) * sizeof(u64) + 16;
 }
 
 int main_stages(int slices) {
@@ -1160,12 +1342,61 @@ cudaError_t launch_main(const CUtensorMap& mq, const CUtensorMap& mx, const Main
                         cudaStream_t stream) {
     auto kern = tc_main_kernel<kFp8>;
     if (mp.stages < 2 || mp.stages > kMaxStages) return cudaErrorInvalidValue;
+    if (mp.cs < 1 || qblocks % mp.cs || kTile % mp.cs) return cudaErrorInvalidValue;
     const size_t sm = main_smem(mp.slices, mp.stages);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     ProfScope ps(kFp8 ? "tc_main_kernel_fp8" : "tc_main_kernel_bf16", stream);
-    kern<<<dim3(mp.nchunks, qblocks), kThreads, sm, stream>>>(mq, mx, mp);
+    // qblocks of kQTile queries; clusters of mp.cs CTAs along them
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(mp.nchunks, qblocks);
+    cfg.blockDim = dim3(kMainThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = (unsigned)mp.cs;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, mq, mx, mp);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+// Clusters of cs main-pass CTAs that can be resident at once (cached per device, format and size).
+template <bool kFp8>
+cudaError_t main_max_clusters(size_t smem, int cs, int* out) {
+    static std::mutex mu;
+    static int cache[64][3] = {};  // [device][log2 cs]
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int li = cs == 4 ? 2 : (cs == 2 ? 1 : 0);
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 64 && cache[dev][li] > 0) {
+        *out = cache[dev][li];
+        return cudaSuccess;
+    }
+    auto kern = tc_main_kernel<kFp8>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1);
+    cfg.blockDim = dim3(kMainThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if ((e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg)) != cudaSuccess) return e;
+    if (dev < 64) cache[dev][li] = n;
+    *out = n;
+    return cudaSuccess;
 }
 
 template <bool kFp8, int MODE, int WMAX>
@@ -1195,7 +1426,7 @@ cudaError_t launch_full(int wmax, const CUtensorMap& ma, const CUtensorMap& mb, 
 size_t lowp_scratch_bytes(const lhr_db* db, int nq, bool fp8, int W) {
     const LowpPlan pl = plan(db, nq, fp8, W);
     return pl.codes_bytes + pl.qs_bytes + pl.pilot_bytes + pl.tau_bytes + pl.cnt_bytes + pl.cand_bytes +
-           pl.partial_bytes;
+           pl.partial_bytes + pl.sort_bytes;
 }
 
 cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int W, int k, int64_t* idx, float* dist,
@@ -1216,6 +1447,11 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
     u64* cand = reinterpret_cast<u64*>(base);
     base += pl.cand_bytes;
     u64* partial = reinterpret_cast<u64*>(base);
+    base += pl.partial_bytes;
+    void* codes_s = base;
+    int* perm = reinterpret_cast<int*>(base + a256((size_t)pl.nq_sorted * db->dim * (fp8 ? 1 : 2)));
+    float* tgrp = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(perm) +
+                                           a256((size_t)pl.nq_sorted * sizeof(int)));
     cudaError_t e;
     {
         ProfScope ps("quantize_queries_kernel", stream);
@@ -1261,14 +1497,50 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
                                                                  tau_key, tau_s);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
+        {
+            // queries in ascending-threshold order, in 256-query blocks, for the main pass
+            ProfScope ps("sort_queries_kernel", stream);
+            int n2 = 1;
+            while (n2 < pl.nq_sorted) n2 <<= 1;
+            const size_t ssm = pl.nq_sorted <= kSortMax ? (size_t)n2 * sizeof(u64) : 0;
+            if ((e = cudaFuncSetAttribute(sort_queries_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)ssm)) != cudaSuccess)
+                return e;
+            sort_queries_kernel<<<pl.qblocks_main, kSortThreads, ssm, stream>>>(
+                tau_s, nq, pl.nq_sorted, reinterpret_cast<const uint4*>(codes), db->dim * (fp8 ? 1 : 2) / 16,
+                reinterpret_cast<uint4*>(codes_s), perm, tgrp);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        // one CTA per cluster: sharing each database tile across the query blocks of a cluster (each
+        // CTA loading 1/cs of it) cuts L2 reads but couples the CTAs' pipelines, and measured slower
+        const int cs = 1;
+        CUtensorMap mqs, mxp;
+        if (!make_map(&mqs, codes_s, pl.nq_sorted, db->dim, fp8) ||
+            !make_map(&mxp, fp8 ? db->X8 : db->Xb, db->n, db->dim, fp8, kTile / cs))
+            return cudaErrorInvalidValue;
         // main pass: every key <= tau into the candidate buffers
         if ((e = cudaMemsetAsync(cnt, 0, (size_t)nq * sizeof(unsigned), stream)) != cudaSuccess) return e;
         MainParams mp{};
         mp.n = db->n;
         mp.slices = tp.slices;
         mp.stages = main_stages(tp.slices);
-        mp.chunk_rows = pl.main.chunk_rows;
-        mp.nchunks = pl.main.nchunks;
+        {
+            // as many chunks as keep every cluster resident at once (clusters live inside one GPC,
+            // so fewer than sms / cs clusters may fit): no second wave
+            int max_clusters = 0;
+            const size_t msm = main_smem(mp.slices, main_stages(mp.slices));
+            if ((fp8 ? main_max_clusters<true>(msm, cs, &max_clusters)
+                     : main_max_clusters<false>(msm, cs, &max_clusters)) != cudaSuccess ||
+                max_clusters < 1)
+                max_clusters = db->sms / cs;
+            const int max_ctas = std::min(db->sms, max_clusters * cs);
+            const Chunking c = chunking(db->n, pl.qblocks_main, max_ctas);
+            mp.chunk_rows = c.chunk_rows;
+            mp.nchunks = c.nchunks;
+        }
+        mp.perm = perm;
+        mp.tgrp = tgrp;
+        mp.cs = cs;
         mp.sn = fp8 ? db->sn8 : db->snb;
         mp.qs = qs;
         mp.tau_s = tau_s;
@@ -1277,7 +1549,8 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
         mp.cnt = cnt;
         mp.nq = nq;
         mp.err = db->err;
-        e = fp8 ? launch_main<true>(ma, mb, mp, pl.qblocks, stream) : launch_main<false>(ma, mb, mp, pl.qblocks, stream);
+        e = fp8 ? launch_main<true>(mqs, mxp, mp, pl.qblocks_main, stream)
+                : launch_main<false>(mqs, mxp, mp, pl.qblocks_main, stream);
         if (e != cudaSuccess) return e;
     }
     // full pass: always without a sample, otherwise only where a main pass fell short
