@@ -184,7 +184,7 @@ def measure_gemm_peak(dev, kind: str, n: int = 8192, reps: int = 10):
 
 
 # every kernel the library times under lhr_profile_enable (names as it records them)
-KERNELS = ("quantize_queries_kernel", "tc_pilot_kernel_fp8", "tc_pilot_kernel_bf16", "tau_kernel",
+KERNELS = ("quantize_queries_kernel", "tc_pilot_kernel_fp8", "tc_pilot_kernel_bf16", "tau_kernel", "sort_queries_kernel",
            "tc_main_kernel_fp8", "tc_main_kernel_bf16", "tc_full_kernel_fp8", "tc_full_kernel_bf16",
            "merge_rerank_kernel", "scan_pilot", "scan_topk_kernel", "small_topk_kernel", "aggregate_kernel",
            "hier_fused_kernel", "coarse_kernel", "collect_kernel", "shortlist_kernel", "wnorm_kernel",

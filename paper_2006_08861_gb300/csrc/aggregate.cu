@@ -1,6 +1,7 @@
 // Algorithm 2 (§3.2): 2-D multi-frame localization candidate aggregation,
-// one CTA per window, entirely on the device so a window's answer never makes
-// a host round trip.
+// one warp per window (one CTA for windows of more than 1,024 candidate
+// slots), entirely on the device so a window's answer never makes a host
+// round trip.
 //
 //   initialization  candidate row -> floor-plan tile through the database's
 //                   geo-referenced table (tiles precomputed at build:
@@ -51,8 +52,8 @@ __device__ T block_sum(T v, T* red) {
     return s;
 }
 
-__global__ void __launch_bounds__(kAggThreads) aggregate_kernel(const AggParams p) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// Window w (kWarpCand < total <= kMaxCand candidate slots from b0) by the whole block.
+__device__ void aggregate_block(const AggParams& p, int w, long long b0, long long total, unsigned char* smem) {
     u64* keys = reinterpret_cast<u64*>(smem);                      // kMaxCand tile keys (sorted)
     int* cand_rows = reinterpret_cast<int*>(keys + kMaxCand);      // kMaxCand candidate rows
     float* cand_d = reinterpret_cast<float*>(cand_rows + kMaxCand);  // kMaxCand distances
@@ -62,25 +63,7 @@ __global__ void __launch_bounds__(kAggThreads) aggregate_kernel(const AggParams 
     int* ctl = reinterpret_cast<int*>(redl + 32);                  // control words
 
     const AggArgs& a = p.a;
-    const int w = blockIdx.x;
     const int t = threadIdx.x;
-    long long b0 = a.offsets[w], b1 = a.offsets[w + 1];
-    if (a.per_frame > 0) {
-        b0 *= a.per_frame;
-        b1 *= a.per_frame;
-    }
-    const long long total = b1 - b0;
-    if (total <= 0 || total > kMaxCand || b0 < 0 || b1 > a.limit) {
-        if (t == 0) {
-            a.status[w] = kErrInvalidArg;
-            a.xy_out[2 * w] = a.xy_out[2 * w + 1] = __longlong_as_double(0x7ff8000000000000ll);
-        }
-        return;
-    }
-    if (total <= kWarpCand) {
-        if (t < 32) aggregate_warp(p, w, b0, total, keys, cand_rows, cand_d, cnt);
-        return;
-    }
     if (t == 0) ctl[0] = 0;
     __syncthreads();
     // initialization: rows -> tiles (padding rows -1 are skipped)
@@ -284,7 +267,57 @@ __global__ void __launch_bounds__(kAggThreads) aggregate_kernel(const AggParams 
     }
 }
 
-size_t agg_smem() {
+// Per-warp shared memory of the warp path: tile keys, rows and distances of up
+// to kWarpCand slots, and kWarpCand + 1 run starts (16-byte multiple).
+constexpr size_t kWarpSlice = ((size_t)kWarpCand * (sizeof(u64) + 2 * sizeof(int)) + (kWarpCand + 1) * sizeof(int) + 15) / 16 * 16;
+constexpr int kAggWindows = kAggThreads / 32;  // windows per CTA: one per warp
+
+// Algorithm 2 for kAggWindows windows per CTA: each warp takes one window of at
+// most kWarpCand slots in its own slice of shared memory; larger windows are
+// then run one at a time by the whole block over all of it.
+__global__ void __launch_bounds__(kAggThreads) aggregate_kernel(const AggParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int large_w[kAggWindows];
+    __shared__ long long large_b0[kAggWindows], large_n[kAggWindows];
+    const AggArgs& a = p.a;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = blockIdx.x * kAggWindows + warp;
+    bool large = false;
+    long long b0 = 0, total = 0;
+    if (w < a.nw) {
+        b0 = a.offsets[w];
+        long long b1 = a.offsets[w + 1];
+        if (a.per_frame > 0) {
+            b0 *= a.per_frame;
+            b1 *= a.per_frame;
+        }
+        total = b1 - b0;
+        if (total <= 0 || total > kMaxCand || b0 < 0 || b1 > a.limit) {
+            if (lane == 0) write_invalid(a, w);
+        } else if (total <= kWarpCand) {
+            unsigned char* sl = smem + (size_t)warp * kWarpSlice;
+            u64* keys = reinterpret_cast<u64*>(sl);
+            int* rows = reinterpret_cast<int*>(keys + kWarpCand);
+            float* dd = reinterpret_cast<float*>(rows + kWarpCand);
+            int* cnt = reinterpret_cast<int*>(dd + kWarpCand);
+            aggregate_warp(p, w, b0, total, keys, rows, dd, cnt);
+        } else {
+            large = true;
+        }
+    }
+    if (lane == 0) {
+        large_w[warp] = large ? w : -1;
+        large_b0[warp] = b0;
+        large_n[warp] = total;
+    }
+    __syncthreads();
+    for (int k = 0; k < kAggWindows; ++k) {
+        if (large_w[k] >= 0) aggregate_block(p, large_w[k], large_b0[k], large_n[k], smem);
+        __syncthreads();
+    }
+}
+
+constexpr size_t agg_smem() {
     return kMaxCand * (sizeof(u64) + sizeof(int) + sizeof(float) + sizeof(int)) + 2 * sizeof(int) +
            32 * (sizeof(double) + sizeof(long long)) + (8 + kAggThreads / 32) * sizeof(int);
 }
@@ -309,10 +342,11 @@ cudaError_t launch_aggregate(const lhr_db* db, const AggArgs& a, cudaStream_t st
     p.rlim = (long long)floor(sqrt((double)a.r2max)) + 1;
     p.err = db->err;
     const size_t sm = agg_smem();
+    static_assert(kAggWindows * kWarpSlice <= agg_smem(), "the warps' slices fit in the block path's shared memory");
     cudaError_t e = cudaFuncSetAttribute(aggregate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     ProfScope ps("aggregate_kernel", stream);
-    aggregate_kernel<<<a.nw, kAggThreads, sm, stream>>>(p);
+    aggregate_kernel<<<(a.nw + kAggWindows - 1) / kAggWindows, kAggThreads, sm, stream>>>(p);
     return cudaGetLastError();
 }
 

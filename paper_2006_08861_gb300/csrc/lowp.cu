@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                 }
-                        };
+            };
             static_assert(kTile / kHalves == 64, "two 32-column loads per warp and tile");
             const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kTile);
             const int cb = half * (kTile / kHalves);
@@ -1161,7 +1161,8 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_rerank_kernel(
         warp_sort(cw, p2, lane);
     }
     const int take = min(n, W);
-    // FP32 direct re-rank of the shortlist, four rows in flight
+    // FP32 direct re-rank of the shortlist, kInFlight rows in flight
+    constexpr int kInFlight = CPL <= 2 ? 8 : 4;
     const int D4 = D / 4;
     float4 qv[CPL];
 #pragma unroll
@@ -1171,11 +1172,11 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_rerank_kernel(
     }
     const float2 neg1 = make_float2(-1.f, -1.f);
     u64 L = kKeyEmpty, thr = kKeyEmpty;
-    for (int i0 = 0; i0 < take; i0 += 4) {
-        uint32_t r[4];
-        float4 x[4][CPL];
+    for (int i0 = 0; i0 < take; i0 += kInFlight) {
+        uint32_t r[kInFlight];
+        float4 x[kInFlight][CPL];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < kInFlight; ++b) {
             r[b] = i0 + b < take ? (uint32_t)cw[i0 + b] : 0xffffffffu;
 #pragma unroll
             for (int j = 0; j < CPL; ++j) {
@@ -1185,9 +1186,9 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_rerank_kernel(
                               : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
-        float d[4];
+        float d[kInFlight];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < kInFlight; ++b) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int j = 0; j < CPL; ++j) {
@@ -1201,10 +1202,10 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_rerank_kernel(
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int b = 0; b < 4; ++b) d[b] += __shfl_xor_sync(kFull, d[b], o);
+            for (int b = 0; b < kInFlight; ++b) d[b] += __shfl_xor_sync(kFull, d[b], o);
         }
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < kInFlight; ++b) {
             if (r[b] == 0xffffffffu) continue;
             const u64 key = make_key(d[b], r[b]);
             if (key < thr) {
