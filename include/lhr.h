@@ -270,26 +270,37 @@ lhr_status lhr_loc_mse(const double* yhat, const double* y, int32_t nw, const do
  * Serving runtime (no counterpart in the paper's own system, which localizes
  * one user at a time): continuous batching of requests from many concurrent
  * user streams. Each submitted frame is retrieved once (lhr_query's path for
- * `shortlist`) and its top k is cached in the stream's device ring; a request
- * for the stream's last m frames (Algorithm 2, §3.2) gathers the cached
- * candidates. A scheduler thread forms ticks of up to max_batch_frames queued
- * frames, oldest first, and launches each on one of n_lanes CUDA streams when
- * a lane is free and the tick's scratch fits mem_budget_bytes beside the ticks
- * in flight, so ticks overlap on the device. Results equal lhr_query /
- * lhr_aggregate_2d on the same frames: batching changes the schedule only.
+ * `shortlist` / `score`) and its top k is cached in the stream's device ring;
+ * a request for the stream's last m frames (Algorithm 2, §3.2) gathers the
+ * cached candidates. A scheduler thread forms ticks of up to max_batch_frames
+ * queued frames, oldest first, and launches each on one of n_lanes CUDA
+ * streams when a lane is free and the tick's scratch fits mem_budget_bytes
+ * beside the ticks in flight, so ticks overlap on the device. Results equal
+ * lhr_query / lhr_aggregate_2d on the same frames: batching changes the
+ * schedule only.
+ *
+ * Streams are admitted by memory: with ring_mem_bytes > 0 the server holds
+ * floor(ring_mem_bytes / ring bytes) device rings (ring bytes = ring_frames x
+ * (D x 4 + n_s x k x 12)); a stream must be opened (lhr_server_open_stream),
+ * which fails with LHR_ERR_OOM while every ring is held, and closing a stream
+ * (lhr_server_close_stream) returns its ring once its frames are done. With
+ * ring_mem_bytes = 0 every stream id is open from the start.
  */
 typedef struct lhr_server lhr_server;
 typedef struct {
-    int32_t n_streams;        /* user streams, ids 0 .. n_streams - 1 */
+    int32_t n_streams;        /* user stream ids 0 .. n_streams - 1 */
     int32_t max_window;       /* longest window m a request may ask for (>= 1) */
     int32_t ring_frames;      /* frames (and top-k lists) kept per stream on the device, > max_window */
     int32_t max_batch_frames; /* frames per tick, i.e. per retrieval launch (>= 1) */
     int32_t n_lanes;          /* CUDA streams the ticks rotate over (>= 2) */
     int32_t k;                /* top k per frame and subspace (1 .. 32) */
-    int32_t shortlist;        /* 0: exhaustive FP32 scan; S: coarse-to-fine (the db needs a coarse level) */
-    int32_t reserved;         /* 0 */
+    int32_t shortlist;        /* 0: exhaustive scan (or low-precision scores); S: coarse-to-fine (needs a coarse level) */
+    lhr_dtype score;          /* LHR_F32; LHR_BF16 / LHR_FP8_E4M3: tensor-core scores + FP32 re-rank (shortlist 0) */
     int64_t mem_budget_bytes; /* device scratch the ticks in flight may hold together (> 0) */
     lhr_agg_params agg;       /* Algorithm 2 parameters of every window */
+    int32_t rerank_width;     /* low-precision scores: rows re-ranked in FP32 per frame (k .. 128); else ignored */
+    int32_t reserved;         /* 0 */
+    int64_t ring_mem_bytes;   /* 0: every stream open, one ring each; > 0: device memory for rings, streams opened on demand */
 } lhr_server_config;
 
 typedef struct {
@@ -314,6 +325,16 @@ lhr_status lhr_server_submit(lhr_server* s, int32_t stream_id, const float* fram
  * for the first); *n_out receives the count. LHR_ERR_CUDA once a tick failed. */
 lhr_status lhr_server_poll(lhr_server* s, lhr_server_result* out, int32_t max_results, int32_t* n_out,
                            int32_t wait_ms);
+/* Admits a new stream when a ring is free: *stream_id receives its id (its frames
+ * start from none). LHR_ERR_OOM when every ring is held by an open stream;
+ * LHR_ERR_INVALID_ARG when the server opened every stream at creation. */
+lhr_status lhr_server_open_stream(lhr_server* s, int32_t* stream_id);
+/* Closes an open stream: no more submissions are accepted for it, and its ring
+ * returns to the server once its queued and in-flight frames are done. Waits up
+ * to timeout_ms for that; LHR_ERR_TIMEOUT means the frames are still running
+ * and the ring returns by itself when they finish. Results of its windows stay
+ * available to lhr_server_poll. */
+lhr_status lhr_server_close_stream(lhr_server* s, int32_t stream_id, int32_t timeout_ms);
 /* Waits until every submitted frame is processed (LHR_ERR_TIMEOUT after timeout_ms). */
 lhr_status lhr_server_drain(lhr_server* s, int32_t timeout_ms);
 /* Finishes queued work, stops the scheduler and frees everything. */

@@ -52,8 +52,9 @@ class AggParams(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("n_streams", ctypes.c_int32), ("max_window", ctypes.c_int32), ("ring_frames", ctypes.c_int32),
                 ("max_batch_frames", ctypes.c_int32), ("n_lanes", ctypes.c_int32), ("k", ctypes.c_int32),
-                ("shortlist", ctypes.c_int32), ("reserved", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64),
-                ("agg", AggParams)]
+                ("shortlist", ctypes.c_int32), ("score", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64),
+                ("agg", AggParams), ("rerank_width", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ring_mem_bytes", ctypes.c_int64)]
 
 
 class ServerResult(ctypes.Structure):
@@ -92,6 +93,8 @@ def _load():
         "lhr_server_submit": [P, I32, P, I32, I64],
         "lhr_server_poll": [P, ctypes.POINTER(ServerResult), I32, ctypes.POINTER(I32), I32],
         "lhr_server_drain": [P, I32],
+        "lhr_server_open_stream": [P, ctypes.POINTER(I32)],
+        "lhr_server_close_stream": [P, I32, I32],
         "lhr_server_destroy": [P],
         "lhr_profile_enable": [I32],
         "lhr_profile_read": [ctypes.c_char_p, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double), I32],
@@ -470,11 +473,13 @@ class Server:
     def __init__(self, db: Database, n_streams: int, max_window: int, k: int, shortlist: int = 0,
                  ring_frames: int | None = None, max_batch_frames: int = 64, n_lanes: int = 2,
                  mem_budget_bytes: int = 1 << 30, mode: str = "tile", top_c: int = 10, radius_m: float = 3.0,
-                 toler_pct: int = 20, tau: float = 1.0):
+                 toler_pct: int = 20, tau: float = 1.0, score: str = "f32", rerank_width: int = 64,
+                 ring_mem_bytes: int = 0):
         self.db = db
         ring = ring_frames if ring_frames is not None else 2 * max_window + max_batch_frames
-        cfg = ServerConfig(n_streams, max_window, ring, max_batch_frames, n_lanes, k, shortlist, 0,
-                           mem_budget_bytes, agg_params(mode, top_c, radius_m, toler_pct, tau))
+        cfg = ServerConfig(n_streams, max_window, ring, max_batch_frames, n_lanes, k, shortlist, _SCORE[score],
+                           mem_budget_bytes, agg_params(mode, top_c, radius_m, toler_pct, tau), rerank_width, 0,
+                           ring_mem_bytes)
         h = ctypes.c_void_p()
         _check(_lib.lhr_server_create(db.handle, ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
@@ -494,6 +499,16 @@ class Server:
 
     def drain(self, timeout_ms: int = 60000):
         _check(_lib.lhr_server_drain(self._h, timeout_ms))
+
+    def open_stream(self) -> int:
+        """Admits a new stream if a device ring is free (LhrError LHR_ERR_OOM otherwise)."""
+        sid = ctypes.c_int32()
+        _check(_lib.lhr_server_open_stream(self._h, ctypes.byref(sid)))
+        return sid.value
+
+    def close_stream(self, stream_id: int, timeout_ms: int = 60000):
+        """Closes a stream; its ring returns once its frames are done."""
+        _check(_lib.lhr_server_close_stream(self._h, stream_id, timeout_ms))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -521,6 +536,14 @@ def lhr_server_poll(server: Server, wait_ms: int = 0, max_results: int = 4096):
 
 def lhr_server_drain(server: Server, timeout_ms: int = 60000):
     server.drain(timeout_ms)
+
+
+def lhr_server_open_stream(server: Server) -> int:
+    return server.open_stream()
+
+
+def lhr_server_close_stream(server: Server, stream_id: int, timeout_ms: int = 60000):
+    server.close_stream(stream_id, timeout_ms)
 
 
 def lhr_server_destroy(server: Server):

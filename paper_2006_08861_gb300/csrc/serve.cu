@@ -125,10 +125,16 @@ struct lhr_server {
     lhr_server_config cfg{};
     lhr_query_params qp{};
     int D = 0, kc = 0, R = 0;
+    int n_rings = 0;          // device rings (frames + cached top-k lists), one per open stream
+    bool on_demand = false;   // streams are opened and closed by the caller (rings admitted by memory)
     float* ring_frames = nullptr;
     int64_t* cache_idx = nullptr;
     float* cache_dist = nullptr;
-    std::vector<std::vector<lhr::SlotInfo>> slots;  // [stream][R]
+    std::vector<std::vector<lhr::SlotInfo>> slots;  // [ring][R]
+    std::vector<int32_t> ring_of;                   // ring of each stream id, -1 = none
+    std::vector<int32_t> state;                     // per stream id: 0 closed, 1 open, 2 closing
+    std::vector<int32_t> free_rings;
+    std::vector<int64_t> queued;                    // frames per stream waiting in the submission queue
     std::vector<int64_t> next_seq;                  // frames submitted per stream
     std::vector<int32_t> in_flight;                 // frames per stream in busy lanes
     std::vector<lhr::Lane> lanes;
@@ -150,10 +156,21 @@ namespace {
 
 size_t tick_scratch(const lhr_server* S, int nb) {
     const lhr_db* db = S->db;
+    if (S->qp.score != LHR_F32) return lowp_scratch_bytes(db, nb, S->qp.score == LHR_FP8_E4M3, S->qp.rerank_width);
     if (S->qp.shortlist > 0)
         return hier_fused_eligible(db, nb, S->qp.shortlist) ? hier_scratch_bytes(db, nb)
                                                             : coarse_scratch_bytes(db, nb, S->qp.shortlist);
     return scan_scratch_bytes(db, nb, S->qp.k, true);
+}
+
+// A closing stream's ring goes back to the free list once none of its frames is
+// queued or in flight (caller holds S->mu).
+void maybe_release(lhr_server* S, int st) {
+    if (S->state[st] == 2 && S->queued[st] == 0 && S->in_flight[st] == 0) {
+        S->free_rings.push_back(S->ring_of[st]);
+        S->ring_of[st] = -1;
+        S->state[st] = 0;
+    }
 }
 
 // Lanes whose tick finished: their windows become results.
@@ -181,6 +198,7 @@ void finish_lanes(lhr_server* S, bool block) {
             S->doneq.push_back(r);
         }
         for (int32_t st : L.frame_streams) S->in_flight[st]--;
+        for (int32_t st : L.frame_streams) maybe_release(S, st);
         S->completed += (int64_t)L.frame_streams.size();
         S->reserved -= L.reserved;
         L.busy = false;
@@ -206,12 +224,13 @@ bool launch_tick(lhr_server* S, int li) {
     {
         std::lock_guard<std::mutex> lk(S->mu);
         // a stream may not hold more frames in flight than its ring can keep
-        // beside the max_window frames its windows read
-        std::vector<int32_t> add(S->cfg.n_streams, 0);
+        // beside the max_window frames its windows read; a taken frame counts
+        // as in flight at once, so its stream's ring stays while it is used
         while (!S->subq.empty() && (int)take.size() < S->cfg.max_batch_frames) {
             const Submission& sb = S->subq.front();
-            if (S->in_flight[sb.stream] + add[sb.stream] + 1 > R - maxm) break;
-            add[sb.stream]++;
+            if (S->in_flight[sb.stream] + 1 > R - maxm) break;
+            S->in_flight[sb.stream]++;
+            S->queued[sb.stream]--;
             take.push_back(std::move(S->subq.front()));
             S->subq.pop_front();
         }
@@ -228,18 +247,19 @@ bool launch_tick(lhr_server* S, int li) {
     for (int b = 0; b < nb; ++b) {
         Submission& sb = take[b];
         const int st = sb.stream;
+        const int rg = S->ring_of[st];  // open or closing: the ring stays until its frames are done
         const int64_t seq = S->next_seq[st]++;
         const int slot = (int)(seq % R);
         std::memcpy(L.h_frames + (size_t)b * D, sb.frame.data(), (size_t)D * sizeof(float));
-        L.h_map[b] = st * R + slot;
-        S->slots[st][slot] = SlotInfo{seq, li, tick};
+        L.h_map[b] = rg * R + slot;
+        S->slots[rg][slot] = SlotInfo{seq, li, tick};
         L.frame_streams.push_back(st);
         if (sb.m > 0) {
             const int m = (int)std::min<int64_t>(sb.m, seq + 1);
             for (int64_t f = seq - m + 1; f <= seq; ++f) {
                 const int fs = (int)(f % R);
-                const SlotInfo& si = S->slots[st][fs];
-                L.h_wslots[wframes++] = st * R + fs;
+                const SlotInfo& si = S->slots[rg][fs];
+                L.h_wslots[wframes++] = rg * R + fs;
                 if (si.tick != tick) deps.emplace_back(si.lane, si.tick);
             }
             L.windows.push_back(WindowReq{sb.request_id, st, m, sb.t});
@@ -247,7 +267,6 @@ bool launch_tick(lhr_server* S, int li) {
             L.h_woff[nwin] = wframes * kc;
         }
     }
-    for (int32_t st : L.frame_streams) S->in_flight[st]++;
     L.reserved = tick_scratch(S, nb);
     {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -374,7 +393,9 @@ lhr_status lhr_server_create(const lhr_db* db, const lhr_server_config* cfg, lhr
     if (cfg->ring_frames < cfg->max_window + 1)
         return fail(LHR_ERR_INVALID_ARG, "ring_frames must exceed max_window");
     if (cfg->mem_budget_bytes <= 0) return fail(LHR_ERR_INVALID_ARG, "mem_budget_bytes must be > 0");
-    lhr_query_params qp{cfg->k, cfg->shortlist, LHR_F32, 0};
+    if (cfg->reserved != 0 || cfg->ring_mem_bytes < 0)
+        return fail(LHR_ERR_INVALID_ARG, "reserved must be 0 and ring_mem_bytes >= 0");
+    lhr_query_params qp{cfg->k, cfg->shortlist, cfg->score, cfg->score == LHR_F32 ? 0 : cfg->rerank_width};
     lhr_status st = check_query_params(db, &qp);
     if (st != LHR_OK) return st;
     if ((st = check_agg_params(&cfg->agg)) != LHR_OK) return st;
@@ -391,13 +412,33 @@ lhr_status lhr_server_create(const lhr_db* db, const lhr_server_config* cfg, lhr
     S->kc = db->n_sub * cfg->k;
     S->R = cfg->ring_frames;
     const int D = S->D, kc = S->kc, R = S->R, NB = cfg->max_batch_frames;
-    const size_t nslot = (size_t)cfg->n_streams * R;
+    const size_t ring_bytes = (size_t)R * ((size_t)D * sizeof(float) + (size_t)kc * (sizeof(int64_t) + sizeof(float)));
+    S->on_demand = cfg->ring_mem_bytes > 0;
+    S->n_rings = S->on_demand ? (int)std::min<int64_t>(cfg->n_streams, cfg->ring_mem_bytes / (int64_t)ring_bytes)
+                              : cfg->n_streams;
+    if (S->n_rings < 1) {
+        delete S;
+        if (prev >= 0) cudaSetDevice(prev);
+        return fail(LHR_ERR_INVALID_ARG, "ring_mem_bytes holds no ring (ring_frames x (D x 4 + n_s x k x 12) bytes)");
+    }
+    const size_t nslot = (size_t)S->n_rings * R;
     cudaError_t e = cudaMalloc(&S->ring_frames, nslot * D * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&S->cache_idx, nslot * kc * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMalloc(&S->cache_dist, nslot * kc * sizeof(float));
-    S->slots.assign(cfg->n_streams, std::vector<SlotInfo>(R));
+    S->slots.assign(S->n_rings, std::vector<SlotInfo>(R));
     S->next_seq.assign(cfg->n_streams, 0);
     S->in_flight.assign(cfg->n_streams, 0);
+    S->queued.assign(cfg->n_streams, 0);
+    S->ring_of.assign(cfg->n_streams, -1);
+    S->state.assign(cfg->n_streams, 0);
+    if (S->on_demand) {
+        for (int r = S->n_rings - 1; r >= 0; --r) S->free_rings.push_back(r);
+    } else {
+        for (int st = 0; st < cfg->n_streams; ++st) {
+            S->ring_of[st] = st;
+            S->state[st] = 1;
+        }
+    }
     S->lanes.resize(cfg->n_lanes);
     for (Lane& L : S->lanes) {
         if (e != cudaSuccess) break;
@@ -447,6 +488,8 @@ lhr_status lhr_server_submit(lhr_server* S, int32_t stream_id, const float* fram
         std::lock_guard<std::mutex> lk(S->mu);
         if (!S->error.empty()) return fail(LHR_ERR_CUDA, S->error);
         if (S->stop) return fail(LHR_ERR_INVALID_ARG, "server is stopping");
+        if (S->state[stream_id] != 1) return fail(LHR_ERR_INVALID_ARG, "stream is not open");
+        S->queued[stream_id]++;
         S->subq.push_back(std::move(sb));
         S->submitted++;
     }
@@ -468,6 +511,41 @@ lhr_status lhr_server_poll(lhr_server* S, lhr_server_result* out, int32_t max_re
     }
     *n_out = n;
     if (!S->error.empty()) return fail(LHR_ERR_CUDA, S->error);
+    return LHR_OK;
+}
+
+lhr_status lhr_server_open_stream(lhr_server* S, int32_t* stream_id) {
+    if (!S || !stream_id) return fail(LHR_ERR_INVALID_ARG, "server and stream_id must be non-NULL");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (!S->on_demand) return fail(LHR_ERR_INVALID_ARG, "every stream was opened at creation (ring_mem_bytes = 0)");
+    if (!S->error.empty()) return fail(LHR_ERR_CUDA, S->error);
+    if (S->free_rings.empty()) return fail(LHR_ERR_OOM, "admission refused: every ring is held by an open stream");
+    int id = -1;
+    for (int st = 0; st < S->cfg.n_streams && id < 0; ++st)
+        if (S->state[st] == 0) id = st;
+    if (id < 0) return fail(LHR_ERR_OOM, "admission refused: every stream id is in use");
+    const int rg = S->free_rings.back();
+    S->free_rings.pop_back();
+    S->ring_of[id] = rg;
+    S->state[id] = 1;
+    S->next_seq[id] = 0;
+    for (SlotInfo& si : S->slots[rg]) si = SlotInfo{};
+    *stream_id = id;
+    return LHR_OK;
+}
+
+lhr_status lhr_server_close_stream(lhr_server* S, int32_t stream_id, int32_t timeout_ms) {
+    if (!S) return fail(LHR_ERR_INVALID_ARG, "server is NULL");
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (stream_id < 0 || stream_id >= S->cfg.n_streams || S->state[stream_id] == 0)
+        return fail(LHR_ERR_INVALID_ARG, "stream is not open");
+    if (!S->on_demand) return fail(LHR_ERR_INVALID_ARG, "every stream was opened at creation (ring_mem_bytes = 0)");
+    S->state[stream_id] = 2;  // closing: no more submissions; the ring returns when its frames are done
+    maybe_release(S, stream_id);
+    const bool done = S->cv_done.wait_for(lk, std::chrono::milliseconds(std::max(timeout_ms, 0)),
+                                          [&] { return S->state[stream_id] == 0 || !S->error.empty(); });
+    if (!S->error.empty()) return fail(LHR_ERR_CUDA, S->error);
+    if (!done) return fail(LHR_ERR_TIMEOUT, "stream still has frames in flight (its ring returns when they finish)");
     return LHR_OK;
 }
 
