@@ -108,6 +108,26 @@ def hierarchical_topk(Q, X, coarse_dim: int, shortlist: int, k: int):
     return idx, dist, short
 
 
+def hierarchical_topk_subspaces(Q, X, coarse_dim: int, shortlist: int, k: int, subspace, n_subspaces=None):
+    """Coarse-to-fine top-k of every frame in every subspace (§3.1: each
+    subspace is searched on its own): ``hierarchical_topk`` over the rows of
+    subspace s alone, its rows reported in the database's numbering.
+    Returns ``idx`` int64 (nq, n_s, k) and ``dist`` float64 (nq, n_s, k).
+    """
+    Q = np.atleast_2d(np.asarray(Q))
+    X = np.asarray(X)
+    subspace = np.asarray(subspace)
+    ns = int(subspace.max()) + 1 if n_subspaces is None else int(n_subspaces)
+    idx = np.empty((Q.shape[0], ns, k), dtype=np.int64)
+    dist = np.empty((Q.shape[0], ns, k), dtype=np.float64)
+    for s in range(ns):
+        rows = np.nonzero(subspace == s)[0].astype(np.int64)
+        i_s, d_s, _ = hierarchical_topk(Q, X[rows], coarse_dim, shortlist, k)
+        idx[:, s] = np.where(i_s >= 0, rows[np.maximum(i_s, 0)], -1)
+        dist[:, s] = d_s
+    return idx, dist
+
+
 def window_candidates(frame_idx: np.ndarray, offsets: np.ndarray):
     """Candidates of each window: the per-frame lists of its frames, concatenated.
 

@@ -157,7 +157,9 @@ lhr_status check_query_params(const lhr_db* db, const lhr_query_params* p) {
         if (p->shortlist < p->k || p->shortlist > 4096)
             return fail(LHR_ERR_INVALID_ARG, "shortlist must be in [k, 4096]");
         if (!db->Xc) return fail(LHR_ERR_INVALID_ARG, "database was built without a coarse level (coarse_dim = 0)");
-        if (db->n_sub != 1) return fail(LHR_ERR_INVALID_ARG, "coarse-to-fine needs a single-subspace database");
+        for (int64_t rows : db->sub_rows_h)
+            if (rows < p->shortlist)
+                return fail(LHR_ERR_INVALID_ARG, "shortlist must not exceed the rows of any subspace");
     }
     if (p->score != LHR_F32) {
         if (p->rerank_width < p->k || p->rerank_width > 128)
@@ -180,6 +182,35 @@ lhr_status run_retrieval(const lhr_db* db, const float* q, int nq, const lhr_que
         if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
         e = launch_lowp(db, q, nq, fp8, p->rerank_width, p->k, idx, dist, scr.ptr, s);
         if (e != cudaSuccess) return cuda_fail(e, "low-precision launch");
+    } else if (p->shortlist > 0 && db->n_sub > 1) {
+        // subspaces are searched independently (§3.1): the coarse-to-fine path over each
+        // subspace's contiguous internal rows, its rows then mapped into slot s of the output
+        int64_t off = 0;
+        for (int s2 = 0; s2 < db->n_sub; ++s2) {
+            lhr_db view = *db;
+            const int64_t rows = db->sub_rows_h[s2];
+            view.X = db->X + off * db->dim;
+            view.Xc = db->Xc + off * db->coarse_dim;
+            view.xnorm = db->xnorm + off;
+            view.n = rows;
+            view.n_sub = 1;
+            view.perm = view.iperm = nullptr;
+            const bool fused = hier_fused_eligible(&view, nq, p->shortlist);
+            const size_t tbytes = ((size_t)nq * p->k * (sizeof(int64_t) + sizeof(float)) + 255) / 256 * 256;
+            const size_t pbytes = fused ? hier_scratch_bytes(&view, nq) : coarse_scratch_bytes(&view, nq, p->shortlist);
+            e = scr.alloc(tbytes + pbytes, s);
+            if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+            int64_t* tidx = reinterpret_cast<int64_t*>(scr.ptr);
+            float* tdist = reinterpret_cast<float*>(tidx + (size_t)nq * p->k);
+            void* pscr = reinterpret_cast<unsigned char*>(scr.ptr) + tbytes;
+            e = fused ? launch_hier_fused(&view, q, nq, p->shortlist, p->k, tidx, tdist, nullptr, pscr, s)
+                      : launch_coarse(&view, q, nq, p->shortlist, p->k, tidx, tdist, pscr, s);
+            if (e != cudaSuccess) return cuda_fail(e, "coarse-to-fine launch");
+            e = launch_subspace_remap(tidx, tdist, nq, p->k, db->n_sub, s2, off, db->perm, idx, dist, s);
+            if (e != cudaSuccess) return cuda_fail(e, "subspace remap launch");
+            scr.release();
+            off += rows;
+        }
     } else if (p->shortlist > 0 && hier_fused_eligible(db, nq, p->shortlist)) {
         e = scr.alloc(hier_scratch_bytes(db, nq), s);
         if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");

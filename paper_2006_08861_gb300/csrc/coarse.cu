@@ -358,6 +358,29 @@ CoarseLayout layout(const lhr_db* db, int nq) {
 
 size_t coarse_scratch_bytes(const lhr_db* db, int nq, int /*shortlist*/) { return layout(db, nq).total; }
 
+namespace {
+// One subspace's [nq][k] result (rows relative to the subspace's first internal
+// row `off`) into slot s of the [nq][n_sub][k] output, in the caller's rows.
+__global__ void subspace_remap_kernel(const int64_t* __restrict__ tidx, const float* __restrict__ tdist, int nq, int k,
+                                      int n_sub, int s, int64_t off, const int32_t* __restrict__ perm,
+                                      int64_t* __restrict__ idx, float* __restrict__ dist) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq * k) return;
+    const int f = i / k, j = i % k;
+    const int64_t r = tidx[i];
+    const size_t o = ((size_t)f * n_sub + s) * k + j;
+    idx[o] = r < 0 ? -1 : (perm != nullptr ? (int64_t)perm[off + r] : off + r);
+    dist[o] = tdist[i];
+}
+}  // namespace
+
+cudaError_t launch_subspace_remap(const int64_t* tidx, const float* tdist, int nq, int k, int n_sub, int s, int64_t off,
+                                  const int32_t* perm, int64_t* idx, float* dist, cudaStream_t stream) {
+    const int n = nq * k;
+    subspace_remap_kernel<<<(n + 255) / 256, 256, 0, stream>>>(tidx, tdist, nq, k, n_sub, s, off, perm, idx, dist);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_coarse(const lhr_db* db, const float* q, int nq, int shortlist, int k, int64_t* idx, float* dist,
                           void* scratch, cudaStream_t stream) {
     const CoarseLayout Lo = layout(db, nq);

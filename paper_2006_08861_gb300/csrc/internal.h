@@ -136,6 +136,9 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
 size_t coarse_scratch_bytes(const lhr_db* db, int nq, int shortlist);
 cudaError_t launch_coarse(const lhr_db* db, const float* q, int nq, int shortlist, int k, int64_t* idx,
                           float* dist, void* scratch, cudaStream_t stream);
+// One subspace's [nq][k] result into slot s of [nq][n_sub][k], rows mapped to the caller's.
+cudaError_t launch_subspace_remap(const int64_t* tidx, const float* tdist, int nq, int k, int n_sub, int s, int64_t off,
+                                  const int32_t* perm, int64_t* idx, float* dist, cudaStream_t stream);
 
 // Algorithm 2 (aggregate.cu). Candidates of window w: rows idx[c] for c in
 // [cand_begin(w), cand_end(w)) where the range is cand_offsets[w]..[w+1]

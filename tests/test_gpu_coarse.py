@@ -146,3 +146,51 @@ def test_hierarchical_configuration_windows(lhr):
     err = np.hypot(*(xy.cpu().numpy() - win.true_xy).T)
     assert np.mean(err < 3.0) >= 0.75
     h.close()
+
+
+def test_subspaces_coarse_to_fine_papers_experiment_shape(lhr):
+    # §4's experiment shape through the coarse-to-fine path: P = 5 paths
+    # (subspaces, interleaved in the database so rows are permuted), windows of
+    # M = 11 frames, top N = 15 per frame and path: 825 candidates per window,
+    # then Algorithm 2. Per frame and path against the FP64 oracle (the
+    # coarse-to-fine form run over each subspace alone); positions against
+    # Algorithm 2 of the oracle on the same candidates.
+    n, dim, dc, S, k, P, M = 30_000, 128, 32, 256, 15, 5, 11
+    db = synth.make_database(n, dim, seed=81)
+    corridor = np.floor(db.arc / 103.0).astype(np.int64)          # 100 m corridors + 3 m connectors
+    sub = (corridor % P).astype(np.int32)
+    win = synth.make_windows(db, 3, M, seed=82)
+    h = lhr.lhr_build_db(db.feats, db.xy, subspace=sub, coarse_dim=dc)
+    assert h.n_subspaces == P
+    frames = torch.from_numpy(win.frames).cuda()
+    offs = torch.from_numpy(win.offsets).cuda()
+    idx, dist, xy, st = lhr.lhr_query_window(h, frames, offs, k, shortlist=S, mode="tile")
+    torch.cuda.synchronize()
+    assert lhr.lhr_db_error(h) == 0
+    gi, gd = idx.cpu().numpy(), dist.cpu().numpy()
+    assert gi.shape == (win.frames.shape[0], P, k) and (gi >= 0).all()
+    o_idx, o_dist = oret.hierarchical_topk_subspaces(win.frames, db.feats, dc, S, k + 1, sub, P)
+    strict = 0
+    for s in range(P):
+        rows = np.nonzero(sub == s)[0]
+        Xs = db.feats[rows]
+        pos = {int(r): i for i, r in enumerate(rows)}
+        for f in range(win.frames.shape[0]):
+            if _shortlist_separated(win.frames[f], Xs, dc, S):
+                check_list(win.frames[f], db.feats, gi[f, s], gd[f, s], o_idx[f, s], o_dist[f, s], k, rows=rows,
+                           where=f"f{f} s{s}")
+                strict += 1
+            else:
+                assert np.isin(gi[f, s], rows).all()
+                check_hier_ambiguous(win.frames[f], Xs, dc, S, np.array([pos[int(r)] for r in gi[f, s]]), gd[f, s],
+                                     k, where=f"f{f} s{s}")
+    assert strict >= (win.frames.shape[0] * P) // 2, strict
+    cands = oret.window_candidates(gi, win.offsets)
+    assert all(c.size == 825 for c in cands)   # N x M x P of §4
+    o_xy, o_st = oagg.aggregate_windows(cands, db.xy, mode="tile")
+    assert np.array_equal(st.cpu().numpy(), o_st)
+    assert np.max(np.abs(xy.cpu().numpy() - o_xy)) <= XY_ATOL
+    # the shortlist may not exceed a subspace's rows
+    with pytest.raises(lhr.LhrError):
+        lhr.lhr_query_window(h, frames, offs, k, shortlist=int(np.bincount(sub).min()) + 1)
+    h.close()

@@ -133,6 +133,35 @@ def test_hierarchical_uses_the_prefix_and_the_shortlist():
     assert ex_i[0, 0].tolist() == [1] and ex_d[0, 0].tolist() == [50.0]
 
 
+def test_hierarchical_per_subspace_with_full_shortlists_equals_exhaustive_per_subspace():
+    # shortlists as large as the largest subspace reduce the coarse-to-fine form
+    # to exhaustive search, subspace by subspace (the exhaustive per-subspace
+    # oracle is pinned above against each subspace alone)
+    rng = np.random.default_rng(16)
+    X = rng.standard_normal((500, 24)).astype(np.float32)
+    sub = rng.integers(0, 4, 500).astype(np.int32)
+    Q = rng.standard_normal((6, 24)).astype(np.float32)
+    big = int(np.bincount(sub).max())
+    h_i, h_d = retrieval.hierarchical_topk_subspaces(Q, X, 8, big, 7, sub, 4)
+    ex_i, ex_d = retrieval.exhaustive_topk(Q, X, 7, subspace=sub, n_subspaces=4)
+    assert (h_i == ex_i).all() and np.array_equal(h_d, ex_d)
+    # and every returned row lies in its subspace
+    assert all((sub[h_i[:, s]] == s).all() for s in range(4))
+
+
+def test_hierarchical_per_subspace_uses_each_subspaces_own_shortlist():
+    # subspace 0 holds rows 0, 2; subspace 1 holds rows 1, 3. With S = 1 the
+    # prefix picks row 2 in subspace 0 (prefix exact, tail far) and row 1 in
+    # subspace 1, although rows 0 and 3 are nearer over the whole feature.
+    X = np.array([[4, 4, 0, 0], [0, 1, 9, 9], [0, 0, 9, 9], [3, 3, 0, 0]], dtype=np.float32)
+    sub = np.array([0, 1, 0, 1], dtype=np.int32)
+    q = np.zeros((1, 4), dtype=np.float32)
+    h_i, h_d = retrieval.hierarchical_topk_subspaces(q, X, 2, 1, 1, sub)
+    assert h_i.tolist() == [[[2], [1]]] and h_d.tolist() == [[[162.0], [163.0]]]
+    ex_i, ex_d = retrieval.exhaustive_topk(q, X, 1, subspace=sub)
+    assert ex_i.tolist() == [[[0], [3]]] and ex_d.tolist() == [[[32.0], [18.0]]]
+
+
 # ---------------------------------------------------------------- O4 windows
 def test_candidate_count_of_the_papers_experiment():
     # §4: N = 15 candidates per frame, M = 11 frames, P = 5 paths -> 825.
