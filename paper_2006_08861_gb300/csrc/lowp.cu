@@ -12,46 +12,41 @@
 // Keys are (orderable score bits << 32 | row); the shortlist is the W
 // smallest keys, exactly.
 //
-// Both tensor-core kernels are warp-specialised, 10 warps, one CTA per
-// (128-query block, database chunk):
-//   warp 0  producer: TMA (cp.async.bulk.tensor.2d, 128-byte swizzle) of the
-//           block's 128 query codes once, then the chunk's 128-row tiles, one
-//           128-byte K slice per stage, through a mbarrier ring as deep as
-//           shared memory allows (7-8 stages).
-//   warp 1  TMEM allocator and MMA issuer: tcgen05.mma (M = N = 128, K = 16
-//           BF16 / 32 FP8 per instruction) into four 128-column FP32
-//           accumulators in TMEM, in turn per tile (the tensor core runs up to
-//           three tiles ahead of the epilogue); tcgen05.commit frees ring
-//           stages and publishes accumulators.
-//   warps 2-9 epilogue: two warps per TMEM lane quadrant, each reading half of
-//           a tile's 128 columns with two 32-column tcgen05.ld.
-// tc_main_kernel (the main pass): the database tile is the MMA's A operand, so
-//   a TMEM lane -- an epilogue thread -- is a database row and a column is a
-//   query. The row's (m s_j, n_j) sit in two registers (loaded from global
-//   memory a tile ahead) and the thread's 64 queries' thresholds tau_q in 64
-//   more, so scoring reads no shared memory: per pair of columns one packed
-//   fma and one packed add (score - tau_q), then a minimum over 32 columns.
-//   A row with a key <= tau_q (rare; a warp ballot) is moved across the warp
-//   with shuffles so that lane l checks the query it owns (column l), and
-//   stages the key in shared memory; eight staged keys of a query go to its
-//   candidate buffer with one atomic. tau_q is the 8th smallest sample key of
-//   the query (pilot pass, then tau_kernel), so at least 8 keys, about 8 x 64
-//   in expectation, qualify.
-//   Under the tensor core's and TMA's shared-memory traffic a shared or local
-//   load in the epilogue waits about a microsecond; the scoring loop issues
-//   none, and the rare path is kept small (it runs from the instruction cache
-//   beside the scoring loop).
-// tc_kernel (pilot and fallback passes): the query block is the A operand, a
-//   thread is a query and reads each column's (s_j, n_j) from shared memory
-//   (a 1-D bulk copy per tile):
-//     pilot  over every 64th database row (a copy built with the database):
-//            the thread keeps its query's 8 smallest sample keys in a static
-//            register network;
-//     full   (fallback, and the only pass for databases too small to sample):
-//            the thread keeps its query's exact top W of the chunk in local
-//            memory, filled through a 16-entry shared-memory survivor
-//            buffer. When run after a main pass it exits at once unless a
-//            query of its block collected fewer than W or more than kCap keys.
+// Per batch of queries:
+//   query_amax_kernel + quantize_queries_kernel  the batch's power-of-two scale and the codes
+//   tc_main_kernel<kPilot = true>   pilot over every 64th database row (a copy built with the
+//                                   database): per query, the 8 smallest 32-row bucket minima
+//   tau_kernel                      tau_q = the 8th smallest of them (at least 8 sample rows score
+//                                   at most tau_q; about 8 x 64 database rows in expectation)
+//   sort_queries_kernel             queries in ascending tau order: sorted codes, the query at each
+//                                   position, and per 32 positions the largest tau (group bound)
+//   tc_main_kernel<kPilot = false>  main pass: every key <= tau_q into query q's candidate buffer
+//   tc_kernel (full)                fallback: exact per-chunk top W of a 128-query block whose
+//                                   candidate count fell outside [W, kCap]; exits at once otherwise
+//   merge_rerank_kernel             the W smallest candidates, re-scored in FP32 (direct form), top k
+//
+// tc_main_kernel: warp-specialised, 18 warps, one CTA per (256-query block, database chunk), one
+// CTA per SM:
+//   warp 0  producer: TMA (cp.async.bulk.tensor.2d, 128-byte swizzle) of the block's 256 query
+//           codes once, then the chunk's 128-row tiles, one 128-byte K slice per stage, through a
+//           mbarrier ring as deep as shared memory allows.
+//   warp 1  TMEM allocator and MMA issuer: tcgen05.mma M = 128 rows (A, the database tile) x
+//           N = 256 queries (B, resident) x K = 32 FP8 / 16 BF16 into two 256-column FP32
+//           accumulators (all of TMEM), in turn per tile; tcgen05.commit frees ring stages and
+//           publishes accumulators.
+//   warps 2-17 epilogue: four warps per TMEM lane quadrant, a thread = a database row and one
+//           64-column quarter of the queries, read as two 32-column groups. A group's smallest
+//           score for the row is fma(m s_j, max dot, n_j) (m s_j <= 0; fma is monotone), compared
+//           with the group's bound. Rows that pass go through the warp's shared-memory transpose
+//           buffer so that lane l checks column l -- the query it owns -- exactly, and stages a
+//           qualifying key; a full stage goes to the query's candidate buffer with one atomic.
+//           In pilot mode the epilogue instead takes, per group and 32-row bucket, the column
+//           minima (a butterfly over the warp) and keeps each query's 8 smallest.
+// tc_kernel (fallback pass): 10 warps, one CTA per (128-query block, database chunk); the query
+//   block is the A operand, a thread is a query and reads each column's (s_j, n_j) from shared
+//   memory (a 1-D bulk copy per tile) and keeps its query's exact top W of the chunk in local
+//   memory, filled through a 16-entry shared-memory survivor buffer. It is the only pass for
+//   databases too small to sample.
 // merge_rerank_kernel, one warp per query: the shortlist is the W smallest
 //   keys of the query's candidate buffer (for W <= 64 a running 64 smallest in
 //   registers over 64-key chunks; else, and after the full pass, a sort of the
@@ -206,7 +201,7 @@ __device__ __forceinline__ u64 score_key(float t, uint32_t row) {
 }
 
 
-enum { kModePilot = 0, kModeFull = 2 };
+enum { kModeFull = 2 };
 constexpr int kPilotR = 8;        // sample keys kept per query by the pilot pass
 constexpr int kCap = 2048;        // candidate keys kept per query by the main pass
 constexpr int kMergeWarps = 4;
@@ -239,6 +234,8 @@ struct MainParams {
     unsigned* cnt;        // keys <= tau seen per query
     int nq;
     int cs;               // CTAs per cluster along the query blocks (1, 2 or 4): they share each database tile
+    u64* pilot_out;       // pilot mode: [query][lists][kPilotR] keys of 32-row bucket minima
+    int pilot_lists;      // pilot mode: lists per query (chunks x 4 lane quadrants)
     int* err;
 };
 
@@ -292,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     extern __shared__ unsigned char smem_raw[];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int chunk = blockIdx.x, qblock = blockIdx.y;
-    if (MODE == kModeFull && p.cnt != nullptr) {
+    if (p.cnt != nullptr) {
         // fallback after a main pass: run only if a query of this block needs it
         bool need = false;
         if (threadIdx.x < kTile) {
@@ -312,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int stages = p.stages;
     float2* sSN = reinterpret_cast<float2*>(sB + (size_t)stages * kSliceTile);  // kSnSlots x 128
     u64* sBuf = reinterpret_cast<u64*>(sSN + kSnSlots * kTile);  // full: kBuf x kEpiThreads (slot-major)
-    u64* bars = MODE == kModeFull ? sBuf + kBuf * kEpiThreads : sBuf;
+    u64* bars = sBuf + kBuf * kEpiThreads;
     u64* full = bars;
     u64* empty = full + kMaxStages;
     u64* a_full = empty + kMaxStages;
@@ -456,13 +453,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t qi = (int64_t)qblock * kTile + qrow;
         const bool qvalid = qi < p.nq;
         const float m = qvalid ? __ldg(p.qs + 1) : 0.f;
-        // pilot: the sample keys; full: exact top W
-        u64 net[kPilotR];
-#pragma unroll
-        for (int i = 0; i < kPilotR; ++i) net[i] = kKeyEmpty;
-        u64 list[MODE == kModeFull ? WMAX : 1];
-        if (MODE == kModeFull)
-            for (int i = 0; i < WMAX; ++i) list[i] = kKeyEmpty;
+        // exact top W of the chunk
+        u64 list[WMAX];
+        for (int i = 0; i < WMAX; ++i) list[i] = kKeyEmpty;
         u64 thr = kKeyEmpty;
         int nb = 0;
         u64* buf = sBuf + ew * 32 + lane;
@@ -490,17 +483,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int col = c0 + j;
                         const float2 sn = snt[col];
                         const float score = fmaf(m * sn.x, __uint_as_float(v[j]), sn.y);
-                        if (MODE == kModePilot) {
-                            if (col < nr) net_insert(net, score_key(score, (uint32_t)(r + col)));
-                        } else {
-                            const u64 key = score_key(score, (uint32_t)(r + col));
-                            if (col < nr && key < thr) {
-                                buf[nb * kEpiThreads] = key;
-                                if (++nb == kBuf) {
-                                    flush_buffer<WMAX>(list, buf, kEpiThreads, nb, p.W);
-                                    nb = 0;
-                                    thr = list[p.W - 1];
-                                }
+                        const u64 key = score_key(score, (uint32_t)(r + col));
+                        if (col < nr && key < thr) {
+                            buf[nb * kEpiThreads] = key;
+                            if (++nb == kBuf) {
+                                flush_buffer<WMAX>(list, buf, kEpiThreads, nb, p.W);
+                                nb = 0;
+                                thr = list[p.W - 1];
                             }
                         }
                     }
@@ -523,17 +512,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&sn_empty[sl]);
         }
-        if (MODE == kModePilot && qvalid) {
-            u64* dst = p.partial + ((size_t)qi * p.nchunks * kHalves + lchunk) * kPilotR;
-#pragma unroll
-            for (int i = 0; i < kPilotR; ++i) dst[i] = net[i];
-        }
-        if (MODE == kModeFull) {
-            if (nb) flush_buffer<WMAX>(list, buf, kEpiThreads, nb, p.W);
-            if (qvalid) {
-                u64* dst = p.partial + ((size_t)qi * p.nchunks * kHalves + lchunk) * p.W;
-                for (int i = 0; i < p.W; ++i) dst[i] = list[i];
-            }
+        if (nb) flush_buffer<WMAX>(list, buf, kEpiThreads, nb, p.W);
+        if (qvalid) {
+            u64* dst = p.partial + ((size_t)qi * p.nchunks * kHalves + lchunk) * p.W;
+            for (int i = 0; i < p.W; ++i) dst[i] = list[i];
         }
     }
     tc_fence_before();
@@ -648,7 +630,41 @@ __device__ __forceinline__ void main_survivors(const MainParams& p, const uint32
 // so a TMEM lane -- an epilogue thread -- is a database row and a column is a
 // query. Two 256-column FP32 accumulators fill TMEM; the tensor core works on
 // one tile while the epilogue reads the other.
-template <bool kFp8>
+// Minimum over the warp's 32 rows of each of a group's 32 columns: a
+// butterfly in which every step exchanges half of the remaining columns with
+// the partner lane; lane l ends with column l's minimum.
+__device__ __forceinline__ float column_min32(float (&c)[32], int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool upper = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < s; ++i) {
+            const float send = upper ? c[i] : c[i + s];
+            const float keep = upper ? c[i + s] : c[i];
+            c[i] = fminf(keep, __shfl_xor_sync(kFull, send, s));
+        }
+    }
+    return c[0];
+}
+
+// Sorted register network of kPilotR scores (static indices only).
+__device__ __forceinline__ void fnet_insert(float (&net)[kPilotR], float x) {
+    if (!(x < net[kPilotR - 1])) return;
+#pragma unroll
+    for (int i = kPilotR - 1; i > 0; --i) {
+        const float prev = net[i - 1];
+        net[i] = x < prev ? prev : (x < net[i] ? x : net[i]);
+    }
+    net[0] = fminf(x, net[0]);
+}
+
+// kPilot = false: the main pass (below). kPilot = true: the pilot over the
+// database sample with the same pipeline: per 32-row bucket (a warp's rows of a
+// tile) and query, the smallest score (column_min32), each query keeping its
+// kPilotR smallest bucket minima per (chunk, lane quadrant). Every bucket
+// minimum is a distinct row, so at least kPilotR sample rows score at most the
+// kPilotR-th smallest of them (the threshold tau_kernel takes).
+template <bool kFp8, bool kPilot>
 __global__ void __launch_bounds__(kMainThreads, 1)
     tc_main_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmX, const MainParams p) {
     extern __shared__ unsigned char smem_raw[];
@@ -798,6 +814,66 @@ __global__ void __launch_bounds__(kMainThreads, 1)
                 record_error(p.err, kErrTimeout);
             }
         }
+    } else if (kPilot) {
+        // ------------------------------------------------ pilot epilogue: thread = sample row
+        const int ew = warp - 2;
+        const int quad = warp & 3;
+        const int rl = quad * 32 + lane;
+        const int cb = (ew / 4) * (32 * kMGroups);
+        const int64_t q0 = (int64_t)qblock * kQTile + cb + lane;  // the queries this lane's columns end with
+        const float kInfF = __int_as_float(0x7f800000);
+        float net0[kPilotR], net1[kPilotR];
+#pragma unroll
+        for (int i = 0; i < kPilotR; ++i) net0[i] = net1[i] = kInfF;
+        const float m = __ldg(p.qs + 1);
+        const int rows_left = (int)(row1 - row0);
+        const float2* snp = p.sn + row0 + rl;
+        float2 sn_next = ntiles > 0 ? __ldg(snp) : make_float2(0.f, 0.f);
+        for (int t = 0; t < ntiles; ++t) {
+            const int a = t % kMainAcc;
+            const float2 sn = sn_next;
+            if (t + 1 < ntiles) sn_next = __ldg(snp + (t + 1) * kTile);
+            if (!mbar_wait(&acc_full[a], (uint32_t)((t / kMainAcc) & 1), abort_flag)) {
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    record_error(p.err, kErrTimeout);
+                }
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kQTile + cb);
+            const float B = m * sn.x, A = sn.y;
+            const bool rowvalid = t * kTile + rl < rows_left;
+            uint32_t v[32];
+            float c[32];
+            tmem_ld32_issue(tbase, v);
+            tmem_ld_wait(v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) c[j] = rowvalid ? fmaf(B, __uint_as_float(v[j]), A) : kInfF;
+            fnet_insert(net0, column_min32(c, lane));
+            tmem_ld32_issue(tbase + 32u, v);
+            tmem_ld_wait(v);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[a]);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) c[j] = rowvalid ? fmaf(B, __uint_as_float(v[j]), A) : kInfF;
+            fnet_insert(net1, column_min32(c, lane));
+        }
+        // keys (score, row 0xffffffff): every key of that score is at most the threshold key
+        const int list = chunk * 4 + quad;
+#pragma unroll
+        for (int g = 0; g < kMGroups; ++g) {
+            const int64_t q = q0 + 32 * g;
+            if (q < p.nq) {
+                u64* dst = p.pilot_out + ((size_t)q * p.pilot_lists + list) * kPilotR;
+#pragma unroll
+                for (int i = 0; i < kPilotR; ++i) {
+                    const float x = g == 0 ? net0[i] : net1[i];
+                    dst[i] = x < kInfF ? score_key(x, 0xffffffffu) : kKeyEmpty;
+                }
+            }
+        }
     } else {
         // ------------------------------------------------ epilogue: thread = database row
         const int ew = warp - 2;                        // epilogue warp 0 .. kMainEpiWarps - 1
@@ -844,20 +920,26 @@ __global__ void __launch_bounds__(kMainThreads, 1)
             const uint32_t row = (uint32_t)(row0 + rr);
             // per group: the row's smallest score over the group's queries is fma(B, max dot, A)
             // (B = m s_j <= 0, and a correctly rounded fma is monotone in each operand), tested
-            // against the group's largest threshold. One group in registers at a time: 18 warps
-            // leave 96 registers per thread.
-            // one 32-column group in registers at a time: 18 warps leave 96 registers per thread
+            // against the group's largest threshold.
+            // one 32-column group in registers at a time: 18 warps leave 96 registers per thread.
+            // Group 0's passing rows (at most kTRows; more is rare) wait in the transpose buffer, so
+            // the accumulator goes back to the MMA issuer right after group 1 is in registers.
             uint32_t v[32];
             tmem_ld32_issue(tbase, v);
             tmem_ld_wait(v);
             const unsigned ev0 = __ballot_sync(kFull, rowvalid && fmaf(B, max32(v), A) <= T0);
-            if (ev0) main_survivors(p, v, A, B, ev0, row, lane, tbuf, slot0, own_q_all + et, own_tau_all + et, n0);
+            const int defer0 = __popc(ev0) <= kTRows ? __popc(ev0) : 0;
+            if (defer0) stage_rows(v, A, B, row, ev0, lane, tbuf);
+            else if (ev0) main_survivors(p, v, A, B, ev0, row, lane, tbuf, slot0, own_q_all + et, own_tau_all + et, n0);
             tmem_ld32_issue(tbase + 32u, v);
             tmem_ld_wait(v);
-            // the accumulator is in registers: hand it back to the MMA issuer before scoring
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[a]);
+            if (defer0) {
+                check_rows(p, tbuf, defer0, lane, slot0, own_q_all + et, own_tau_all + et, n0);
+                __syncwarp();
+            }
             const unsigned ev1 = __ballot_sync(kFull, rowvalid && fmaf(B, max32(v), A) <= T1);
             if (ev1)
                 main_survivors(p, v, A, B, ev1, row, lane, tbuf, slot1, own_q_all + kMainEpiThreads + et,
@@ -1292,11 +1374,11 @@ LowpPlan plan(const lhr_db* db, int nq, bool fp8, int W) {
     pl.wmax = W <= 32 ? 32 : (W <= 64 ? 64 : 128);
     pl.sampled = (fp8 ? db->X8_s : db->Xb_s) != nullptr;
     pl.main = chunking(db->n, pl.qblocks, db->sms);
-    pl.pilot = chunking(std::max<int64_t>(db->n_sample, 1), pl.qblocks, db->sms);
+    pl.pilot = chunking(std::max<int64_t>(db->n_sample, 1), pl.qblocks_main, db->sms);
     const int elem = fp8 ? 1 : 2;
     pl.codes_bytes = a256((size_t)pl.nq_pad * db->dim * elem);
     pl.qs_bytes = a256(4 * sizeof(float));  // s_Q, m, max |q| bits
-    pl.pilot_bytes = pl.sampled ? a256((size_t)nq * pl.pilot.nchunks * kHalves * kPilotR * sizeof(u64)) : 0;
+    pl.pilot_bytes = pl.sampled ? a256((size_t)nq * pl.pilot.nchunks * 4 * kPilotR * sizeof(u64)) : 0;
     pl.tau_bytes = pl.sampled ? a256((size_t)pl.nq_pad * sizeof(u64)) + a256((size_t)pl.nq_pad * sizeof(float)) : 0;
     pl.cnt_bytes = pl.sampled ? a256((size_t)nq * sizeof(unsigned)) : 0;
     pl.cand_bytes = pl.sampled ? a256((size_t)nq * kCap * sizeof(u64)) : 0;
@@ -1312,7 +1394,7 @@ constexpr size_t kSmemLimit = 227 * 1024;  // dynamic shared memory per CTA
 
 size_t tc_smem_fixed(int slices, int mode) {
     return 1024 + (size_t)slices * kSliceTile + kSnSlots * kTile * sizeof(float2) +
-           (mode != kModePilot ? (size_t)kBuf * kEpiThreads * sizeof(u64) : 0) +
+           (size_t)kBuf * kEpiThreads * sizeof(u64) +
            (2 * kMaxStages + 1 + 2 * kAcc + 2 * kSnSlots) * sizeof(u64) + 16;
 }
 
@@ -1338,16 +1420,18 @@ int main_stages(int slices) {
     return std::min(kMaxStages, fit);
 }
 
-template <bool kFp8>
+template <bool kFp8, bool kPilot = false>
 cudaError_t launch_main(const CUtensorMap& mq, const CUtensorMap& mx, const MainParams& mp, int qblocks,
                         cudaStream_t stream) {
-    auto kern = tc_main_kernel<kFp8>;
+    auto kern = tc_main_kernel<kFp8, kPilot>;
     if (mp.stages < 2 || mp.stages > kMaxStages) return cudaErrorInvalidValue;
     if (mp.cs < 1 || qblocks % mp.cs || kTile % mp.cs) return cudaErrorInvalidValue;
     const size_t sm = main_smem(mp.slices, mp.stages);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    ProfScope ps(kFp8 ? "tc_main_kernel_fp8" : "tc_main_kernel_bf16", stream);
+    ProfScope ps(kPilot ? (kFp8 ? "tc_pilot_kernel_fp8" : "tc_pilot_kernel_bf16")
+                        : (kFp8 ? "tc_main_kernel_fp8" : "tc_main_kernel_bf16"),
+                 stream);
     // qblocks of kQTile queries; clusters of mp.cs CTAs along them
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(mp.nchunks, qblocks);
@@ -1380,7 +1464,7 @@ cudaError_t main_max_clusters(size_t smem, int cs, int* out) {
         *out = cache[dev][li];
         return cudaSuccess;
     }
-    auto kern = tc_main_kernel<kFp8>;
+    auto kern = tc_main_kernel<kFp8, false>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1);
@@ -1481,20 +1565,26 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
     tp.err = db->err;
     if (pl.sampled) {
         if (!make_map(&ms, fp8 ? db->X8_s : db->Xb_s, db->n_sample, db->dim, fp8)) return cudaErrorInvalidValue;
-        // pilot over the sample
-        TcParams pp = tp;
-        pp.n = db->n_sample;
-        pp.chunk_rows = pl.pilot.chunk_rows;
-        pp.nchunks = pl.pilot.nchunks;
-        pp.sn = fp8 ? db->sn8_s : db->snb_s;
-        pp.partial = pilot;
-        pp.stages = tc_stages(pp.slices, kModePilot);
-        e = fp8 ? launch_tc<true, kModePilot, 32>(ma, ms, pp, pl.qblocks, stream, "tc_pilot_kernel_fp8")
-                : launch_tc<false, kModePilot, 32>(ma, ms, pp, pl.qblocks, stream, "tc_pilot_kernel_bf16");
+        // pilot over the sample: the main pass's pipeline, 32-row bucket minima per query
+        MainParams pm{};
+        pm.n = db->n_sample;
+        pm.slices = tp.slices;
+        pm.stages = main_stages(tp.slices);
+        pm.chunk_rows = pl.pilot.chunk_rows;
+        pm.nchunks = pl.pilot.nchunks;
+        pm.sn = fp8 ? db->sn8_s : db->snb_s;
+        pm.qs = qs;
+        pm.nq = nq;
+        pm.cs = 1;
+        pm.pilot_out = pilot;
+        pm.pilot_lists = pl.pilot.nchunks * 4;
+        pm.err = db->err;
+        e = fp8 ? launch_main<true, true>(ma, ms, pm, pl.qblocks_main, stream)
+                : launch_main<false, true>(ma, ms, pm, pl.qblocks_main, stream);
         if (e != cudaSuccess) return e;
         {
             ProfScope ps("tau_kernel", stream);
-            tau_kernel<<<(pl.nq_pad + 7) / 8, 256, 0, stream>>>(pilot, pl.pilot.nchunks * kHalves, nq, pl.nq_pad,
+            tau_kernel<<<(pl.nq_pad + 7) / 8, 256, 0, stream>>>(pilot, pl.pilot.nchunks * 4, nq, pl.nq_pad,
                                                                  tau_key, tau_s);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
