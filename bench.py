@@ -149,7 +149,8 @@ def load_peaks() -> dict:
 def measure_gemm_peak(dev, kind: str, n: int = 8192, reps: int = 10):
     """Dense GEMM throughput (TFLOP/s, best of `reps`, CUDA events) of a library GEMM on this GPU:
     kind "fp8" = torch._scaled_mm on e4m3 operands (cuBLASLt), "f32" = FP32 torch.matmul with TF32
-    off (cuBLAS SGEMM on the FP32 FMA pipes). None when the library call is unavailable."""
+    off (cuBLAS SGEMM on the FP32 FMA pipes), "tf32" = FP32 torch.matmul with TF32 tensor-core math
+    allowed (8192^3). None when the library call is unavailable."""
     import torch
     try:
         if kind == "fp8":
@@ -159,8 +160,8 @@ def measure_gemm_peak(dev, kind: str, n: int = 8192, reps: int = 10):
             fn = lambda: torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
         else:
             prev = torch.backends.cuda.matmul.allow_tf32
-            torch.backends.cuda.matmul.allow_tf32 = False
-            n = 4096
+            torch.backends.cuda.matmul.allow_tf32 = kind == "tf32"
+            n = 8192 if kind == "tf32" else 4096
             a = torch.randn(n, n, device=dev)
             b = torch.randn(n, n, device=dev)
             fn = lambda: torch.matmul(a, b)
@@ -188,7 +189,8 @@ KERNELS = ("quantize_queries_kernel", "tc_pilot_kernel_fp8", "tc_pilot_kernel_bf
            "tc_main_kernel_fp8", "tc_main_kernel_bf16", "tc_full_kernel_fp8", "tc_full_kernel_bf16",
            "merge_rerank_kernel", "scan_pilot", "scan_topk_kernel", "small_topk_kernel", "aggregate_kernel",
            "hier_fused_kernel", "coarse_kernel", "collect_kernel", "shortlist_kernel", "wnorm_kernel",
-           "many_bound_kernel", "many_select_kernel", "many_kernel", "soft_forward_kernel",
+           "many_bound_kernel", "many_select_kernel", "tf32_many_kernel", "tf32_prep_kernel", "many_kernel",
+           "soft_forward_kernel",
            "soft_backward_kernel")
 
 
@@ -935,14 +937,34 @@ def run_differentiation(args, rank, world, local):
     tot = max_over_ranks(sum(ms), world)
     kt = read_kernels(lhr, args.steps, sum(ms))
     share = kt["kernels"]
-    # the selection's main kernel: the many-frame pass (>= 64 frames) or the streaming scan
-    sel = "many_kernel" if "many_kernel" in share else "scan_topk_kernel"
+    # the selection's main kernel: the many-frame pass (TF32 tensor cores, or the FP32 register-tiled
+    # form where D is not a multiple of 32) or the streaming scan
+    sel = next((n for n in ("tf32_many_kernel", "many_kernel") if n in share), "scan_topk_kernel")
     sel_us = share.get(sel, {"avg_us": float("nan")})["avg_us"]
     flops = 2.0 * B * m * c["n"] * c["dim"]  # one multiply-add per (frame, row, dim) of the expanded form
-    f32_meas = measure_gemm_peak(dev, "f32")
-    derived = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock (GHz), TFLOP/s
-    alu_peak = f32_meas if f32_meas else derived
     achieved = flops / (sel_us / 1e6) / 1e12
+    if sel == "tf32_many_kernel":
+        peaks = load_peaks()
+        tf32_meas = measure_gemm_peak(dev, "tf32")
+        ratio = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
+        scaled = peaks["bf16"] * ratio if peaks.get("bf16") else None
+        peak = tf32_meas if tf32_meas else scaled
+        roof = {"bound": "tensor", "kernel": f"{sel} (weighted selection filter, TF32 operands)",
+                "achieved": round(achieved, 2), "peak": round(peak, 1),
+                "peak_source": ("cuBLAS TF32 GEMM 8192^3 (torch.matmul, allow_tf32), best of 10, this run"
+                                if tf32_meas else f"measured BF16 x {ratio:.3f} (nominal TF32/BF16), {peaks['source']}"),
+                "peak_bf16_scaled": round(scaled, 1) if scaled else None}
+    else:
+        f32_meas = measure_gemm_peak(dev, "f32")
+        derived = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock (GHz), TFLOP/s
+        peak = f32_meas if f32_meas else derived
+        roof = {"bound": "alu", "kernel": f"{sel} (weighted selection)", "achieved": round(achieved, 2),
+                "peak": round(peak, 1),
+                "peak_source": ("FP32 SGEMM 4096^3 with TF32 off (cuBLAS), best of 10, this run"
+                                if f32_meas else "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (derived)"),
+                "peak_derived": round(derived, 1)}
+    roof.update({"unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None, "avg_launch_us": sel_us,
+                 "algorithmic_flops_per_launch": flops, "timed_in": "event pairs recorded inside the timed steps"})
     # gradient check of one window against the FP64 oracle (selection from the GPU)
     loss, fr = step(0)
     g_fr = fr.grad.detach().cpu().numpy()
@@ -967,14 +989,7 @@ def run_differentiation(args, rank, world, local):
         "config": {"workload": "differentiation", "desc": "N=200000 D=256, B=256 windows of m=5, k=32, w=1, "
                                                           "tau=0.1: soft retrieval forward + location loss + backward",
                    "l2": "flushed before every timed step", "launch": "eager (autograd)"},
-        "roofline": {"bound": "alu", "kernel": f"{sel} (weighted selection)",
-                     "achieved": round(achieved, 2), "peak": round(alu_peak, 1),
-                     "peak_source": ("FP32 SGEMM 4096^3 with TF32 off (cuBLAS), best of 10, this run"
-                                     if f32_meas else "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (derived)"),
-                     "peak_derived": round(derived, 1), "unit": "TFLOP/s",
-                     "frac": round(achieved / alu_peak, 4), "traffic": None,
-                     "avg_launch_us": sel_us, "algorithmic_flops_per_launch": flops,
-                     "timed_in": "event pairs recorded inside the timed steps"},
+        "roofline": roof,
         "kernels": kt,
         "grad_check": {"dq_max_rel_err_vs_fp64_window0": dq_err, "loss": float(loss.item())},
         "cpu_baseline": cpu,

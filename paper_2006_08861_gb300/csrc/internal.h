@@ -106,7 +106,7 @@ size_t scan_scratch_bytes(const lhr_db* db, int nq, int k, bool pilot);
 // many.cu: exhaustive top k for many frames at once (register-tiled expanded
 // form over the pilot's bound, exact re-score of the candidates)
 bool many_eligible(const lhr_db* db, int nq, int k);
-size_t many_scratch_bytes(int nq);
+size_t many_scratch_bytes(const lhr_db* db, int nq);
 cudaError_t launch_many(const lhr_db* db, const float* q, int nq, int k, const float* w, const float* xn,
                         const float* xmax_w, const unsigned* bmin, float margin_scale, int64_t* idx, float* dist,
                         void* scratch, cudaStream_t stream);
@@ -126,6 +126,14 @@ bool hier_fused_eligible(const lhr_db* db, int nq, int shortlist);
 size_t hier_scratch_bytes(const lhr_db* db, int nq);
 cudaError_t launch_hier_fused(const lhr_db* db, const float* q, int nq, int shortlist, int k, int64_t* idx,
                               float* dist, const AggArgs* agg_args, void* scratch, cudaStream_t stream);
+
+// Sorts the keys key[0, nq) ascending (ties by index) and writes, for sorted
+// position i < n_sorted (a multiple of 256): perm[i] = the index there (-1 past
+// nq), its row_bytes of `codes` (a zero row past nq) into codes_s, and per 32
+// positions the largest key among their valid indices (-inf if none) into
+// gmax. Batches above 16,384 keep their order (lowp.cu).
+cudaError_t launch_sort_queries(const float* key, int nq, int n_sorted, const void* codes, int row_bytes,
+                                void* codes_s, int* perm, float* gmax, cudaStream_t stream);
 
 // Low-precision tensor-core scores + FP32 re-rank (lowp.cu).
 size_t lowp_scratch_bytes(const lhr_db* db, int nq, bool fp8, int W);

@@ -63,6 +63,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc.cuh"
 
 namespace lhr {
 namespace {
@@ -81,117 +82,14 @@ constexpr int kThreads = 64 + kEpiThreads;  // producer, MMA issuer, epilogue
 constexpr int kQTile = 256;       // queries per CTA of the main pass (UMMA N)
 constexpr int kMainAcc = 2;       // main pass: 2 x 256 FP32 accumulator columns = all of TMEM
 
-// ------------------------------------------------------------------ PTX
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, u64* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// The same tile box delivered to the shared memory of every CTA of the cluster
-// in `mask` (same offsets in each), completing bytes on each CTA's barrier at
-// `bar`'s offset.
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int c0, int c1, u64* bar,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
-        "%3}], [%4], %5;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-// All threads of every CTA of the cluster (a plain block barrier when the cluster is one CTA).
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tc_commit(u64* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// Arrival, once this thread's earlier tcgen05 operations complete, on the barrier
-// at `bar`'s offset in every CTA of the cluster in `mask`.
-__device__ __forceinline__ void tc_commit_mc(u64* bar, uint16_t mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                     smem_u32(bar)),
-                 "h"(mask)
-                 : "memory");
-}
+// ------------------------------------------------------------------ PTX (tc.cuh)
+using namespace tc;
 
 template <bool kFp8>
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, u64 adesc, u64 bdesc, uint32_t idesc, uint32_t accum) {
-    if (kFp8) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-            : "memory");
-    }
+    tc::tc_mma<kFp8 ? kTcFP8 : kTcBF16>(d_tmem, adesc, bdesc, idesc, accum);
 }
-
-// tcgen05.ld of 32 columns without the wait: the registers are valid only after
-// tmem_ld_wait on the same array, which names them so nothing reads them earlier.
-__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
-                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
-                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
-                 :
-                 : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row core groups 1024 bytes apart.
-__device__ __forceinline__ u64 sw128_desc(uint32_t saddr) {
-    u64 d = (u64)((saddr >> 4) & 0x3FFFu);
-    d |= (u64)1 << 16;              // leading-dimension offset (unused with this swizzle)
-    d |= (u64)(1024 >> 4) << 32;    // stride-dimension offset: 1024 B between 8-row groups
-    d |= (u64)1 << 46;              // descriptor version for tcgen05
-    d |= (u64)2 << 61;              // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor: dense, FP32 accumulate, A/B K-major, M = 128, N = n
-// (128 or 256). BF16 inputs: format 1 in both operand fields (kind::f16);
-// E4M3: format 0 (kind::f8f6f4).
-__host__ __device__ constexpr uint32_t tc_idesc(bool fp8, int n = kTile) {
-    return (1u << 4)                      // D format: F32
-           | ((fp8 ? 0u : 1u) << 7)       // A format
-           | ((fp8 ? 0u : 1u) << 10)      // B format
-           | ((uint32_t)(n >> 3) << 17)      // N >> 3
-           | ((uint32_t)(kTile >> 4) << 24); // M >> 4
-}
+__host__ __device__ constexpr uint32_t tc_idesc(bool fp8, int n = kTile) { return tc::tc_idesc(fp8 ? kTcFP8 : kTcBF16, n); }
 
 // Orderable key of a (possibly negative) FP32 score and a row.
 __device__ __forceinline__ u64 score_key(float t, uint32_t row) {
@@ -523,28 +421,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAcc * kTile) : "memory");
-}
-
-// Maximum of 32 accumulator values (three-input max: one instruction on this architecture).
-__device__ __forceinline__ float fmax3(float a, float b, float c) {
-    float r;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-
-// Maximum of 32 accumulator values in four interleaved chains of three-input
-// maxima (few live temporaries: the values of two groups are in registers).
-__device__ __forceinline__ float max32(const uint32_t (&v)[32]) {
-    float c[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) c[i] = fmax3(__uint_as_float(v[i]), __uint_as_float(v[4 + i]), __uint_as_float(v[8 + i]));
-#pragma unroll
-    for (int j = 12; j < 28; j += 8)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) c[i] = fmax3(c[i], __uint_as_float(v[j + i]), __uint_as_float(v[j + 4 + i]));
-#pragma unroll
-    for (int i = 0; i < 4; ++i) c[i] = fmaxf(c[i], __uint_as_float(v[28 + i]));
-    return fmax3(c[0], c[1], fmaxf(c[2], c[3]));
 }
 
 // Main pass layout: 2 + kMainEpiWarps warps. Epilogue warp w reads TMEM lane
@@ -1309,35 +1185,8 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_rerank_kernel(
 }
 
 // ------------------------------------------------------------------ host
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static std::once_flag once;
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    std::call_once(once, [] {
-        cudaDriverEntryPointQueryResult q;
-        void* f = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-    });
-    return fn;
-}
-
-// 2-D map over a row-major rows x D array of 1- or 2-byte codes; box = 128
-// bytes of K by 128 rows, 128-byte swizzle, zero fill past the last row.
 bool make_map(CUtensorMap* map, const void* base, int64_t rows, int D, bool fp8, int box_rows = kTile) {
-    auto fn = encode_fn();
-    if (!fn) return false;
-    const int elem = fp8 ? 1 : 2;
-    cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)D * elem};
-    cuuint32_t box[2] = {(cuuint32_t)(kSliceBytes / elem), (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    const CUresult r = fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                          const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
+    return tc::make_map(map, base, rows, D, fp8 ? kTcFP8 : kTcBF16, box_rows);
 }
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -1508,6 +1357,21 @@ cudaError_t launch_full(int wmax, const CUtensorMap& ma, const CUtensorMap& mb, 
 
 }  // namespace
 
+cudaError_t launch_sort_queries(const float* key, int nq, int n_sorted, const void* codes, int row_bytes,
+                                void* codes_s, int* perm, float* gmax, cudaStream_t stream) {
+    if (n_sorted % kQTile || row_bytes % 16) return cudaErrorInvalidValue;
+    int n2 = 1;
+    while (n2 < n_sorted) n2 <<= 1;
+    const size_t ssm = n_sorted <= kSortMax ? (size_t)n2 * sizeof(u64) : 0;
+    cudaError_t e = cudaFuncSetAttribute(sort_queries_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+    if (e != cudaSuccess) return e;
+    ProfScope ps("sort_queries_kernel", stream);
+    sort_queries_kernel<<<n_sorted / kQTile, kSortThreads, ssm, stream>>>(
+        key, nq, n_sorted, reinterpret_cast<const uint4*>(codes), row_bytes / 16, reinterpret_cast<uint4*>(codes_s),
+        perm, gmax);
+    return cudaGetLastError();
+}
+
 size_t lowp_scratch_bytes(const lhr_db* db, int nq, bool fp8, int W) {
     const LowpPlan pl = plan(db, nq, fp8, W);
     return pl.codes_bytes + pl.qs_bytes + pl.pilot_bytes + pl.tau_bytes + pl.cnt_bytes + pl.cand_bytes +
@@ -1588,20 +1452,10 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
                                                                  tau_key, tau_s);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        {
-            // queries in ascending-threshold order, in 256-query blocks, for the main pass
-            ProfScope ps("sort_queries_kernel", stream);
-            int n2 = 1;
-            while (n2 < pl.nq_sorted) n2 <<= 1;
-            const size_t ssm = pl.nq_sorted <= kSortMax ? (size_t)n2 * sizeof(u64) : 0;
-            if ((e = cudaFuncSetAttribute(sort_queries_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)ssm)) != cudaSuccess)
-                return e;
-            sort_queries_kernel<<<pl.qblocks_main, kSortThreads, ssm, stream>>>(
-                tau_s, nq, pl.nq_sorted, reinterpret_cast<const uint4*>(codes), db->dim * (fp8 ? 1 : 2) / 16,
-                reinterpret_cast<uint4*>(codes_s), perm, tgrp);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
+        // queries in ascending-threshold order, in 256-query blocks, for the main pass
+        if ((e = launch_sort_queries(tau_s, nq, pl.nq_sorted, codes, db->dim * (fp8 ? 1 : 2), codes_s, perm, tgrp,
+                                     stream)) != cudaSuccess)
+            return e;
         // one CTA per cluster: sharing each database tile across the query blocks of a cluster (each
         // CTA loading 1/cs of it) cuts L2 reads but couples the CTAs' pipelines, and measured slower
         const int cs = 1;

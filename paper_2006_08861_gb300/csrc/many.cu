@@ -22,12 +22,18 @@
 // distance <= e_k + margin_f); those rows are re-scored with the exact
 // direct form sum w (q - x)^2 and the top k (distance, row) keys written. A
 // frame whose buffer overflowed is scanned exhaustively by its warp.
+//
+// Where D is a multiple of 32 the filter runs on the tensor cores instead
+// (tf32_many_kernel: tcgen05.mma kind::tf32, 128 rows x 128 frames per MMA,
+// operands staged by TMA, accumulators in TMEM) with the margin widened for
+// TF32 operands; the candidates and their exact re-score are the same.
 #include <cuda_pipeline.h>
 
 #include <algorithm>
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc.cuh"
 
 namespace lhr {
 namespace {
@@ -370,6 +376,295 @@ __global__ void many_select_kernel(ManyParams p) {
     }
 }
 
+// ------------------------------------------------------------------ TF32 tensor-core pass
+// The filter of many_kernel on the tensor cores: u(f, r) = -2 (w q_f) . x_r + ||x_r||_w^2
+// by tcgen05.mma kind::tf32 (operands truncated to TF32, FP32 accumulate) over
+// M = 128 rows x N = 128 frames tiles, one CTA per (128-frame block, row chunk).
+// The frames come in ascending order of their filter bound (thr_f - qn_f), so a
+// 32-frame group has a tight bound: its largest. A row's smallest u over a
+// group is fma(-2, max dot, ||x_r||_w^2); rows under the group bound go through
+// the warp's transpose buffer and lane l checks frame l exactly as many_kernel
+// does: e = fma(-2, dot, ||x_r||_w^2 + ||q_f||_w^2) <= thr_f. The margin in thr_f
+// and in many_select_kernel covers TF32 operands (many_bound_kernel).
+using namespace tc;
+constexpr int kFT = 128;                 // frames per CTA (UMMA N)
+constexpr int kFAcc = 4;                 // 128-column FP32 accumulators (all of TMEM)
+constexpr int kFEpiWarps = 8;            // two per TMEM lane quadrant, 64 columns each
+constexpr int kFEpiThreads = 32 * kFEpiWarps;
+constexpr int kFThreads = 64 + kFEpiThreads;
+constexpr int kFMaxStages = 8;
+constexpr int kFOwn = 4;                 // staged keys per owned frame
+constexpr int kFTRows = 8;               // rows a warp moves through its transpose buffer at a time
+constexpr int kFTStride = 36;            // floats per buffered row: 32 values, then (xn, -, row, -)
+constexpr int kFSlice = kFT * kTcSliceBytes;  // 16 KB: one 128-byte K slice of 128 rows
+
+struct TfParams {
+    int64_t n;
+    int slices, stages;
+    int64_t chunk_rows;
+    int nchunks;
+    const float* xn;      // per row ||x||_w^2 (n values)
+    const int* fperm;     // per sorted position: the frame there, -1 = padding
+    const float* gbound;  // per 32 sorted positions: the largest (thr_f - qn_f) + slack
+    const float* thr;     // per frame: filter threshold on e
+    const float* qn;      // per frame: ||q||_w^2
+    unsigned* cnt;        // per frame: candidates seen
+    u64* cand;            // per frame: kMCap candidate keys (orderable e, row)
+    int nq;
+    int* err;
+};
+
+__device__ __forceinline__ void tf_flush(const TfParams& p, const u64* slot, int f, int n) {
+    const unsigned pos = atomicAdd(p.cnt + f, (unsigned)n);
+    for (int i = 0; i < n; ++i)
+        if (pos + i < (unsigned)kMCap) p.cand[(size_t)f * kMCap + pos + i] = slot[i * kFEpiThreads];
+}
+
+// Rows of `ev` through the transpose buffer; lane l checks frame f_own (column l).
+__device__ __forceinline__ void tf_survivors(const TfParams& p, const uint32_t (&v)[32], float xn, uint32_t row,
+                                             unsigned ev, int lane, float* tbuf, u64* slot, int f_own, float thr_own,
+                                             float qn_own, int& n_own) {
+    const unsigned lt = (1u << lane) - 1u;
+    while (ev) {
+        const unsigned sel = __ballot_sync(kFull, ((ev >> lane) & 1u) && __popc(ev & lt) < kFTRows);
+        if ((sel >> lane) & 1u) {
+            float4* dst = reinterpret_cast<float4*>(tbuf + __popc(sel & lt) * kFTStride);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                     __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+            dst[8] = make_float4(xn, 0.f, __uint_as_float(row), 0.f);
+        }
+        __syncwarp();
+        const int nsel = __popc(sel);
+        for (int r = 0; r < nsel; ++r) {
+            const float x = tbuf[r * kFTStride + lane];
+            const float4 mt = *reinterpret_cast<const float4*>(tbuf + r * kFTStride + 32);
+            const float e = fmaf(-2.f, x, mt.x + qn_own);
+            if (f_own >= 0 && e <= thr_own) {
+                slot[n_own * kFEpiThreads] = orderable_key(e, __float_as_uint(mt.z));
+                if (++n_own == kFOwn) {
+                    tf_flush(p, slot, f_own, n_own);
+                    n_own = 0;
+                }
+            }
+        }
+        __syncwarp();
+        ev &= ~sel;
+    }
+}
+
+__global__ void __launch_bounds__(kFThreads, 1)
+    tf32_many_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmX, const TfParams p) {
+    extern __shared__ unsigned char smem_raw[];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int chunk = blockIdx.x, fblock = blockIdx.y;
+    unsigned char* smem =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int stages = p.stages;
+    unsigned char* sQ = smem;                                    // slices x 16 KB: the block's frames (w q)
+    unsigned char* sX = sQ + (size_t)p.slices * kFSlice;         // stages x 16 KB: database slices
+    u64* own_slot = reinterpret_cast<u64*>(sX + (size_t)stages * kFSlice);  // 2 kFOwn x threads
+    float* tbuf_all = reinterpret_cast<float*>(own_slot + 2 * kFOwn * kFEpiThreads);
+    u64* full = reinterpret_cast<u64*>(tbuf_all + kFEpiWarps * kFTRows * kFTStride);
+    u64* empty = full + kFMaxStages;
+    u64* q_full = empty + kFMaxStages;
+    u64* acc_full = q_full + 1;
+    u64* acc_empty = acc_full + kFAcc;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + kFAcc);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+    const int64_t row0 = (int64_t)chunk * p.chunk_rows;
+    const int64_t row1 = min(p.n, row0 + p.chunk_rows);
+    const int ntiles = row1 > row0 ? (int)((row1 - row0 + kTcM - 1) / kTcM) : 0;
+    constexpr int kElemPerSlice = kTcSliceBytes / 4;  // 32 floats
+    constexpr int kMmaK = 8;                          // TF32 elements per MMA (32 bytes)
+    constexpr int kMmaPerSlice = kElemPerSlice / kMmaK;
+    constexpr uint32_t kIdesc = tc_idesc(kTcTF32, kFT);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(q_full, 1);
+        for (int i = 0; i < kFAcc; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], kFEpiWarps);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(kFAcc * kFT)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(q_full, (uint32_t)p.slices * kFSlice);
+            for (int s = 0; s < p.slices; ++s)
+                tma_load_2d(sQ + (size_t)s * kFSlice, &tmQ, s * kElemPerSlice, fblock * kFT, q_full);
+            int b_issued = 0, st = 0;
+            uint32_t ph = 0;
+            for (int t = 0; t < ntiles && !*abort_flag; ++t) {
+                const int r = (int)(row0 + (int64_t)t * kTcM);
+                for (int s = 0; s < p.slices; ++s) {
+                    if (!mbar_wait(&empty[st], ph ^ 1u, abort_flag)) {
+                        *abort_flag = 1;
+                        record_error(p.err, kErrTimeout);
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[st], kFSlice);
+                    tma_load_2d(sX + (size_t)st * kFSlice, &tmX, s * kElemPerSlice, r, &full[st]);
+                    ++b_issued;
+                    if (++st == stages) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            if (*abort_flag) {
+                // let this thread's copies still in flight land before the CTA exits (bounded waits)
+                mbar_wait(q_full, 0u, nullptr);
+                for (int it = b_issued > stages ? b_issued - stages : 0; it < b_issued; ++it)
+                    mbar_wait(&full[it % stages], (uint32_t)((it / stages) & 1), nullptr);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = mbar_wait(q_full, 0u, abort_flag);
+            int st = 0;
+            uint32_t ph = 0;
+            for (int t = 0; ok && t < ntiles; ++t) {
+                const int a = t % kFAcc;
+                if (!mbar_wait(&acc_empty[a], (uint32_t)((t / kFAcc) & 1) ^ 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(a * kFT);
+                for (int s = 0; s < p.slices; ++s) {
+                    if (!mbar_wait(&full[st], ph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t x_base = smem_u32(sX + (size_t)st * kFSlice);
+                    const uint32_t q_base = smem_u32(sQ + (size_t)s * kFSlice);
+#pragma unroll
+                    for (int kk = 0; kk < kMmaPerSlice; ++kk) {
+                        const uint32_t off = (uint32_t)(kk * kMmaK * 4);
+                        tc::tc_mma<kTcTF32>(d_tmem, sw128_desc(x_base + off), sw128_desc(q_base + off), kIdesc,
+                                            (s | kk) != 0 ? 1u : 0u);
+                    }
+                    tc_commit(&empty[st]);
+                    if (++st == stages) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                tc_commit(&acc_full[a]);
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                record_error(p.err, kErrTimeout);
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue: thread = database row
+        const int ew = warp - 2;
+        const int quad = warp & 3;
+        const int rl = quad * 32 + lane;
+        const int cb = (ew / 4) * 64;                         // first column (frame) of this warp's half
+        const int64_t p0 = (int64_t)fblock * kFT + cb;        // its sorted position
+        float* tbuf = tbuf_all + ew * kFTRows * kFTStride;
+        const int et = threadIdx.x - 64;
+        u64* slot0 = own_slot + et;
+        u64* slot1 = slot0 + kFOwn * kFEpiThreads;
+        const float G0 = __ldg(p.gbound + p0 / 32), G1 = __ldg(p.gbound + p0 / 32 + 1);
+        const int f0 = __ldg(p.fperm + p0 + lane), f1 = __ldg(p.fperm + p0 + 32 + lane);
+        const float ninf = -__int_as_float(0x7f800000);
+        const float thr0 = f0 >= 0 ? __ldg(p.thr + f0) : ninf, thr1 = f1 >= 0 ? __ldg(p.thr + f1) : ninf;
+        const float qn0 = f0 >= 0 ? __ldg(p.qn + f0) : 0.f, qn1 = f1 >= 0 ? __ldg(p.qn + f1) : 0.f;
+        int n0 = 0, n1 = 0;
+        for (int t = 0; t < ntiles; ++t) {
+            const int a = t % kFAcc;
+            const int64_t row = row0 + (int64_t)t * kTcM + rl;
+            const bool rowvalid = row < row1;
+            const float xn = rowvalid ? __ldg(p.xn + row) : 0.f;
+            if (!mbar_wait(&acc_full[a], (uint32_t)((t / kFAcc) & 1), abort_flag)) {
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    record_error(p.err, kErrTimeout);
+                }
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kFT + cb);
+            uint32_t va[32], vb[32];
+            tmem_ld32_issue(tbase, va);
+            tmem_ld32_issue(tbase + 32u, vb);
+            tmem_ld_wait(va);  // waits for both loads; the second wait only names vb's registers
+            tmem_ld_wait(vb);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[a]);
+            const unsigned ev0 = __ballot_sync(kFull, rowvalid && fmaf(-2.f, max32(va), xn) <= G0);
+            if (ev0) tf_survivors(p, va, xn, (uint32_t)row, ev0, lane, tbuf, slot0, f0, thr0, qn0, n0);
+            const unsigned ev1 = __ballot_sync(kFull, rowvalid && fmaf(-2.f, max32(vb), xn) <= G1);
+            if (ev1) tf_survivors(p, vb, xn, (uint32_t)row, ev1, lane, tbuf, slot1, f1, thr1, qn1, n1);
+        }
+        if (n0) tf_flush(p, slot0, f0, n0);
+        if (n1) tf_flush(p, slot1, f1, n1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kFAcc * kFT) : "memory");
+}
+
+// Per frame: w q (the B operand rows) and the filter's sort key thr_f - qn_f, raised by a
+// rounding slack so the group test fma(-2, dot, ||x||_w^2) <= bound never rejects a pair the
+// frame's own test e <= thr_f keeps.
+__global__ void tf32_prep_kernel(const float* Q, const float* w, int nq, int D, const float* thr, const float* qn,
+                                 const float* xnmax_w, float xnmax, float* wq, float* fkey) {
+    const int lane = threadIdx.x & 31;
+    const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (f >= nq) return;
+    for (int d = lane; d < D; d += 32) {
+        const float q = Q[(size_t)f * D + d];
+        wq[(size_t)f * D + d] = w ? w[d] * q : q;
+    }
+    if (lane == 0) {
+        const float t = thr[f], qv = qn[f];
+        if (xnmax_w != nullptr) xnmax = __ldg(xnmax_w);
+        const float slack = 4.0f * 5.9604645e-08f * (fabsf(t) + fabsf(qv) + xnmax);  // 4 units in the last place
+        fkey[f] = (t - qv) + slack;
+    }
+}
+
+size_t tf32_smem(int slices, int stages) {
+    return 1024 + (size_t)(slices + stages) * kFSlice + (size_t)2 * kFOwn * kFEpiThreads * sizeof(u64) +
+           (size_t)kFEpiWarps * kFTRows * kFTStride * sizeof(float) + (2 * kFMaxStages + 1 + 2 * kFAcc) * sizeof(u64) +
+           16;
+}
+
+int tf32_stages(int slices) {
+    const size_t fixed = tf32_smem(slices, 0);
+    const size_t lim = 227 * 1024;
+    const int fit = fixed < lim ? (int)((lim - fixed) / kFSlice) : 0;
+    return std::min(kFMaxStages, fit);
+}
+
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t many_smem(int D, int kc) {
@@ -389,14 +684,45 @@ bool many_eligible(const lhr_db* db, int nq, int k) {
            db->dim <= 256 && db->n < 1000000;
 }
 
-size_t many_scratch_bytes(int nq) {
-    return 3 * a256((size_t)nq * sizeof(float)) + a256((size_t)nq * sizeof(unsigned)) +
-           a256((size_t)nq * kMCap * sizeof(u64));
+// The TF32 pass serves whole 32-float K slices of at most 256 dimensions and row
+// indices that fit the candidate keys.
+bool tf32_eligible(const lhr_db* db) { return db->dim % 32 == 0 && db->dim <= 256 && db->n < (int64_t)1 << 31; }
+
+int tf32_sorted(int nq) { return (nq + 255) / 256 * 256; }
+
+size_t many_scratch_bytes(const lhr_db* db, int nq) {
+    size_t b = 3 * a256((size_t)nq * sizeof(float)) + a256((size_t)nq * sizeof(unsigned)) +
+               a256((size_t)nq * kMCap * sizeof(u64));
+    if (tf32_eligible(db)) {
+        const size_t ns = (size_t)tf32_sorted(nq);
+        b += a256((size_t)nq * sizeof(float)) + a256((size_t)nq * db->dim * sizeof(float)) +
+             a256(ns * db->dim * sizeof(float)) + a256(ns * sizeof(int)) + a256(ns / 32 * sizeof(float));
+    }
+    return b;
+}
+
+// Row chunks per frame block so that the CTAs fill whole waves of the SMs as
+// far as possible (CTAs x rows per CTA, in waves).
+int tf32_chunks(int nfb, int sms, int64_t n) {
+    const int64_t tiles = (n + kTcM - 1) / kTcM;
+    int best = 1;
+    double best_cost = 1e300;
+    for (int c = 1; c <= 4 * sms && c <= tiles && (int64_t)c * nfb <= 65535; ++c) {
+        const int64_t rows = (tiles + c - 1) / c;  // tiles per chunk
+        const int64_t waves = ((int64_t)c * nfb + sms - 1) / sms;
+        const double cost = (double)waves * (double)(rows + 2);  // + per-CTA fixed cost, about two tiles
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = c;
+        }
+    }
+    return best;
 }
 
 cudaError_t launch_many(const lhr_db* db, const float* q, int nq, int k, const float* w, const float* xn,
                         const float* xmax_w, const unsigned* bmin, float margin_scale, int64_t* idx, float* dist,
                         void* scratch, cudaStream_t stream) {
+    const bool tf32 = tf32_eligible(db);
     ManyParams p{};
     p.X = db->X;
     p.xn = xn;
@@ -407,27 +733,29 @@ cudaError_t launch_many(const lhr_db* db, const float* q, int nq, int k, const f
     p.nq = nq;
     p.k = k;
     p.bmin = bmin;
-    p.margin_scale = margin_scale;
+    // TF32 operands (10 stored mantissa bits, truncated or rounded): each product
+    // w q_d x_d is off by less than (2^-9 + 2^-20) of its magnitude, so 2 |dot
+    // error| <= (2^-9 + 2^-20) 2 ||q||_w ||x||_w <= (2^-10 + 2^-21) rad^2; the FP32
+    // accumulation term is doubled for the tensor core's own summation order.
+    p.margin_scale = tf32 ? 2.f * margin_scale + 1.0f / 1024.f * 1.001f : margin_scale;
     p.xmax = (float)(sqrt((double)db->xnorm_max) * 1.0001);
     p.xmax_w = xmax_w;
     unsigned char* base = reinterpret_cast<unsigned char*>(scratch);
-    p.thr = reinterpret_cast<float*>(base);
-    p.qn = reinterpret_cast<float*>(base + a256((size_t)nq * sizeof(float)));
-    p.mg = reinterpret_cast<float*>(base + 2 * a256((size_t)nq * sizeof(float)));
-    p.cnt = reinterpret_cast<unsigned*>(base + 3 * a256((size_t)nq * sizeof(float)));
-    p.cand = reinterpret_cast<u64*>(base + 3 * a256((size_t)nq * sizeof(float)) + a256((size_t)nq * sizeof(unsigned)));
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        unsigned char* r = base + off;
+        off += a256(bytes);
+        return r;
+    };
+    p.thr = reinterpret_cast<float*>(take((size_t)nq * sizeof(float)));
+    p.qn = reinterpret_cast<float*>(take((size_t)nq * sizeof(float)));
+    p.mg = reinterpret_cast<float*>(take((size_t)nq * sizeof(float)));
+    p.cnt = reinterpret_cast<unsigned*>(take((size_t)nq * sizeof(unsigned)));
+    p.cand = reinterpret_cast<u64*>(take((size_t)nq * kMCap * sizeof(u64)));
     p.perm = db->perm;
     p.idx = idx;
     p.dist = dist;
     p.err = db->err;
-    const int nfb = (nq + kMF - 1) / kMF;
-    // about one CTA per SM over frame blocks x row chunks; chunks are whole tiles
-    const int chunks = std::max(1, (db->sms + nfb - 1) / nfb);
-    int64_t cr = (db->n + chunks - 1) / chunks;
-    cr = (cr + kMRows - 1) / kMRows * kMRows;
-    p.chunk_rows = cr;
-    const int nchunks = (int)((db->n + cr - 1) / cr);
-    if (nchunks > 65535) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(p.cnt, 0, (size_t)nq * sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
     {
@@ -435,9 +763,63 @@ cudaError_t launch_many(const lhr_db* db, const float* q, int nq, int k, const f
         many_bound_kernel<<<(nq + 7) / 8, 256, 0, stream>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const int kc = db->dim % 128 == 0 ? 128 : 64;
-    const size_t sm = many_smem(db->dim, kc);
-    {
+    if (tf32) {
+        const int D = db->dim, ns = tf32_sorted(nq);
+        float* fkey = reinterpret_cast<float*>(take((size_t)nq * sizeof(float)));
+        float* wq = reinterpret_cast<float*>(take((size_t)nq * D * sizeof(float)));
+        float* wq_s = reinterpret_cast<float*>(take((size_t)ns * D * sizeof(float)));
+        int* fperm = reinterpret_cast<int*>(take((size_t)ns * sizeof(int)));
+        float* gbound = reinterpret_cast<float*>(take((size_t)ns / 32 * sizeof(float)));
+        {
+            ProfScope ps("tf32_prep_kernel", stream);
+            tf32_prep_kernel<<<(nq + 7) / 8, 256, 0, stream>>>(q, w, nq, D, p.thr, p.qn, xmax_w, db->xnorm_max, wq,
+                                                                fkey);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        if ((e = launch_sort_queries(fkey, nq, ns, wq, D * (int)sizeof(float), wq_s, fperm, gbound, stream)) !=
+            cudaSuccess)
+            return e;
+        CUtensorMap tmQ, tmX;
+        if (!make_map(&tmQ, wq_s, ns, D, kTcTF32, kFT) || !make_map(&tmX, db->X, db->n, D, kTcTF32, kTcM))
+            return cudaErrorInvalidValue;
+        TfParams t{};
+        t.n = db->n;
+        t.slices = D / 32;
+        t.stages = tf32_stages(t.slices);
+        if (t.stages < 2) return cudaErrorInvalidValue;
+        const int nfb = ns / kFT;
+        const int nchunks = tf32_chunks(nfb, db->sms, db->n);
+        int64_t cr = (db->n + nchunks - 1) / nchunks;
+        t.chunk_rows = (cr + kTcM - 1) / kTcM * kTcM;
+        t.nchunks = (int)((db->n + t.chunk_rows - 1) / t.chunk_rows);
+        if (t.nchunks < 1) t.nchunks = 1;
+        t.xn = xn;
+        t.fperm = fperm;
+        t.gbound = gbound;
+        t.thr = p.thr;
+        t.qn = p.qn;
+        t.cnt = p.cnt;
+        t.cand = p.cand;
+        t.nq = nq;
+        t.err = db->err;
+        const size_t sm = tf32_smem(t.slices, t.stages);
+        if ((e = cudaFuncSetAttribute(tf32_many_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+            cudaSuccess)
+            return e;
+        ProfScope ps("tf32_many_kernel", stream);
+        tf32_many_kernel<<<dim3(t.nchunks, nfb), kFThreads, sm, stream>>>(tmQ, tmX, t);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+        const int nfb = (nq + kMF - 1) / kMF;
+        // about one CTA per SM over frame blocks x row chunks; chunks are whole tiles
+        const int chunks = std::max(1, (db->sms + nfb - 1) / nfb);
+        int64_t cr = (db->n + chunks - 1) / chunks;
+        cr = (cr + kMRows - 1) / kMRows * kMRows;
+        p.chunk_rows = cr;
+        const int nchunks = (int)((db->n + cr - 1) / cr);
+        if (nchunks > 65535) return cudaErrorInvalidValue;
+        const int kc = db->dim % 128 == 0 ? 128 : 64;
+        const size_t sm = many_smem(db->dim, kc);
         auto kern = kc == 128 ? (w ? many_kernel<true, 128> : many_kernel<false, 128>)
                               : (w ? many_kernel<true, 64> : many_kernel<false, 64>);
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)

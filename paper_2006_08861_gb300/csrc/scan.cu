@@ -901,7 +901,7 @@ cudaError_t scan_pass(const lhr_db* db, const ScanSrc& src, const char* label, c
 }  // namespace
 
 size_t scan_scratch_bytes(const lhr_db* db, int nq, int k, bool pilot) {
-    if (pilot && use_pilot(db, nq) && many_eligible(db, nq, k)) return pilot_bytes(db, nq) + many_scratch_bytes(nq);
+    if (pilot && use_pilot(db, nq) && many_eligible(db, nq, k)) return pilot_bytes(db, nq) + many_scratch_bytes(db, nq);
     const ScanConfig c = choose_config(db, nq);
     const size_t main = pass_bytes(c, db->nchunks, db->n_sub, nq, k);
     return pilot && use_pilot(db, nq) ? main + pilot_bytes(db, nq) : main;

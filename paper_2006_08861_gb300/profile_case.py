@@ -7,7 +7,9 @@ database, Q frames near database rows), "hier" (lhr_query_window: one window
 of 5 frames on the 100,000 x 256 building-scale database, coarse prefix 32,
 shortlist 512, k = 20), "lowp" (tensor-core lhr_query, Q frames, BF16/FP8
 copies, re-rank width 64), "weighted" (lhr_query_weighted, Q frames, unit
-weights). --time prints each kernel's mean device time (event pairs).
+weights), "soft" (the soft-retrieval selection: lhr_query_weighted with unit
+weights for 256 windows x 5 frames, k = 32, on the 200,000 x 256 synthetic
+floor-plan database). --time prints each kernel's mean device time (event pairs).
 """
 import argparse
 import os
@@ -18,7 +20,7 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("case", choices=["scan", "hier", "lowp", "weighted"])
+    ap.add_argument("case", choices=["scan", "hier", "lowp", "weighted", "soft"])
     ap.add_argument("--n", type=int, default=500_000)
     ap.add_argument("--dim", type=int, default=256)
     ap.add_argument("--nq", type=int, default=8)
@@ -41,6 +43,15 @@ def main(argv=None):
         ft = torch.from_numpy(w.frames).to(dev)
         offs = torch.from_numpy(w.offsets).to(dev)
         call = lambda: lhr.lhr_query_window(h, ft, offs, 20, shortlist=512)
+    elif a.case == "soft":
+        import synth
+        c = synth.CONFIGS["differentiation"]
+        db = synth.make_database(c["n"], c["dim"], seed=synth.db_seed(c["index"]))
+        w = synth.make_windows(db, c["nw"], c["m"], seed=synth.query_seed(c["index"]))
+        h = lhr.lhr_build_db(db.feats, db.xy)
+        ft = torch.from_numpy(w.frames).to(dev)
+        wt = torch.ones(c["dim"], device=dev)
+        call = lambda: lhr.lhr_query_weighted(h, ft, c["k"], wt)
     else:
         X = rng.standard_normal((a.n, a.dim), dtype=np.float32)
         h = lhr.lhr_build_db(X, np.zeros((a.n, 2)), lowp=3 if a.case == "lowp" else 0)
@@ -61,10 +72,11 @@ def main(argv=None):
             call()
         torch.cuda.synchronize()
         lhr.lhr_profile_enable(False)
-        for name in ("hier_fused", "scan_pilot", "wnorm", "scan_topk", "many_bound", "many_kernel", "many_select",
+        for name in ("hier_fused", "scan_pilot", "wnorm", "scan_topk", "many_bound", "tf32_prep", "sort_queries",
+                     "tf32_many", "many_kernel", "many_select",
                      "small_topk", "coarse_kernel", "collect", "shortlist",
                      "aggregate", "quantize", "tc_pilot", "tau_kernel", "tc_main", "tc_full", "merge_rerank"):
-            n, ms = lhr.lhr_profile_read(name)
+            n, ms = lhr.lhr_profile_read(name, reset=True)
             if n:
                 print(f"{a.case} {name}: {n} launches, mean {ms / n * 1e3:.1f} us")
     err = lhr.lhr_db_error(h)

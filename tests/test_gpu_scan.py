@@ -239,6 +239,35 @@ def test_many_frames_exact_ties(lhr):
     assert np.array_equal(gd.astype(np.float64), o_dist)
 
 
+@pytest.mark.parametrize("n,dim,nq,k,weighted", [
+    (100_003, 256, 300, 32, False),  # 8 K slices, three frame blocks of 128 and a padded fourth
+    (70_001, 192, 257, 10, True),    # 6 K slices, weighted, one frame past a 256-frame sort unit
+    (66_000, 64, 64, 1, False),      # 2 K slices, a single frame block, k = 1
+])
+def test_many_frames_tensor_core_filter(lhr, n, dim, nq, k, weighted):
+    # many frames go through the TF32 tensor-core filter; frames with very
+    # different thresholds (noise 0.01 .. 3) share 32-frame groups only after
+    # the threshold sort, so an unsorted or wrong group bound loses rows here
+    rng = np.random.default_rng(n + nq)
+    X = rng.standard_normal((n, dim)).astype(np.float32)
+    noise = np.exp(rng.uniform(np.log(0.01), np.log(3.0), nq)).astype(np.float32)[:, None]
+    Q = (X[rng.integers(0, n, nq)] + noise * rng.standard_normal((nq, dim))).astype(np.float32)
+    if weighted:
+        w = rng.uniform(0.5, 1.5, dim).astype(np.float32)
+        db = lhr.lhr_build_db(X, np.zeros((n, 2)))
+        gi, gd = lhr.lhr_query_weighted(db, torch.from_numpy(Q).cuda(), k, torch.from_numpy(w).cuda())
+        torch.cuda.synchronize()
+        assert lhr.lhr_db_error(db) == 0
+        gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+        oi, od = oret.exhaustive_topk(Q, X, k + 1, w=w)
+        exact = sum(check_list(Q[qi], X, gi[qi, 0], gd[qi, 0], oi[qi, 0], od[qi, 0], k, where=f"q{qi}", w=w)
+                    for qi in range(nq))
+    else:
+        _, gi, gd = _run(lhr, X, Q, k)
+        exact = _compare(X, Q, k, gi, gd)
+    assert exact >= nq * k // 2  # ranks separated from both neighbours, compared bit-exactly
+
+
 def test_pilot_and_plain_scan_agree(lhr):
     # lhr_query seeds from the pilot; lhr_query_static never does
     rng = np.random.default_rng(44)
