@@ -189,7 +189,8 @@ KERNELS = ("quantize_queries_kernel", "tc_pilot_kernel_fp8", "tc_pilot_kernel_bf
            "tc_main_kernel_fp8", "tc_main_kernel_bf16", "tc_full_kernel_fp8", "tc_full_kernel_bf16",
            "merge_rerank_kernel", "scan_pilot", "scan_topk_kernel", "small_topk_kernel", "aggregate_kernel",
            "hier_fused_kernel", "coarse_kernel", "collect_kernel", "shortlist_kernel", "wnorm_kernel",
-           "many_bound_kernel", "many_select_kernel", "tf32_many_kernel", "tf32_prep_kernel", "many_kernel",
+           "many_bound_kernel", "many_select_kernel", "tf32_many_kernel", "tf32_pilot_kernel", "tf32_prep_kernel",
+           "many_kernel",
            "soft_forward_kernel",
            "soft_backward_kernel")
 

@@ -103,9 +103,12 @@ struct ProfScope {
 // `pilot`: seed the scan's thresholds from the pilot sample when the database
 // has one (same results, fewer exact recomputes; more scratch).
 size_t scan_scratch_bytes(const lhr_db* db, int nq, int k, bool pilot);
-// many.cu: exhaustive top k for many frames at once (register-tiled expanded
-// form over the pilot's bound, exact re-score of the candidates)
+// many.cu: exhaustive top k for many frames at once (the expanded form over a
+// pilot's bound, exact re-score of the candidates). many_tf32: the filter and
+// its pilot run on the tensor cores (launch_many takes bmin = nullptr);
+// otherwise the FP32 register-tiled form over the scan pilot's bmin.
 bool many_eligible(const lhr_db* db, int nq, int k);
+bool many_tf32(const lhr_db* db);
 size_t many_scratch_bytes(const lhr_db* db, int nq);
 cudaError_t launch_many(const lhr_db* db, const float* q, int nq, int k, const float* w, const float* xn,
                         const float* xmax_w, const unsigned* bmin, float margin_scale, int64_t* idx, float* dist,

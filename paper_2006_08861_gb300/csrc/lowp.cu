@@ -506,23 +506,6 @@ __device__ __forceinline__ void main_survivors(const MainParams& p, const uint32
 // so a TMEM lane -- an epilogue thread -- is a database row and a column is a
 // query. Two 256-column FP32 accumulators fill TMEM; the tensor core works on
 // one tile while the epilogue reads the other.
-// Minimum over the warp's 32 rows of each of a group's 32 columns: a
-// butterfly in which every step exchanges half of the remaining columns with
-// the partner lane; lane l ends with column l's minimum.
-__device__ __forceinline__ float column_min32(float (&c)[32], int lane) {
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-        const bool upper = (lane & s) != 0;
-#pragma unroll
-        for (int i = 0; i < s; ++i) {
-            const float send = upper ? c[i] : c[i + s];
-            const float keep = upper ? c[i + s] : c[i];
-            c[i] = fminf(keep, __shfl_xor_sync(kFull, send, s));
-        }
-    }
-    return c[0];
-}
-
 // Sorted register network of kPilotR scores (static indices only).
 __device__ __forceinline__ void fnet_insert(float (&net)[kPilotR], float x) {
     if (!(x < net[kPilotR - 1])) return;

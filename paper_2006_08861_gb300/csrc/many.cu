@@ -63,6 +63,11 @@ struct ManyParams {
     float* mg;            // nq: margin
     unsigned* cnt;        // nq: candidates seen
     u64* cand;            // nq x kMCap
+    // Tensor-core form: the bucket minima are TF32 scores (each within the margin
+    // of its row's exact distance), so the bound adds one margin; fT (nullable)
+    // receives thr - qn + slack, the threshold on ||x||_w^2 - 2 (w q) . x.
+    bool bmin_scored;
+    float* fT;
     const int32_t* perm;  // internal row -> caller row, nullable
     int64_t* idx;
     float* dist;
@@ -115,12 +120,22 @@ __global__ void many_bound_kernel(ManyParams p) {
     for (int o = 16; o > 0; o >>= 1) b = min(b, __shfl_xor_sync(kFull, b, o));
     if (lane == 0) {
         const float inf = __int_as_float(0x7f800000);
-        const float bound = b < 0x7f800000u ? __uint_as_float(b) * (1.0f + 1.0f / 4096.0f) : inf;
-        const float rad = (p.xmax_w != nullptr ? sqrtf(__ldg(p.xmax_w)) * 1.0001f : p.xmax) + sqrtf(a);
+        const float xnmax = p.xmax_w != nullptr ? __ldg(p.xmax_w) : p.xmax * p.xmax;
+        const float rad = (p.xmax_w != nullptr ? sqrtf(xnmax) * 1.0001f : p.xmax) + sqrtf(a);
         const float margin = p.margin_scale * rad * rad;
+        float bound = b < 0x7f800000u ? __uint_as_float(b) * (1.0f + 1.0f / 4096.0f) : inf;
+        if (p.bmin_scored) bound += margin;
+        const float thr = bound + margin;
         p.qn[f] = a;
         p.mg[f] = margin;
-        p.thr[f] = bound + margin;
+        p.thr[f] = thr;
+        if (p.fT != nullptr) {
+            // the pass tests u = fl(||x||_w^2 - 2 (w q) . x) <= fT and keys e = fl(u + qn): a pair
+            // with e <= thr has u <= thr - qn up to three roundings of magnitude at most
+            // |thr| + |qn| + max ||x||_w^2 each; the slack is four units in the last place of that
+            const float slack = 4.0f * 5.9604645e-08f * (fabsf(thr) + a + xnmax);
+            p.fT[f] = (thr - a) + slack;
+        }
     }
 }
 
@@ -377,15 +392,23 @@ __global__ void many_select_kernel(ManyParams p) {
 }
 
 // ------------------------------------------------------------------ TF32 tensor-core pass
-// The filter of many_kernel on the tensor cores: u(f, r) = -2 (w q_f) . x_r + ||x_r||_w^2
-// by tcgen05.mma kind::tf32 (operands truncated to TF32, FP32 accumulate) over
-// M = 128 rows x N = 128 frames tiles, one CTA per (128-frame block, row chunk).
-// The frames come in ascending order of their filter bound (thr_f - qn_f), so a
-// 32-frame group has a tight bound: its largest. A row's smallest u over a
-// group is fma(-2, max dot, ||x_r||_w^2); rows under the group bound go through
-// the warp's transpose buffer and lane l checks frame l exactly as many_kernel
-// does: e = fma(-2, dot, ||x_r||_w^2 + ||q_f||_w^2) <= thr_f. The margin in thr_f
-// and in many_select_kernel covers TF32 operands (many_bound_kernel).
+// The filter of many_kernel on the tensor cores: u(f, r) = ||x_r||_w^2 - 2 (w q_f) . x_r
+// with the dot by tcgen05.mma kind::tf32 (operands truncated to TF32, FP32
+// accumulation) over 128-row x 128-frame tiles, one CTA per (128-frame block,
+// row chunk): database rows stream through a TMA ring, the block's w q rows stay
+// in shared memory, accumulators rotate through TMEM. The epilogue thread of a
+// row tests its 64 frames exactly, u <= fT_f (fT_f = thr_f - ||q_f||_w^2 +
+// slack, held in registers), with a three-input minimum over the 64 differences
+// deciding whether any passes; the passing pairs are keyed (orderable e = u +
+// ||q_f||_w^2, row) into a per-frame stage in shared memory and appended to the
+// frames' buffers at the end, one atomic per frame.
+//
+// kPilot: the same pipeline over every kTfPilotStride-th row (a strided tensor
+// map, no copy) writes bucket minima instead: per warp (32 sample rows) and
+// frame the smallest e (column_min32), clamped at 0, into bucket
+// (sample row / 32) mod 128 by atomic minimum. Minima of distinct buckets are
+// distinct rows, each within the margin of its exact distance, so the k-th
+// smallest plus one margin bounds the frame's k-th exact distance.
 using namespace tc;
 constexpr int kFT = 128;                 // frames per CTA (UMMA N)
 constexpr int kFAcc = 4;                 // 128-column FP32 accumulators (all of TMEM)
@@ -393,67 +416,72 @@ constexpr int kFEpiWarps = 8;            // two per TMEM lane quadrant, 64 colum
 constexpr int kFEpiThreads = 32 * kFEpiWarps;
 constexpr int kFThreads = 64 + kFEpiThreads;
 constexpr int kFMaxStages = 8;
-constexpr int kFOwn = 4;                 // staged keys per owned frame
-constexpr int kFTRows = 8;               // rows a warp moves through its transpose buffer at a time
-constexpr int kFTStride = 36;            // floats per buffered row: 32 values, then (xn, -, row, -)
+constexpr int kFStage = 32;              // staged candidates per frame of the CTA
 constexpr int kFSlice = kFT * kTcSliceBytes;  // 16 KB: one 128-byte K slice of 128 rows
+constexpr int kTfPilotStride = 8;        // pilot sample: every 8th row
 
 struct TfParams {
-    int64_t n;
+    int64_t n;            // rows of this pass (sample rows for the pilot)
     int slices, stages;
     int64_t chunk_rows;
-    int nchunks;
-    const float* xn;      // per row ||x||_w^2 (n values)
-    const int* fperm;     // per sorted position: the frame there, -1 = padding
-    const float* gbound;  // per 32 sorted positions: the largest (thr_f - qn_f) + slack
-    const float* thr;     // per frame: filter threshold on e
+    int64_t xn_stride;    // pass row r has norm xn[r * xn_stride]
+    const float* xn;      // ||x||_w^2 per database row
+    const float* fT;      // per frame: threshold on u (main pass)
     const float* qn;      // per frame: ||q||_w^2
     unsigned* cnt;        // per frame: candidates seen
     u64* cand;            // per frame: kMCap candidate keys (orderable e, row)
+    unsigned* bmin;       // pilot: per frame kMBuckets bucket minima (float bits)
     int nq;
     int* err;
 };
 
-__device__ __forceinline__ void tf_flush(const TfParams& p, const u64* slot, int f, int n) {
-    const unsigned pos = atomicAdd(p.cnt + f, (unsigned)n);
-    for (int i = 0; i < n; ++i)
-        if (pos + i < (unsigned)kMCap) p.cand[(size_t)f * kMCap + pos + i] = slot[i * kFEpiThreads];
-}
-
-// Rows of `ev` through the transpose buffer; lane l checks frame f_own (column l).
-__device__ __forceinline__ void tf_survivors(const TfParams& p, const uint32_t (&v)[32], float xn, uint32_t row,
-                                             unsigned ev, int lane, float* tbuf, u64* slot, int f_own, float thr_own,
-                                             float qn_own, int& n_own) {
-    const unsigned lt = (1u << lane) - 1u;
-    while (ev) {
-        const unsigned sel = __ballot_sync(kFull, ((ev >> lane) & 1u) && __popc(ev & lt) < kFTRows);
-        if ((sel >> lane) & 1u) {
-            float4* dst = reinterpret_cast<float4*>(tbuf + __popc(sel & lt) * kFTStride);
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
-                                     __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
-            dst[8] = make_float4(xn, 0.f, __uint_as_float(row), 0.f);
-        }
-        __syncwarp();
-        const int nsel = __popc(sel);
-        for (int r = 0; r < nsel; ++r) {
-            const float x = tbuf[r * kFTStride + lane];
-            const float4 mt = *reinterpret_cast<const float4*>(tbuf + r * kFTStride + 32);
-            const float e = fmaf(-2.f, x, mt.x + qn_own);
-            if (f_own >= 0 && e <= thr_own) {
-                slot[n_own * kFEpiThreads] = orderable_key(e, __float_as_uint(mt.z));
-                if (++n_own == kFOwn) {
-                    tf_flush(p, slot, f_own, n_own);
-                    n_own = 0;
-                }
-            }
-        }
-        __syncwarp();
-        ev &= ~sel;
+// Appends key to frame column col's stage (the frame's buffer when the stage is full).
+__device__ __forceinline__ void tf_emit(const TfParams& p, unsigned* scnt, u64* stage, int col, int f, u64 key) {
+    const unsigned slot = atomicAdd(&scnt[col], 1u);
+    if (slot < (unsigned)kFStage) {
+        stage[col * kFStage + slot] = key;
+    } else {
+        const unsigned pos = atomicAdd(p.cnt + f, 1u);
+        if (pos < (unsigned)kMCap) p.cand[(size_t)f * kMCap + pos] = key;
     }
 }
 
+// Exact test of one row against a group of 32 frames (columns col0 + j), the
+// passing pairs keyed. Called only when some difference u - fT is <= 0.
+__device__ __forceinline__ void tf_pass32(const TfParams& p, const uint32_t (&v)[32], const float (&T)[32], float xn,
+                                          uint32_t row, int col0, int fbase, const float* sqn, unsigned* scnt,
+                                          u64* stage) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const float u = fmaf(-2.f, __uint_as_float(v[j]), xn);
+        if (u <= T[j]) tf_emit(p, scnt, stage, col0 + j, fbase + col0 + j, orderable_key(u + sqn[col0 + j], row));
+    }
+}
+
+// min over j of (fl(xn - 2 v_j) - T_j): <= 0 exactly when some u_j <= T_j.
+__device__ __forceinline__ float tf_min_diff(const uint32_t (&v)[32], const float (&T)[32], float xn) {
+    float m = fmaf(-2.f, __uint_as_float(v[0]), xn) - T[0];
+#pragma unroll
+    for (int j = 1; j < 31; j += 2)
+        m = fmin3(m, fmaf(-2.f, __uint_as_float(v[j]), xn) - T[j], fmaf(-2.f, __uint_as_float(v[j + 1]), xn) - T[j + 1]);
+    return fminf(m, fmaf(-2.f, __uint_as_float(v[31]), xn) - T[31]);
+}
+
+// Pilot: column minima of e over the warp's 32 rows into the frames' bucket.
+__device__ __forceinline__ void tf_pilot32(const TfParams& p, const uint32_t (&v)[32], float xn, bool rowvalid,
+                                           int col, int f, const float* sqn, int bucket, int lane) {
+    float c[32];
+    const float inf = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) c[j] = rowvalid ? fmaf(-2.f, __uint_as_float(v[j]), xn) : inf;
+    const float mn = column_min32(c, lane);
+    if (f < p.nq && mn < inf) {
+        const float e = fmaxf(mn + sqn[col], 0.f);
+        atomicMin(p.bmin + (size_t)f * kMBuckets + bucket, __float_as_uint(e));
+    }
+}
+
+template <bool kPilot>
 __global__ void __launch_bounds__(kFThreads, 1)
     tf32_many_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmX, const TfParams p) {
     extern __shared__ unsigned char smem_raw[];
@@ -464,19 +492,21 @@ __global__ void __launch_bounds__(kFThreads, 1)
     const int stages = p.stages;
     unsigned char* sQ = smem;                                    // slices x 16 KB: the block's frames (w q)
     unsigned char* sX = sQ + (size_t)p.slices * kFSlice;         // stages x 16 KB: database slices
-    u64* own_slot = reinterpret_cast<u64*>(sX + (size_t)stages * kFSlice);  // 2 kFOwn x threads
-    float* tbuf_all = reinterpret_cast<float*>(own_slot + 2 * kFOwn * kFEpiThreads);
-    u64* full = reinterpret_cast<u64*>(tbuf_all + kFEpiWarps * kFTRows * kFTStride);
+    float* sqn = reinterpret_cast<float*>(sX + (size_t)stages * kFSlice);  // kFT: ||q||_w^2 per column
+    unsigned* scnt = reinterpret_cast<unsigned*>(sqn + kFT);               // kFT: staged keys per column
+    u64* full = reinterpret_cast<u64*>(scnt + kFT);
     u64* empty = full + kFMaxStages;
     u64* q_full = empty + kFMaxStages;
     u64* acc_full = q_full + 1;
     u64* acc_empty = acc_full + kFAcc;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + kFAcc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+    u64* stage = reinterpret_cast<u64*>(tmem_holder + 4);       // main pass: kFT x kFStage keys
 
     const int64_t row0 = (int64_t)chunk * p.chunk_rows;
     const int64_t row1 = min(p.n, row0 + p.chunk_rows);
     const int ntiles = row1 > row0 ? (int)((row1 - row0 + kTcM - 1) / kTcM) : 0;
+    const int fbase = fblock * kFT;
     constexpr int kElemPerSlice = kTcSliceBytes / 4;  // 32 floats
     constexpr int kMmaK = 8;                          // TF32 elements per MMA (32 bytes)
     constexpr int kMmaPerSlice = kElemPerSlice / kMmaK;
@@ -495,6 +525,10 @@ __global__ void __launch_bounds__(kFThreads, 1)
         *abort_flag = 0;
         fence_mbar_init();
     }
+    for (int c = threadIdx.x; c < kFT; c += kFThreads) {
+        sqn[c] = fbase + c < p.nq ? __ldg(p.qn + fbase + c) : 0.f;
+        scnt[c] = 0u;
+    }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
                      "r"(kFAcc * kFT)
@@ -510,7 +544,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
         if (lane == 0) {
             mbar_arrive_expect_tx(q_full, (uint32_t)p.slices * kFSlice);
             for (int s = 0; s < p.slices; ++s)
-                tma_load_2d(sQ + (size_t)s * kFSlice, &tmQ, s * kElemPerSlice, fblock * kFT, q_full);
+                tma_load_2d(sQ + (size_t)s * kFSlice, &tmQ, s * kElemPerSlice, fbase, q_full);
             int b_issued = 0, st = 0;
             uint32_t ph = 0;
             for (int t = 0; t < ntiles && !*abort_flag; ++t) {
@@ -581,25 +615,24 @@ __global__ void __launch_bounds__(kFThreads, 1)
     } else {
         // ------------------------------------------------ epilogue: thread = database row
         const int ew = warp - 2;
-        const int quad = warp & 3;
+        const int quad = warp & 3;                            // TMEM lanes 32 quad .. 32 quad + 31
         const int rl = quad * 32 + lane;
         const int cb = (ew / 4) * 64;                         // first column (frame) of this warp's half
-        const int64_t p0 = (int64_t)fblock * kFT + cb;        // its sorted position
-        float* tbuf = tbuf_all + ew * kFTRows * kFTStride;
-        const int et = threadIdx.x - 64;
-        u64* slot0 = own_slot + et;
-        u64* slot1 = slot0 + kFOwn * kFEpiThreads;
-        const float G0 = __ldg(p.gbound + p0 / 32), G1 = __ldg(p.gbound + p0 / 32 + 1);
-        const int f0 = __ldg(p.fperm + p0 + lane), f1 = __ldg(p.fperm + p0 + 32 + lane);
         const float ninf = -__int_as_float(0x7f800000);
-        const float thr0 = f0 >= 0 ? __ldg(p.thr + f0) : ninf, thr1 = f1 >= 0 ? __ldg(p.thr + f1) : ninf;
-        const float qn0 = f0 >= 0 ? __ldg(p.qn + f0) : 0.f, qn1 = f1 >= 0 ? __ldg(p.qn + f1) : 0.f;
-        int n0 = 0, n1 = 0;
+        float T0[32], T1[32];                                 // per column: the frame's threshold on u
+        if (!kPilot) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int f0 = fbase + cb + j, f1 = f0 + 32;
+                T0[j] = f0 < p.nq ? __ldg(p.fT + f0) : ninf;
+                T1[j] = f1 < p.nq ? __ldg(p.fT + f1) : ninf;
+            }
+        }
         for (int t = 0; t < ntiles; ++t) {
             const int a = t % kFAcc;
             const int64_t row = row0 + (int64_t)t * kTcM + rl;
             const bool rowvalid = row < row1;
-            const float xn = rowvalid ? __ldg(p.xn + row) : 0.f;
+            const float xn = rowvalid ? __ldg(p.xn + row * p.xn_stride) : 0.f;
             if (!mbar_wait(&acc_full[a], (uint32_t)((t / kFAcc) & 1), abort_flag)) {
                 if (lane == 0) {
                     *abort_flag = 1;
@@ -617,49 +650,60 @@ __global__ void __launch_bounds__(kFThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[a]);
-            const unsigned ev0 = __ballot_sync(kFull, rowvalid && fmaf(-2.f, max32(va), xn) <= G0);
-            if (ev0) tf_survivors(p, va, xn, (uint32_t)row, ev0, lane, tbuf, slot0, f0, thr0, qn0, n0);
-            const unsigned ev1 = __ballot_sync(kFull, rowvalid && fmaf(-2.f, max32(vb), xn) <= G1);
-            if (ev1) tf_survivors(p, vb, xn, (uint32_t)row, ev1, lane, tbuf, slot1, f1, thr1, qn1, n1);
+            if (kPilot) {
+                const int bucket = (int)(((row0 + (int64_t)t * kTcM + quad * 32) >> 5) & (kMBuckets - 1));
+                tf_pilot32(p, va, xn, rowvalid, cb + lane, fbase + cb + lane, sqn, bucket, lane);
+                tf_pilot32(p, vb, xn, rowvalid, cb + 32 + lane, fbase + cb + 32 + lane, sqn, bucket, lane);
+            } else if (rowvalid) {
+                if (tf_min_diff(va, T0, xn) <= 0.f) tf_pass32(p, va, T0, xn, (uint32_t)row, cb, fbase, sqn, scnt, stage);
+                if (tf_min_diff(vb, T1, xn) <= 0.f)
+                    tf_pass32(p, vb, T1, xn, (uint32_t)row, cb + 32, fbase, sqn, scnt, stage);
+            }
         }
-        if (n0) tf_flush(p, slot0, f0, n0);
-        if (n1) tf_flush(p, slot1, f1, n1);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kFAcc * kFT) : "memory");
+    if (!kPilot) {
+        // the stages to the frames' buffers: one atomic per frame
+        for (int c = threadIdx.x; c < kFT; c += kFThreads) {
+            const int f = fbase + c;
+            const unsigned n = min(scnt[c], (unsigned)kFStage);
+            if (f < p.nq && n > 0) {
+                const unsigned pos = atomicAdd(p.cnt + f, n);
+                for (unsigned i = 0; i < n; ++i)
+                    if (pos + i < (unsigned)kMCap) p.cand[(size_t)f * kMCap + pos + i] = stage[c * kFStage + i];
+            }
+        }
+    }
 }
 
-// Per frame: w q (the B operand rows) and the filter's sort key thr_f - qn_f, raised by a
-// rounding slack so the group test fma(-2, dot, ||x||_w^2) <= bound never rejects a pair the
-// frame's own test e <= thr_f keeps.
-__global__ void tf32_prep_kernel(const float* Q, const float* w, int nq, int D, const float* thr, const float* qn,
-                                 const float* xnmax_w, float xnmax, float* wq, float* fkey) {
+// Per frame (one warp): the B operand row w q and ||q||_w^2 (summed as many_bound_kernel does).
+__global__ void tf32_prep_kernel(const float* Q, const float* w, int nq, int D, float* wq, float* qn) {
     const int lane = threadIdx.x & 31;
     const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (f >= nq) return;
+    float a = 0.f;
     for (int d = lane; d < D; d += 32) {
         const float q = Q[(size_t)f * D + d];
-        wq[(size_t)f * D + d] = w ? w[d] * q : q;
+        const float v = w ? w[d] * q : q;
+        wq[(size_t)f * D + d] = v;
+        a = fmaf(v, q, a);
     }
-    if (lane == 0) {
-        const float t = thr[f], qv = qn[f];
-        if (xnmax_w != nullptr) xnmax = __ldg(xnmax_w);
-        const float slack = 4.0f * 5.9604645e-08f * (fabsf(t) + fabsf(qv) + xnmax);  // 4 units in the last place
-        fkey[f] = (t - qv) + slack;
-    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
+    if (lane == 0) qn[f] = a;
 }
 
-size_t tf32_smem(int slices, int stages) {
-    return 1024 + (size_t)(slices + stages) * kFSlice + (size_t)2 * kFOwn * kFEpiThreads * sizeof(u64) +
-           (size_t)kFEpiWarps * kFTRows * kFTStride * sizeof(float) + (2 * kFMaxStages + 1 + 2 * kFAcc) * sizeof(u64) +
-           16;
+size_t tf32_smem(int slices, int stages, bool pilot) {
+    return 1024 + (size_t)(slices + stages) * kFSlice + 2 * kFT * sizeof(float) +
+           (2 * kFMaxStages + 1 + 2 * kFAcc) * sizeof(u64) + 16 + (pilot ? 0 : (size_t)kFT * kFStage * sizeof(u64));
 }
 
-int tf32_stages(int slices) {
-    const size_t fixed = tf32_smem(slices, 0);
+int tf32_stages(int slices, bool pilot) {
+    const size_t fixed = tf32_smem(slices, 0, pilot);
     const size_t lim = 227 * 1024;
     const int fit = fixed < lim ? (int)((lim - fixed) / kFSlice) : 0;
     return std::min(kFMaxStages, fit);
@@ -686,31 +730,49 @@ bool many_eligible(const lhr_db* db, int nq, int k) {
 
 // The TF32 pass serves whole 32-float K slices of at most 256 dimensions and row
 // indices that fit the candidate keys.
-bool tf32_eligible(const lhr_db* db) { return db->dim % 32 == 0 && db->dim <= 256 && db->n < (int64_t)1 << 31; }
+// The tensor-core form serves whole 32-float K slices of at most 256
+// dimensions and row indices that fit the candidate keys.
+bool many_tf32(const lhr_db* db) { return db->dim % 32 == 0 && db->dim <= 256 && db->n < (int64_t)1 << 31; }
 
-int tf32_sorted(int nq) { return (nq + 255) / 256 * 256; }
+namespace {
 
-size_t many_scratch_bytes(const lhr_db* db, int nq) {
-    size_t b = 3 * a256((size_t)nq * sizeof(float)) + a256((size_t)nq * sizeof(unsigned)) +
-               a256((size_t)nq * kMCap * sizeof(u64));
-    if (tf32_eligible(db)) {
-        const size_t ns = (size_t)tf32_sorted(nq);
-        b += a256((size_t)nq * sizeof(float)) + a256((size_t)nq * db->dim * sizeof(float)) +
-             a256(ns * db->dim * sizeof(float)) + a256(ns * sizeof(int)) + a256(ns / 32 * sizeof(float));
+struct TfLayout {
+    size_t thr, qn, mg, cnt, cand, fT, wq, bmin, total;
+};
+
+TfLayout many_layout(const lhr_db* db, int nq) {
+    TfLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t r = off;
+        off += a256(bytes);
+        return r;
+    };
+    L.thr = take((size_t)nq * sizeof(float));
+    L.qn = take((size_t)nq * sizeof(float));
+    L.mg = take((size_t)nq * sizeof(float));
+    L.cnt = take((size_t)nq * sizeof(unsigned));
+    L.cand = take((size_t)nq * kMCap * sizeof(u64));
+    if (many_tf32(db)) {
+        L.fT = take((size_t)nq * sizeof(float));
+        L.wq = take((size_t)nq * db->dim * sizeof(float));
+        L.bmin = take((size_t)nq * kMBuckets * sizeof(unsigned));
     }
-    return b;
+    L.total = off;
+    return L;
 }
 
 // Row chunks per frame block so that the CTAs fill whole waves of the SMs as
-// far as possible (CTAs x rows per CTA, in waves).
+// far as possible (waves x tiles per CTA, plus a per-CTA fixed cost of about
+// two tiles: the frames' operand and the pipeline's fill).
 int tf32_chunks(int nfb, int sms, int64_t n) {
     const int64_t tiles = (n + kTcM - 1) / kTcM;
     int best = 1;
     double best_cost = 1e300;
-    for (int c = 1; c <= 4 * sms && c <= tiles && (int64_t)c * nfb <= 65535; ++c) {
-        const int64_t rows = (tiles + c - 1) / c;  // tiles per chunk
+    for (int c = 1; c <= 4 * sms && c <= tiles; ++c) {
+        const int64_t per = (tiles + c - 1) / c;
         const int64_t waves = ((int64_t)c * nfb + sms - 1) / sms;
-        const double cost = (double)waves * (double)(rows + 2);  // + per-CTA fixed cost, about two tiles
+        const double cost = (double)waves * (double)(per + 2);
         if (cost < best_cost) {
             best_cost = cost;
             best = c;
@@ -719,10 +781,48 @@ int tf32_chunks(int nfb, int sms, int64_t n) {
     return best;
 }
 
+// One TF32 pass (pilot over every kTfPilotStride-th row, or the main pass)
+// over the frames' w q rows.
+template <bool kPilot>
+cudaError_t tf32_pass(const lhr_db* db, const float* wq, int nq, TfParams t, cudaStream_t stream) {
+    const int D = db->dim;
+    const int64_t stride = kPilot ? kTfPilotStride : 1;
+    t.n = (db->n + stride - 1) / stride;
+    t.xn_stride = stride;
+    CUtensorMap tmQ, tmX;
+    if (!make_map(&tmQ, wq, nq, D, kTcTF32, kFT) || !make_map(&tmX, db->X, t.n, D, kTcTF32, kTcM, stride * D))
+        return cudaErrorInvalidValue;
+    t.slices = D / 32;
+    t.stages = tf32_stages(t.slices, kPilot);
+    if (t.stages < 2) return cudaErrorInvalidValue;
+    const int nfb = (nq + kFT - 1) / kFT;
+    if (nfb > 65535) return cudaErrorInvalidValue;
+    const int nchunks = tf32_chunks(nfb, db->sms, t.n);
+    const int64_t cr = (t.n + nchunks - 1) / nchunks;
+    t.chunk_rows = (cr + kTcM - 1) / kTcM * kTcM;
+    const int grid_x = (int)((t.n + t.chunk_rows - 1) / t.chunk_rows);
+    const size_t sm = tf32_smem(t.slices, t.stages, kPilot);
+    cudaError_t e =
+        cudaFuncSetAttribute(tf32_many_kernel<kPilot>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    ProfScope ps(kPilot ? "tf32_pilot_kernel" : "tf32_many_kernel", stream);
+    tf32_many_kernel<kPilot><<<dim3(grid_x, nfb), kFThreads, sm, stream>>>(tmQ, tmX, t);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t many_scratch_bytes(const lhr_db* db, int nq) { return many_layout(db, nq).total; }
+
+// bmin: the pilot's bucket minima for the FP32 register-tiled form; the
+// tensor-core form (many_tf32) runs its own pilot and takes nullptr.
 cudaError_t launch_many(const lhr_db* db, const float* q, int nq, int k, const float* w, const float* xn,
                         const float* xmax_w, const unsigned* bmin, float margin_scale, int64_t* idx, float* dist,
                         void* scratch, cudaStream_t stream) {
-    const bool tf32 = tf32_eligible(db);
+    const bool tf32 = many_tf32(db);
+    if (!tf32 && bmin == nullptr) return cudaErrorInvalidValue;
+    const TfLayout L = many_layout(db, nq);
+    unsigned char* base = reinterpret_cast<unsigned char*>(scratch);
     ManyParams p{};
     p.X = db->X;
     p.xn = xn;
@@ -732,7 +832,7 @@ cudaError_t launch_many(const lhr_db* db, const float* q, int nq, int k, const f
     p.w = w;
     p.nq = nq;
     p.k = k;
-    p.bmin = bmin;
+    p.bmin = tf32 ? reinterpret_cast<unsigned*>(base + L.bmin) : bmin;
     // TF32 operands (10 stored mantissa bits, truncated or rounded): each product
     // w q_d x_d is off by less than (2^-9 + 2^-20) of its magnitude, so 2 |dot
     // error| <= (2^-9 + 2^-20) 2 ||q||_w ||x||_w <= (2^-10 + 2^-21) rad^2; the FP32
@@ -740,75 +840,48 @@ cudaError_t launch_many(const lhr_db* db, const float* q, int nq, int k, const f
     p.margin_scale = tf32 ? 2.f * margin_scale + 1.0f / 1024.f * 1.001f : margin_scale;
     p.xmax = (float)(sqrt((double)db->xnorm_max) * 1.0001);
     p.xmax_w = xmax_w;
-    unsigned char* base = reinterpret_cast<unsigned char*>(scratch);
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-        unsigned char* r = base + off;
-        off += a256(bytes);
-        return r;
-    };
-    p.thr = reinterpret_cast<float*>(take((size_t)nq * sizeof(float)));
-    p.qn = reinterpret_cast<float*>(take((size_t)nq * sizeof(float)));
-    p.mg = reinterpret_cast<float*>(take((size_t)nq * sizeof(float)));
-    p.cnt = reinterpret_cast<unsigned*>(take((size_t)nq * sizeof(unsigned)));
-    p.cand = reinterpret_cast<u64*>(take((size_t)nq * kMCap * sizeof(u64)));
+    p.thr = reinterpret_cast<float*>(base + L.thr);
+    p.qn = reinterpret_cast<float*>(base + L.qn);
+    p.mg = reinterpret_cast<float*>(base + L.mg);
+    p.cnt = reinterpret_cast<unsigned*>(base + L.cnt);
+    p.cand = reinterpret_cast<u64*>(base + L.cand);
+    p.bmin_scored = tf32;
+    p.fT = tf32 ? reinterpret_cast<float*>(base + L.fT) : nullptr;
     p.perm = db->perm;
     p.idx = idx;
     p.dist = dist;
     p.err = db->err;
     cudaError_t e = cudaMemsetAsync(p.cnt, 0, (size_t)nq * sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
+    TfParams t{};
+    float* wq = tf32 ? reinterpret_cast<float*>(base + L.wq) : nullptr;
+    if (tf32) {
+        // the frames' w q rows and norms, then the pilot's bucket minima
+        unsigned* bm = reinterpret_cast<unsigned*>(base + L.bmin);
+        if ((e = cudaMemsetAsync(bm, 0xff, (size_t)nq * kMBuckets * sizeof(unsigned), stream)) != cudaSuccess)
+            return e;
+        {
+            ProfScope ps("tf32_prep_kernel", stream);
+            tf32_prep_kernel<<<(nq + 7) / 8, 256, 0, stream>>>(q, w, nq, db->dim, wq, p.qn);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        t.xn = xn;
+        t.fT = p.fT;
+        t.qn = p.qn;
+        t.cnt = p.cnt;
+        t.cand = p.cand;
+        t.bmin = bm;
+        t.nq = nq;
+        t.err = db->err;
+        if ((e = tf32_pass<true>(db, wq, nq, t, stream)) != cudaSuccess) return e;
+    }
     {
         ProfScope ps("many_bound_kernel", stream);
         many_bound_kernel<<<(nq + 7) / 8, 256, 0, stream>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (tf32) {
-        const int D = db->dim, ns = tf32_sorted(nq);
-        float* fkey = reinterpret_cast<float*>(take((size_t)nq * sizeof(float)));
-        float* wq = reinterpret_cast<float*>(take((size_t)nq * D * sizeof(float)));
-        float* wq_s = reinterpret_cast<float*>(take((size_t)ns * D * sizeof(float)));
-        int* fperm = reinterpret_cast<int*>(take((size_t)ns * sizeof(int)));
-        float* gbound = reinterpret_cast<float*>(take((size_t)ns / 32 * sizeof(float)));
-        {
-            ProfScope ps("tf32_prep_kernel", stream);
-            tf32_prep_kernel<<<(nq + 7) / 8, 256, 0, stream>>>(q, w, nq, D, p.thr, p.qn, xmax_w, db->xnorm_max, wq,
-                                                                fkey);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
-        if ((e = launch_sort_queries(fkey, nq, ns, wq, D * (int)sizeof(float), wq_s, fperm, gbound, stream)) !=
-            cudaSuccess)
-            return e;
-        CUtensorMap tmQ, tmX;
-        if (!make_map(&tmQ, wq_s, ns, D, kTcTF32, kFT) || !make_map(&tmX, db->X, db->n, D, kTcTF32, kTcM))
-            return cudaErrorInvalidValue;
-        TfParams t{};
-        t.n = db->n;
-        t.slices = D / 32;
-        t.stages = tf32_stages(t.slices);
-        if (t.stages < 2) return cudaErrorInvalidValue;
-        const int nfb = ns / kFT;
-        const int nchunks = tf32_chunks(nfb, db->sms, db->n);
-        int64_t cr = (db->n + nchunks - 1) / nchunks;
-        t.chunk_rows = (cr + kTcM - 1) / kTcM * kTcM;
-        t.nchunks = (int)((db->n + t.chunk_rows - 1) / t.chunk_rows);
-        if (t.nchunks < 1) t.nchunks = 1;
-        t.xn = xn;
-        t.fperm = fperm;
-        t.gbound = gbound;
-        t.thr = p.thr;
-        t.qn = p.qn;
-        t.cnt = p.cnt;
-        t.cand = p.cand;
-        t.nq = nq;
-        t.err = db->err;
-        const size_t sm = tf32_smem(t.slices, t.stages);
-        if ((e = cudaFuncSetAttribute(tf32_many_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
-            cudaSuccess)
-            return e;
-        ProfScope ps("tf32_many_kernel", stream);
-        tf32_many_kernel<<<dim3(t.nchunks, nfb), kFThreads, sm, stream>>>(tmQ, tmX, t);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = tf32_pass<false>(db, wq, nq, t, stream)) != cudaSuccess) return e;
     } else {
         const int nfb = (nq + kMF - 1) / kMF;
         // about one CTA per SM over frame blocks x row chunks; chunks are whole tiles

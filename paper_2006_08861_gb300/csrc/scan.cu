@@ -919,9 +919,12 @@ cudaError_t scan_with_pilot(const lhr_db* db, const float* q, int nq, int k, con
     const ScanSrc full{db->X, db->xnorm, db->chunks, db->nchunks, db->chunk_off, db->perm};
     unsigned* bmin = nullptr;
     if (pilot && use_pilot(db, nq) && many_eligible(db, nq, k)) {
-        // many frames: the pilot's bound, then the register-tiled pass (many.cu)
-        cudaError_t e = launch_pilot(db, q, nq, wt ? wt->w : nullptr, scratch, &bmin, stream);
-        if (e != cudaSuccess) return e;
+        // many frames (many.cu): the tensor-core form runs its own pilot; the
+        // register-tiled form starts from this pilot's bound
+        if (!many_tf32(db)) {
+            cudaError_t e = launch_pilot(db, q, nq, wt ? wt->w : nullptr, scratch, &bmin, stream);
+            if (e != cudaSuccess) return e;
+        }
         void* ms = reinterpret_cast<unsigned char*>(scratch) + pilot_bytes(db, nq);
         return launch_many(db, q, nq, k, wt ? wt->w : nullptr, wt ? wt->xnw : db->xnorm, wt ? wt->xmax_w : nullptr,
                            bmin, scan_margin_scale(db->dim), idx, dist, ms, stream);

@@ -146,6 +146,30 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
     return r;
 }
 
+// Three-input minimum.
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Minimum over the warp's 32 rows of each of 32 columns (c[j] = this lane's
+// row, column j): a butterfly in which every step exchanges half of the
+// remaining columns with the partner lane; lane l ends with column l's minimum.
+__device__ __forceinline__ float column_min32(float (&c)[32], int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool upper = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < s; ++i) {
+            const float send = upper ? c[i] : c[i + s];
+            const float keep = upper ? c[i + s] : c[i];
+            c[i] = fminf(keep, __shfl_xor_sync(0xffffffffu, send, s));
+        }
+    }
+    return c[0];
+}
+
 // Maximum of 32 accumulator values in four interleaved chains of three-input
 // maxima (few live temporaries).
 __device__ __forceinline__ float max32(const uint32_t (&v)[32]) {
@@ -178,12 +202,15 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 2-D map over a row-major rows x D array of operands of kind k; box = 128
 // bytes of K by box_rows rows, 128-byte swizzle, zero fill past the last row.
-inline bool make_map(CUtensorMap* map, const void* base, int64_t rows, int D, TcKind k, int box_rows) {
+// row_pitch: elements from one mapped row to the next (0 = D; a multiple of D
+// maps every (row_pitch / D)-th row of a larger array).
+inline bool make_map(CUtensorMap* map, const void* base, int64_t rows, int D, TcKind k, int box_rows,
+                     int64_t row_pitch = 0) {
     auto fn = encode_fn();
     if (!fn) return false;
     const int elem = tc_elem_bytes(k);
     cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)D * elem};
+    cuuint64_t strides[1] = {(cuuint64_t)(row_pitch > 0 ? row_pitch : D) * elem};
     cuuint32_t box[2] = {(cuuint32_t)(kTcSliceBytes / elem), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     const CUtensorMapDataType dt = k == kTcFP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
