@@ -189,8 +189,7 @@ KERNELS = ("quantize_queries_kernel", "tc_pilot_kernel_fp8", "tc_pilot_kernel_bf
            "tc_main_kernel_fp8", "tc_main_kernel_bf16", "tc_full_kernel_fp8", "tc_full_kernel_bf16",
            "merge_rerank_kernel", "scan_pilot", "scan_topk_kernel", "small_topk_kernel", "aggregate_kernel",
            "hier_fused_kernel", "coarse_kernel", "collect_kernel", "shortlist_kernel", "wnorm_kernel",
-           "many_bound_kernel", "many_select_kernel", "tf32_many_kernel", "tf32_pilot_kernel", "tf32_prep_kernel",
-           "many_kernel",
+           "many_bound_kernel", "many_select_kernel", "f16_many_kernel", "f16_pilot_kernel", "f16_prep_kernel",
            "soft_forward_kernel",
            "soft_backward_kernel")
 
@@ -938,23 +937,17 @@ def run_differentiation(args, rank, world, local):
     tot = max_over_ranks(sum(ms), world)
     kt = read_kernels(lhr, args.steps, sum(ms))
     share = kt["kernels"]
-    # the selection's main kernel: the many-frame pass (TF32 tensor cores, or the FP32 register-tiled
-    # form where D is not a multiple of 32) or the streaming scan
-    sel = next((n for n in ("tf32_many_kernel", "many_kernel") if n in share), "scan_topk_kernel")
+    # the selection's main kernel: the many-frame tensor-core filter (FP16 operands) or the streaming scan
+    sel = "f16_many_kernel" if "f16_many_kernel" in share else "scan_topk_kernel"
     sel_us = share.get(sel, {"avg_us": float("nan")})["avg_us"]
     flops = 2.0 * B * m * c["n"] * c["dim"]  # one multiply-add per (frame, row, dim) of the expanded form
     achieved = flops / (sel_us / 1e6) / 1e12
-    if sel == "tf32_many_kernel":
+    if sel == "f16_many_kernel":
         peaks = load_peaks()
-        tf32_meas = measure_gemm_peak(dev, "tf32")
-        ratio = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
-        scaled = peaks["bf16"] * ratio if peaks.get("bf16") else None
-        peak = tf32_meas if tf32_meas else scaled
-        roof = {"bound": "tensor", "kernel": f"{sel} (weighted selection filter, TF32 operands)",
+        peak = peaks["bf16"]  # dense FP16 and BF16 tensor rates are equal
+        roof = {"bound": "tensor", "kernel": f"{sel} (weighted selection filter, FP16 operands)",
                 "achieved": round(achieved, 2), "peak": round(peak, 1),
-                "peak_source": ("cuBLAS TF32 GEMM 8192^3 (torch.matmul, allow_tf32), best of 10, this run"
-                                if tf32_meas else f"measured BF16 x {ratio:.3f} (nominal TF32/BF16), {peaks['source']}"),
-                "peak_bf16_scaled": round(scaled, 1) if scaled else None}
+                "peak_source": f"dense BF16 GEMM burst, {peaks['source']} (FP16 runs at the BF16 rate)"}
     else:
         f32_meas = measure_gemm_peak(dev, "f32")
         derived = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock (GHz), TFLOP/s

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -135,7 +136,7 @@ static void free_db(lhr_db* db) {
     if (!db) return;
     void* bufs[] = {db->X, db->xnorm, db->Xc, db->perm, db->iperm, db->xy, db->tile, db->chunks, db->chunk_off,
                     db->Xb, db->snb, db->X8, db->sn8, db->Xb_s, db->snb_s, db->X8_s, db->sn8_s,
-                    db->Xp, db->sub_p, db->err};
+                    db->Xh, db->Xp, db->sub_p, db->err};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete db;
@@ -343,7 +344,7 @@ lhr_status lhr_build_db(const float* feats, const double* xy, const int32_t* sub
     if ((e = dalloc(&db->xy, (size_t)n * 2)) != cudaSuccess) return bail(cuda_fail(e, "allocate xy"));
     if ((e = dalloc(&db->tile, (size_t)n * 2)) != cudaSuccess) return bail(cuda_fail(e, "allocate tiles"));
     if ((e = dalloc(&db->err, 1)) != cudaSuccess) return bail(cuda_fail(e, "allocate error word"));
-    if ((e = dalloc(&flag, 2)) != cudaSuccess) return bail(cuda_fail(e, "allocate flag"));
+    if ((e = dalloc(&flag, 3)) != cudaSuccess) return bail(cuda_fail(e, "allocate flag"));
     if ((e = dalloc(&db->xnorm, (size_t)n + kSnPad)) != cudaSuccess ||
         (e = cudaMemsetAsync(db->xnorm, 0, ((size_t)n + kSnPad) * sizeof(float), s)) != cudaSuccess)
         return bail(cuda_fail(e, "allocate norms"));
@@ -354,6 +355,8 @@ lhr_status lhr_build_db(const float* feats, const double* xy, const int32_t* sub
             (e = cudaMemsetAsync(db->snb, 0, ((size_t)n + kSnPad) * sizeof(float2), s)) != cudaSuccess)
             return bail(cuda_fail(e, "allocate BF16 copy"));
     }
+    if (half_copy_wanted(n, D) && (e = cudaMalloc(&db->Xh, (size_t)n * D * 2)) != cudaSuccess)
+        return bail(cuda_fail(e, "allocate FP16 copy"));
     if (cfg->lowp & LHR_LOWP_FP8) {
         if ((e = cudaMalloc(&db->X8, (size_t)n * D)) != cudaSuccess ||
             (e = dalloc(&db->sn8, (size_t)n + kSnPad)) != cudaSuccess ||
@@ -377,7 +380,7 @@ lhr_status lhr_build_db(const float* feats, const double* xy, const int32_t* sub
             return bail(cuda_fail(e, "allocate FP8 sample"));
     }
     cudaMemsetAsync(db->err, 0, sizeof(int32_t), s);
-    cudaMemsetAsync(flag, 0, 2 * sizeof(int32_t), s);
+    cudaMemsetAsync(flag, 0, 3 * sizeof(int32_t), s);
     const bool feats_dev = is_device_ptr(feats);
     if (need_perm) {
         if ((e = dalloc(&db->perm, (size_t)n)) != cudaSuccess) return bail(cuda_fail(e, "allocate perm"));
@@ -452,12 +455,22 @@ lhr_status lhr_build_db(const float* feats, const double* xy, const int32_t* sub
     if ((e = launch_norms(db, reinterpret_cast<unsigned*>(flag + 1), s)) != cudaSuccess)
         return bail(cuda_fail(e, "norms"));
     if ((e = launch_pilot_sample(db, s)) != cudaSuccess) return bail(cuda_fail(e, "pilot sample"));
-    int32_t flag_h2[2] = {0, 0};
-    cudaMemcpyAsync(flag_h2, flag, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if ((e = launch_half_copy(db, reinterpret_cast<unsigned*>(flag + 2), s)) != cudaSuccess)
+        return bail(cuda_fail(e, "FP16 copy"));
+    int32_t flag_h2[3] = {0, 0, 0};
+    cudaMemcpyAsync(flag_h2, flag, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(cuda_fail(e, "build"));
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(e, "build"));
     const int32_t flag_h = flag_h2[0];
     std::memcpy(&db->xnorm_max, &flag_h2[1], sizeof(float));
+    if (db->Xh) {
+        // the scale the copy kernel derived from the same maximum
+        float amax;
+        std::memcpy(&amax, &flag_h2[2], sizeof(float));
+        int ex = 0;
+        std::frexp(amax, &ex);
+        db->xh_scale = std::ldexp(1.0f, 15 - ex);
+    }
     if (flag_h & 1) return bail(fail(LHR_ERR_INVALID_ARG, "features contain a non-finite value"));
     if (flag_h & 2) return bail(fail(LHR_ERR_INVALID_ARG, "xy contains a non-finite value or a tile outside int32"));
     cudaFree(flag);

@@ -3,6 +3,7 @@
 // finiteness check, subspace gather, floor-plan tiles, coarse prefix slab and
 // the per-row scaled BF16 / FP8-e4m3 copies with their norms.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <math.h>
 
@@ -126,6 +127,31 @@ __global__ void pilot_rows_kernel(const float4* X, int64_t ns, int stride, int r
     }
 }
 
+// max |x| over count values (count % 4 == 0) into *max_bits (float bits of a
+// non-negative value, so unsigned order is float order).
+__global__ void absmax_kernel(const float4* X, int64_t count4, unsigned* max_bits) {
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = X[i];
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(max_bits, __float_as_uint(m));
+}
+
+// Xh = fp16(x * 2^(15 - e)), round to nearest, for max |x| = f 2^e, f in [0.5, 1).
+__global__ void half_copy_kernel(const float4* X, int64_t count4, const unsigned* max_bits, __half2* Xh) {
+    int ex = 0;
+    frexpf(__uint_as_float(*max_bits), &ex);
+    const float sc = ldexpf(1.0f, 15 - ex);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = X[i];
+        Xh[2 * i] = __floats2half2_rn(v.x * sc, v.y * sc);
+        Xh[2 * i + 1] = __floats2half2_rn(v.z * sc, v.w * sc);
+    }
+}
+
 int grid_for(int64_t work, int sms) {
     const int64_t b = (work + 255) / 256;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sms * 8));
@@ -160,6 +186,18 @@ cudaError_t launch_pilot_sample(const lhr_db* db, cudaStream_t stream) {
     const int row_f4 = db->dim / 4;
     pilot_rows_kernel<<<grid_for(db->n_pilot * row_f4, db->sms), 256, 0, stream>>>(
         reinterpret_cast<const float4*>(db->X), db->n_pilot, kSampleStride, row_f4, reinterpret_cast<float4*>(db->Xp));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_half_copy(const lhr_db* db, unsigned* absmax_bits, cudaStream_t stream) {
+    if (!db->Xh) return cudaSuccess;
+    const int64_t count4 = db->n * (int64_t)db->dim / 4;
+    absmax_kernel<<<grid_for(count4, db->sms), 256, 0, stream>>>(reinterpret_cast<const float4*>(db->X), count4,
+                                                                 absmax_bits);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    half_copy_kernel<<<grid_for(count4, db->sms), 256, 0, stream>>>(reinterpret_cast<const float4*>(db->X), count4,
+                                                                    absmax_bits, reinterpret_cast<__half2*>(db->Xh));
     return cudaGetLastError();
 }
 

@@ -61,6 +61,13 @@ struct lhr_db {
     void* Xb_s = nullptr; float2* snb_s = nullptr;
     void* X8_s = nullptr; float2* sn8_s = nullptr;
 
+    // FP16 copy (internal order) of X * xh_scale, xh_scale = 2^(15 - e) for
+    // max |x| = f 2^e, f in [0.5, 1) (so every scaled value is below 2^15 in
+    // magnitude): the operand of the many-frame path's tensor-core filter.
+    // Present when half_copy_wanted(n, dim).
+    void* Xh = nullptr;
+    float xh_scale = 1.f;
+
     // FP32 pilot sample of the exhaustive scan: internal rows 0, 64, 128, ...
     // (n_pilot rows) and the subspace of each. A frame's k-th distance over the
     // sample bounds its k-th over the whole database from above, so the full
@@ -74,6 +81,12 @@ struct lhr_db {
 };
 
 namespace lhr {
+
+// The many-frame path's FP16 operand copy serves whole 128-byte K slices of at
+// most 256 dimensions and row indices that fit its 32-bit candidate keys.
+inline bool half_copy_wanted(int64_t n, int dim) {
+    return dim % 64 == 0 && dim <= 256 && n >= kPilotMinRows && n < ((int64_t)1 << 31);
+}
 
 // Thread-local error message plumbing.
 lhr_status fail(lhr_status st, const std::string& msg);
@@ -103,16 +116,14 @@ struct ProfScope {
 // `pilot`: seed the scan's thresholds from the pilot sample when the database
 // has one (same results, fewer exact recomputes; more scratch).
 size_t scan_scratch_bytes(const lhr_db* db, int nq, int k, bool pilot);
-// many.cu: exhaustive top k for many frames at once (the expanded form over a
-// pilot's bound, exact re-score of the candidates). many_tf32: the filter and
-// its pilot run on the tensor cores (launch_many takes bmin = nullptr);
-// otherwise the FP32 register-tiled form over the scan pilot's bmin.
+// many.cu: exhaustive top k for many frames at once: a tensor-core filter over
+// the FP16 copy (its own pilot, then the full pass) keeps every row that can be
+// in a frame's top k; those are re-scored exactly in FP32.
 bool many_eligible(const lhr_db* db, int nq, int k);
-bool many_tf32(const lhr_db* db);
 size_t many_scratch_bytes(const lhr_db* db, int nq);
 cudaError_t launch_many(const lhr_db* db, const float* q, int nq, int k, const float* w, const float* xn,
-                        const float* xmax_w, const unsigned* bmin, float margin_scale, int64_t* idx, float* dist,
-                        void* scratch, cudaStream_t stream);
+                        const float* xmax_w, float margin_scale, int64_t* idx, float* dist, void* scratch,
+                        cudaStream_t stream);
 
 cudaError_t launch_scan(const lhr_db* db, const float* q, int nq, int k, int64_t* idx, float* dist,
                         void* scratch, bool pilot, cudaStream_t stream);
@@ -203,5 +214,7 @@ cudaError_t launch_gather_rows(const float* src, const int32_t* perm, int64_t n,
 cudaError_t launch_tiles(const double* xy, int64_t n, double t, int32_t* tile, int32_t* flag, cudaStream_t stream);
 cudaError_t launch_norms(const lhr_db* db, unsigned* max_bits, cudaStream_t stream);
 cudaError_t launch_pilot_sample(const lhr_db* db, cudaStream_t stream);
+// db->Xh from db->X: max |x| into *absmax_bits (zeroed by the caller), then the scaled copy.
+cudaError_t launch_half_copy(const lhr_db* db, unsigned* absmax_bits, cudaStream_t stream);
 
 }  // namespace lhr

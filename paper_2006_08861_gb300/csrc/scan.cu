@@ -901,7 +901,7 @@ cudaError_t scan_pass(const lhr_db* db, const ScanSrc& src, const char* label, c
 }  // namespace
 
 size_t scan_scratch_bytes(const lhr_db* db, int nq, int k, bool pilot) {
-    if (pilot && use_pilot(db, nq) && many_eligible(db, nq, k)) return pilot_bytes(db, nq) + many_scratch_bytes(db, nq);
+    if (pilot && many_eligible(db, nq, k)) return many_scratch_bytes(db, nq);
     const ScanConfig c = choose_config(db, nq);
     const size_t main = pass_bytes(c, db->nchunks, db->n_sub, nq, k);
     return pilot && use_pilot(db, nq) ? main + pilot_bytes(db, nq) : main;
@@ -918,16 +918,10 @@ cudaError_t scan_with_pilot(const lhr_db* db, const float* q, int nq, int k, con
                             float* dist, void* scratch, bool pilot, cudaStream_t stream) {
     const ScanSrc full{db->X, db->xnorm, db->chunks, db->nchunks, db->chunk_off, db->perm};
     unsigned* bmin = nullptr;
-    if (pilot && use_pilot(db, nq) && many_eligible(db, nq, k)) {
-        // many frames (many.cu): the tensor-core form runs its own pilot; the
-        // register-tiled form starts from this pilot's bound
-        if (!many_tf32(db)) {
-            cudaError_t e = launch_pilot(db, q, nq, wt ? wt->w : nullptr, scratch, &bmin, stream);
-            if (e != cudaSuccess) return e;
-        }
-        void* ms = reinterpret_cast<unsigned char*>(scratch) + pilot_bytes(db, nq);
+    if (pilot && many_eligible(db, nq, k)) {
+        // many frames: the tensor-core filter and the exact re-score (many.cu)
         return launch_many(db, q, nq, k, wt ? wt->w : nullptr, wt ? wt->xnw : db->xnorm, wt ? wt->xmax_w : nullptr,
-                           bmin, scan_margin_scale(db->dim), idx, dist, ms, stream);
+                           scan_margin_scale(db->dim), idx, dist, scratch, stream);
     }
     if (pilot && use_pilot(db, nq)) {
         const ScanConfig c = choose_config(db, nq);

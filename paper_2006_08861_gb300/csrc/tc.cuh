@@ -19,8 +19,15 @@ constexpr int kTcM = 128;         // rows of A per MMA (M), one TMEM lane each
 constexpr int kTcSliceBytes = 128;  // K bytes per shared-memory row (one 128-byte swizzle atom)
 
 // Operand kinds: tcgen05.mma kind and the format code of A and B in the instruction descriptor.
-enum TcKind { kTcBF16 = 0, kTcFP8 = 1, kTcTF32 = 2 };
-__host__ __device__ constexpr int tc_elem_bytes(TcKind k) { return k == kTcFP8 ? 1 : (k == kTcBF16 ? 2 : 4); }
+enum TcKind { kTcBF16 = 0, kTcFP8 = 1, kTcTF32 = 2, kTcF16 = 3 };
+__host__ __device__ constexpr int tc_elem_bytes(TcKind k) {
+    return k == kTcFP8 ? 1 : (k == kTcTF32 ? 4 : 2);
+}
+// A / B format code in the instruction descriptor: E4M3 0 (kind::f8f6f4), F16 0
+// and BF16 1 (kind::f16), TF32 2 (kind::tf32).
+__host__ __device__ constexpr uint32_t tc_format(TcKind k) {
+    return k == kTcBF16 ? 1u : (k == kTcTF32 ? 2u : 0u);
+}
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, u64* bar) {
     asm volatile(
@@ -78,7 +85,7 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, u64 adesc, u64 bdesc, ui
             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
             : "memory");
-    } else if (K == kTcBF16) {
+    } else if (K == kTcBF16 || K == kTcF16) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
@@ -92,6 +99,42 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, u64 adesc, u64 bdesc, ui
             : "memory");
     }
 }
+
+// MMA with the A operand in tensor memory: M rows x K, a row per TMEM lane,
+// from column a_tmem on 32 bits per column (one TF32 element, or two 16-bit
+// elements, the lower-indexed in the low half).
+template <TcKind K>
+__device__ __forceinline__ void tc_mma_tmem_a(uint32_t d_tmem, uint32_t a_tmem, u64 bdesc, uint32_t idesc,
+                                              uint32_t accum) {
+    if (K == kTcTF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accum)
+            : "memory");
+    } else {
+        static_assert(K == kTcTF32 || K == kTcF16 || K == kTcBF16, "16- or 32-bit operands");
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accum)
+            : "memory");
+    }
+}
+
+// tcgen05.st of 32 columns: this thread's lane of columns taddr .. taddr + 31.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]),
+        "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]),
+        "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // tcgen05.ld of 32 columns without the wait: the registers are valid only after
 // tmem_ld_wait on the same array, which names them so nothing reads them earlier.
@@ -129,12 +172,11 @@ __device__ __forceinline__ u64 sw128_desc(uint32_t saddr) {
 }
 
 // Instruction descriptor: dense, FP32 accumulate, A/B K-major, M = 128, N = n
-// (a multiple of 16, <= 256). Operand format codes: E4M3 0 (kind::f8f6f4),
-// BF16 1 (kind::f16), TF32 2 (kind::tf32).
+// (a multiple of 16, <= 256), operand formats by tc_format.
 __host__ __device__ constexpr uint32_t tc_idesc(TcKind k, int n) {
     return (1u << 4)                                                        // D format: F32
-           | ((k == kTcFP8 ? 0u : (k == kTcBF16 ? 1u : 2u)) << 7)           // A format
-           | ((k == kTcFP8 ? 0u : (k == kTcBF16 ? 1u : 2u)) << 10)          // B format
+           | (tc_format(k) << 7)                                              // A format
+           | (tc_format(k) << 10)                                             // B format
            | ((uint32_t)(n >> 3) << 17)                                     // N >> 3
            | ((uint32_t)(kTcM >> 4) << 24);                                 // M >> 4
 }
@@ -213,8 +255,10 @@ inline bool make_map(CUtensorMap* map, const void* base, int64_t rows, int D, Tc
     cuuint64_t strides[1] = {(cuuint64_t)(row_pitch > 0 ? row_pitch : D) * elem};
     cuuint32_t box[2] = {(cuuint32_t)(kTcSliceBytes / elem), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    const CUtensorMapDataType dt = k == kTcFP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
-                                   : (k == kTcBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+    const CUtensorMapDataType dt = k == kTcFP8    ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                   : k == kTcBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                   : k == kTcF16  ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                  : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

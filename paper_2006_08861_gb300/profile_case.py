@@ -72,8 +72,8 @@ def main(argv=None):
             call()
         torch.cuda.synchronize()
         lhr.lhr_profile_enable(False)
-        for name in ("hier_fused", "scan_pilot", "wnorm", "scan_topk", "many_bound", "tf32_prep", "sort_queries",
-                     "tf32_pilot", "tf32_many", "many_kernel", "many_select",
+        for name in ("hier_fused", "scan_pilot", "wnorm", "scan_topk", "many_bound", "f16_prep", "sort_queries",
+                     "f16_pilot", "f16_many", "many_select",
                      "small_topk", "coarse_kernel", "collect", "shortlist",
                      "aggregate", "quantize", "tc_pilot", "tau_kernel", "tc_main", "tc_full", "merge_rerank"):
             n, ms = lhr.lhr_profile_read(name, reset=True)
