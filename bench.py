@@ -914,28 +914,121 @@ def run_differentiation(args, rank, world, local):
         loss.backward()
         return loss, fr
 
+    # the step captured once into a CUDA graph: the frames and true positions of step i are
+    # copied into the captured inputs, then forward, loss and backward replay without host work
+    fr_s = frames_all[:B * m].clone().requires_grad_(True)
+    y_s = y_all[:B].clone()
+
+    def load(i):
+        j = i % n_sets
+        with torch.no_grad():
+            fr_s.copy_(frames_all[j * B * m:(j + 1) * B * m])
+            y_s.copy_(y_all[j * B:(j + 1) * B])
+
+    def step_static():
+        loss = lhr.loc_mse(lhr.soft_retrieval(h, fr_s, offs, w, tau, k), y_s)
+        loss.backward()
+        return loss
+
     for i in range(args.warmup):
         step(i)
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):  # autograd warm-up on a side stream before capture
+        for i in range(args.warmup):
+            load(i)
+            fr_s.grad = w.grad = tau.grad = None
+            step_static()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+
+    def capture(prof):
+        fr_s.grad = w.grad = tau.grad = None
+        g = torch.cuda.CUDAGraph()
+        lhr.lhr_profile_read(None, reset=True)
+        lhr.lhr_profile_enable(prof)
+        try:
+            with torch.cuda.graph(g):
+                step_static()
+        finally:
+            lhr.lhr_profile_enable(False)
+        return g
+
+    try:
+        g, gi = capture(False), capture(True)
+    except Exception as e:  # capture unsupported: eager steps
+        print(f"# graph capture failed ({e}); timing eager steps", file=sys.stderr)
+        g = gi = None
+    for i in range(args.warmup):
+        if g is not None:
+            load(i)
+            g.replay()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    ms = []
-    lhr.lhr_profile_read(None, reset=True)
+    ms, ms_eager = [], []
     for i in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         barrier(world)
-        lhr.lhr_profile_enable(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        if g is not None:
+            load(args.warmup + i)
+            g.replay()
+        else:
+            step(args.warmup + i)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    # the same steps eager (context), then the instrumented graph for per-kernel times
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         step(args.warmup + i)
         b.record(stream)
+        torch.cuda.synchronize()
+        ms_eager.append(a.elapsed_time(b))
+    tot = max_over_ranks(sum(ms), world)
+    if gi is not None:
+        # the capture recorded each kernel's event pair once; every replay re-records it, so the
+        # times are read (without clearing) after each replay
+        inst, acc = 0.0, {}
+        for i in range(args.steps):
+            load(args.warmup + i)
+            flush.zero_()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            gi.replay()
+            b.record(stream)
+            torch.cuda.synchronize()
+            inst += a.elapsed_time(b)
+            for name in sorted(KERNELS, key=len, reverse=True):
+                n_l, t_ms = lhr.lhr_profile_read(name, reset=False)
+                if n_l:
+                    c0, t0_ = acc.get(name, (0, 0.0))
+                    acc[name] = (c0 + n_l, t0_ + t_ms)
+        lhr.lhr_profile_read(None, reset=True)
+        tot_k = sum(t for _, t in acc.values())
+        kt = {"kernels": {n: {"launches_per_step": round(c / args.steps, 3), "avg_us": round(t / c * 1e3, 3),
+                              "share_of_step": round(t / inst, 4)}
+                          for n, (c, t) in sorted(acc.items(), key=lambda kv: -kv[1][1])},
+              "kernel_ms_per_step": round(tot_k / args.steps, 4),
+              "launches_per_step": round(sum(c for c, _ in acc.values()) / args.steps, 3),
+              "kernel_time_within_step": bool(tot_k <= inst * 1.0001),
+              "instrumented_ms_per_step": round(inst / args.steps, 4),
+              "timed_in": "replays of an instrumented copy of the step's graph (event-record nodes around each kernel)"}
+    else:
+        lhr.lhr_profile_enable(True)
+        for i in range(args.steps):
+            step(args.warmup + i)
         lhr.lhr_profile_enable(False)
         torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
-    clk = clocks.stop()
-    tot = max_over_ranks(sum(ms), world)
-    kt = read_kernels(lhr, args.steps, sum(ms))
+        kt = read_kernels(lhr, args.steps, sum(ms_eager))
     share = kt["kernels"]
     # the selection's main kernel: the many-frame tensor-core filter (FP16 operands) or the streaming scan
     sel = "f16_many_kernel" if "f16_many_kernel" in share else "scan_topk_kernel"
@@ -958,7 +1051,7 @@ def run_differentiation(args, rank, world, local):
                                 if f32_meas else "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (derived)"),
                 "peak_derived": round(derived, 1)}
     roof.update({"unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None, "avg_launch_us": sel_us,
-                 "algorithmic_flops_per_launch": flops, "timed_in": "event pairs recorded inside the timed steps"})
+                 "algorithmic_flops_per_launch": flops, "timed_in": kt.get("timed_in", "event pairs recorded inside the timed steps")})
     # gradient check of one window against the FP64 oracle (selection from the GPU)
     loss, fr = step(0)
     g_fr = fr.grad.detach().cpu().numpy()
@@ -982,7 +1075,10 @@ def run_differentiation(args, rank, world, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "differentiation", "desc": "N=200000 D=256, B=256 windows of m=5, k=32, w=1, "
                                                           "tau=0.1: soft retrieval forward + location loss + backward",
-                   "l2": "flushed before every timed step", "launch": "eager (autograd)"},
+                   "l2": "flushed before every timed step",
+                   "launch": ("CUDA graph of the autograd step (forward, loss, backward captured once; each step "
+                              "copies its frames into the captured inputs)" if g is not None else "eager (autograd)"),
+                   "eager_ms_per_step": round(sum(ms_eager) / args.steps, 4)},
         "roofline": roof,
         "kernels": kt,
         "grad_check": {"dq_max_rel_err_vs_fp64_window0": dq_err, "loss": float(loss.item())},
