@@ -221,12 +221,13 @@ __global__ void many_select_kernel(ManyParams p) {
     }
 }
 
-// ------------------------------------------------------------------ TF32 tensor-core pass
-// The filter of many_kernel on the tensor cores: u(f, r) = ||x_r||_w^2 - 2 (w q_f) . x_r
-// with the dot by tcgen05.mma kind::tf32 (operands truncated to TF32, FP32
-// accumulation), one CTA per (128-frame block, row chunk). The block's w q rows
-// are the A operand, resident in tensor memory (a frame per TMEM lane, one
-// dimension per column), so shared memory holds only the deep TMA ring that
+// ------------------------------------------------------------------ FP16 tensor-core pass
+// The filter on the tensor cores: u(f, r) = ||x_r||_w^2 - 2 (w q_f) . x_r with
+// the dot by tcgen05.mma kind::f16 over FP16 operands (the database copy Xh and
+// each frame's w q, both scaled by powers of two; FP32 accumulation), one CTA
+// per (128-frame block, row chunk). The block's w q rows are the A operand,
+// resident in tensor memory (a frame per TMEM lane, two dimensions per
+// column), so shared memory holds only the deep TMA ring that
 // streams the database rows (the B operand, 128 rows per tile); the 128 x 128
 // accumulators alternate in the rest of TMEM. The epilogue thread of TMEM lane m
 // owns frame m over 64 of the tile's rows: per 32 rows the smallest u (three-

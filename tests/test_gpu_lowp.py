@@ -96,6 +96,40 @@ def test_sampled_threshold_path_against_oracle(lhr, fmt_name):
     assert gi[0, 0] == 5 and np.all(gd[0] == 0.0)
 
 
+def test_fp8_main_pass_dense_candidates(lhr):
+    # FP8 at D = 256 over a sampled database (the thresholded main pass), 300
+    # queries: a ragged last 256-query block. Rows 1000 .. 2199 are near-copies
+    # of row 7 that query 1 sits on: about 1,200 candidates inside one row
+    # chunk, far past what the epilogue stages per query before a flush, all
+    # below the candidate buffer's 2,048.
+    fmt, bit = FMT["fp8"]
+    rng = np.random.default_rng(77)
+    n, dim, nq, W, k = 300_000, 256, 300, 64, 20
+    X = rng.standard_normal((n, dim)).astype(np.float32)
+    X[1000:2200] = X[7] + 0.02 * rng.standard_normal((1200, dim)).astype(np.float32)
+    Q = (X[rng.integers(0, n, nq)] + 0.3 * rng.standard_normal((nq, dim))).astype(np.float32)
+    Q[1] = X[7] + 0.01 * rng.standard_normal(dim).astype(np.float32)
+    db = lhr.lhr_build_db(X, np.zeros((n, 2)), lowp=bit)
+    idx, dist = lhr.lhr_query(db, torch.from_numpy(Q).cuda(), k, score="fp8", rerank_width=W)
+    torch.cuda.synchronize()
+    assert lhr.lhr_db_error(db) == 0
+    gi, gd = idx.cpu().numpy()[:, 0], dist.cpu().numpy()[:, 0]
+    s_rows, codes = olowp.quantize_rows(X, fmt)
+    s_Q = olowp.batch_scale(Q, fmt)
+    sample = [1, 255, 256, 299] + np.random.default_rng(78).choice(np.arange(2, nq), size=16, replace=False).tolist()
+    checked = 0
+    for qi in sample:
+        if not _shortlist_separated(Q[qi], X, fmt, W, s_rows, codes, s_Q):
+            continue
+        o_idx, o_dist, _ = olowp.lowp_topk(Q[qi:qi + 1], X, fmt, W, k + 1, codes=codes, s_rows=s_rows,
+                                           q_scale=s_Q)
+        check_list(Q[qi], X, gi[qi], gd[qi], o_idx[0], o_dist[0], k, where=f"fp8 q{qi}")
+        checked += 1
+    assert checked >= len(sample) // 2
+    # query 1's answers are among the near-copies of row 7
+    assert np.all((gi[1] == 7) | ((gi[1] >= 1000) & (gi[1] < 2200)))
+
+
 def test_width_equal_to_database_is_exhaustive(lhr):
     rng = np.random.default_rng(3)
     X = rng.standard_normal((100, 128)).astype(np.float32)
