@@ -47,12 +47,13 @@
 //   memory (a 1-D bulk copy per tile) and keeps its query's exact top W of the chunk in local
 //   memory, filled through a 16-entry shared-memory survivor buffer. It is the only pass for
 //   databases too small to sample.
-// merge_rerank_kernel, one warp per query: the shortlist is the W smallest
-//   keys of the query's candidate buffer (for W <= 64 a running 64 smallest in
-//   registers over 64-key chunks; else, and after the full pass, a sort of the
-//   candidates or of the per-chunk lists cut at the smallest chunk's W-th
-//   key); its rows are re-scored with the exact FP32 direct form and the top
-//   k kept.
+// merge_rerank_kernel, one block of four warps per query: the shortlist is the
+//   W smallest keys of the query's candidate buffer (for W <= 64 each warp keeps
+//   a running 64 smallest in registers over its share of the 64-key chunks and
+//   warp 0 merges the four; else, and after the full pass, warp 0 sorts the
+//   candidates or the per-chunk lists cut at the smallest chunk's W-th key);
+//   the four warps re-score its rows with the exact FP32 direct form (eight
+//   rows in flight each) and the sorted exact keys give the top k.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -1022,29 +1023,33 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_rerank_kernel(
     const u64* __restrict__ partial, int nchunks, int W, const u64* __restrict__ cand,
     const unsigned* __restrict__ cnt, const float* __restrict__ X, int D, const float* __restrict__ Q, int nq, int k,
     int64_t* __restrict__ idx, float* __restrict__ dist) {
-    extern __shared__ u64 cand_sm[];  // kMergeWarps x kCap
+    extern __shared__ u64 merge_sm[];
+    u64* cw = merge_sm;               // kCap: the shortlist
+    u64* wl = merge_sm + kCap;        // kMergeWarps x 64: per-warp lists, then the exact keys
+    __shared__ int s_n;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int qi = blockIdx.x * kMergeWarps + warp;
+    const int qi = blockIdx.x;  // one query per block
     if (qi >= nq) return;
-    u64* cw = cand_sm + (size_t)warp * kCap;
     const unsigned c = cand != nullptr ? cnt[qi] : 0u;
-    int n = 0;
-    bool sorted = false;
     if (cand != nullptr && c >= (unsigned)W && c <= (unsigned)kCap && W <= 64) {
-        // the main pass collected every key <= tau, and there are W..kCap of
-        // them: a running 64 smallest in registers, one 64-key chunk at a time
-        // (the next chunk's loads in flight; chunks with nothing below the
-        // current 64th key skipped)
+        // the main pass collected every key <= tau, and there are W..kCap of them: each warp
+        // keeps the 64 smallest of its share of the 64-key chunks (chunk w, w + kMergeWarps, ...;
+        // the next chunk's loads in flight, chunks with nothing below its current 64th skipped),
+        // then warp 0 merges the lists
         const int nc = (int)c;
         const u64* cq = cand + (size_t)qi * kCap;
+        constexpr int kStep = 64 * kMergeWarps;
         u64 best[2] = {kKeyEmpty, kKeyEmpty}, nxt[2];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) nxt[e] = e * 32 + lane < nc ? __ldcg(cq + e * 32 + lane) : kKeyEmpty;
-        for (int base = 0; base < nc; base += 64) {
+        for (int e = 0; e < 2; ++e) {
+            const int i = warp * 64 + e * 32 + lane;
+            nxt[e] = i < nc ? __ldcg(cq + i) : kKeyEmpty;
+        }
+        for (int base = warp * 64; base < nc; base += kStep) {
             u64 cur[2] = {nxt[0], nxt[1]};
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-                const int i = base + 64 + e * 32 + lane;
+                const int i = base + kStep + e * 32 + lane;
                 nxt[e] = i < nc ? __ldcg(cq + i) : kKeyEmpty;
             }
             const u64 worst = __shfl_sync(kFull, best[1], 31);
@@ -1053,56 +1058,68 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_rerank_kernel(
             warp_merge64(best, cur, lane);
         }
 #pragma unroll
-        for (int e = 0; e < 2; ++e) cw[e * 32 + lane] = best[e];
-        n = W;
-        sorted = true;
-    } else if (cand != nullptr && c >= (unsigned)W && c <= (unsigned)kCap) {
-        // the main pass collected every key <= tau, and there are W..kCap of them
-        n = (int)c;
-        for (int i = lane; i < n; i += 32) cw[i] = __ldcg(cand + (size_t)qi * kCap + i);
-    } else {
-        // per-chunk top-W lists of the full pass; every key of the global top W
-        // is <= the smallest chunk's W-th key
-        const u64* P = partial + (size_t)qi * nchunks * W;
-        const int total = nchunks * W;
-        u64 bound = kKeyEmpty;
-        for (int ch = lane; ch < nchunks; ch += 32) {
-            const u64 v = __ldcg(P + (size_t)ch * W + W - 1);
-            bound = v < bound ? v : bound;
-        }
-        bound = warp_min_u64(bound);
-        int cntle = count_le(P, total, bound, lane);
-        if (cntle > kCap) {
-            // many keys near the bound: bisect for the W-th smallest key
-            u64 lo = 0, hi = bound;
-            while (lo < hi) {
-                const u64 mid = lo + (hi - lo) / 2;
-                if (count_le(P, total, mid, lane) >= W) hi = mid;
-                else lo = mid + 1;
+        for (int e = 0; e < 2; ++e) wl[warp * 64 + e * 32 + lane] = best[e];
+        __syncthreads();
+        if (warp == 0) {
+            for (int w = 1; w < kMergeWarps; ++w) {
+                const u64 cur[2] = {wl[w * 64 + lane], wl[w * 64 + 32 + lane]};
+                warp_merge64(best, cur, lane);
             }
-            bound = lo;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) cw[e * 32 + lane] = best[e];
+            if (lane == 0) s_n = W;
         }
-        for (int base = 0; base < total; base += 32) {
-            const int i = base + lane;
-            const u64 key = i < total ? __ldcg(P + i) : kKeyEmpty;
-            const bool take = key != kKeyEmpty && key <= bound;
-            const unsigned m = __ballot_sync(kFull, take);
-            const int pos = n + __popc(m & ((1u << lane) - 1u));
-            if (take && pos < kCap) cw[pos] = key;
-            n += __popc(m);
+    } else if (warp == 0) {
+        int n = 0;
+        if (cand != nullptr && c >= (unsigned)W && c <= (unsigned)kCap) {
+            // the main pass collected every key <= tau, and there are W..kCap of them
+            n = (int)c;
+            for (int i = lane; i < n; i += 32) cw[i] = __ldcg(cand + (size_t)qi * kCap + i);
+        } else {
+            // per-chunk top-W lists of the full pass; every key of the global top W
+            // is <= the smallest chunk's W-th key
+            const u64* P = partial + (size_t)qi * nchunks * W;
+            const int total = nchunks * W;
+            u64 bound = kKeyEmpty;
+            for (int ch = lane; ch < nchunks; ch += 32) {
+                const u64 v = __ldcg(P + (size_t)ch * W + W - 1);
+                bound = v < bound ? v : bound;
+            }
+            bound = warp_min_u64(bound);
+            int cntle = count_le(P, total, bound, lane);
+            if (cntle > kCap) {
+                // many keys near the bound: bisect for the W-th smallest key
+                u64 lo = 0, hi = bound;
+                while (lo < hi) {
+                    const u64 mid = lo + (hi - lo) / 2;
+                    if (count_le(P, total, mid, lane) >= W) hi = mid;
+                    else lo = mid + 1;
+                }
+                bound = lo;
+            }
+            for (int base = 0; base < total; base += 32) {
+                const int i = base + lane;
+                const u64 key = i < total ? __ldcg(P + i) : kKeyEmpty;
+                const bool take = key != kKeyEmpty && key <= bound;
+                const unsigned m = __ballot_sync(kFull, take);
+                const int pos = n + __popc(m & ((1u << lane) - 1u));
+                if (take && pos < kCap) cw[pos] = key;
+                n += __popc(m);
+            }
+            n = min(n, kCap);
         }
-        n = min(n, kCap);
-    }
-    __syncwarp();
-    if (!sorted) {
+        __syncwarp();
         int p2 = 32;
         while (p2 < n) p2 <<= 1;
         for (int i = n + lane; i < p2; i += 32) cw[i] = kKeyEmpty;
         __syncwarp();
         warp_sort(cw, p2, lane);
+        if (lane == 0) s_n = n;
     }
-    const int take = min(n, W);
-    // FP32 direct re-rank of the shortlist, kInFlight rows in flight
+    __syncthreads();
+    const int take = min(s_n, W);
+    // FP32 direct re-rank of the shortlist: warp w takes kInFlight rows at a time (rows
+    // w * kInFlight + j kMergeWarps kInFlight ..), their keys into wl
     constexpr int kInFlight = CPL <= 2 ? 8 : 4;
     const int D4 = D / 4;
     float4 qv[CPL];
@@ -1112,8 +1129,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_rerank_kernel(
         qv[j] = cc < D4 ? reinterpret_cast<const float4*>(Q + (size_t)qi * D)[cc] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const float2 neg1 = make_float2(-1.f, -1.f);
-    u64 L = kKeyEmpty, thr = kKeyEmpty;
-    for (int i0 = 0; i0 < take; i0 += kInFlight) {
+    for (int i0 = warp * kInFlight; i0 < take; i0 += kMergeWarps * kInFlight) {
         uint32_t r[kInFlight];
         float4 x[kInFlight][CPL];
 #pragma unroll
@@ -1145,24 +1161,30 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_rerank_kernel(
 #pragma unroll
             for (int b = 0; b < kInFlight; ++b) d[b] += __shfl_xor_sync(kFull, d[b], o);
         }
+        if (lane < kInFlight) {
 #pragma unroll
-        for (int b = 0; b < kInFlight; ++b) {
-            if (r[b] == 0xffffffffu) continue;
-            const u64 key = make_key(d[b], r[b]);
-            if (key < thr) {
-                list_insert(L, key, k, lane);
-                thr = __shfl_sync(kFull, L, k - 1);
-            }
+            for (int b = 0; b < kInFlight; ++b)
+                if (b == lane && r[b] != 0xffffffffu) wl[i0 + b] = make_key(d[b], r[b]);
         }
     }
-    if (lane < k) {
-        const size_t o = (size_t)qi * k + lane;
-        if (L == kKeyEmpty) {
-            idx[o] = -1;
-            dist[o] = __int_as_float(0x7f800000);
-        } else {
-            idx[o] = (int64_t)key_row(L);
-            dist[o] = key_dist(L);
+    __syncthreads();
+    if (warp == 0) {
+        // the exact keys sorted; the first k are the answer
+        int p2 = 32;
+        while (p2 < take) p2 <<= 1;
+        for (int i = take + lane; i < p2; i += 32) wl[i] = kKeyEmpty;
+        __syncwarp();
+        warp_sort(wl, p2, lane);
+        if (lane < k) {
+            const size_t o = (size_t)qi * k + lane;
+            const u64 L = lane < take ? wl[lane] : kKeyEmpty;
+            if (L == kKeyEmpty) {
+                idx[o] = -1;
+                dist[o] = __int_as_float(0x7f800000);
+            } else {
+                idx[o] = (int64_t)key_row(L);
+                dist[o] = key_dist(L);
+            }
         }
     }
 }
@@ -1495,9 +1517,9 @@ cudaError_t launch_lowp(const lhr_db* db, const float* q, int nq, bool fp8, int 
     if (e != cudaSuccess) return e;
     const int d4 = db->dim / 4;
     const int cpl = d4 <= 32 ? 1 : (d4 <= 64 ? 2 : 4);
-    const size_t msm = (size_t)kMergeWarps * kCap * sizeof(u64);
+    const size_t msm = (size_t)(kCap + kMergeWarps * 64) * sizeof(u64);
     const u64* candp = pl.sampled ? cand : nullptr;
-    const int blocks = (nq + kMergeWarps - 1) / kMergeWarps;
+    const int blocks = nq;  // one query per block
 #define LHR_MR(C)                                                                                              \
     do {                                                                                                       \
         e = cudaFuncSetAttribute(merge_rerank_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm); \
