@@ -123,21 +123,6 @@ __global__ void many_bound_kernel(ManyParams p) {
     }
 }
 
-// Exact distance sum w (q - x)^2 of row r to frame f, by one warp (lanes split
-// the dimensions; fixed butterfly order).
-__device__ __forceinline__ float warp_exact(const ManyParams& p, int f, uint32_t r, int lane) {
-    float a = 0.f;
-    const float* x = p.X + (size_t)r * p.D;
-    const float* q = p.Q + (size_t)f * p.D;
-    for (int d = lane; d < p.D; d += 32) {
-        const float diff = q[d] - x[d];
-        a = p.w ? fmaf(p.w[d] * diff, diff, a) : fmaf(diff, diff, a);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
-    return a;
-}
-
 // Exact distance of row r (this lane's own row) to frame f, the lane alone
 // (the exhaustive fallback).
 __device__ __forceinline__ float lane_exact(const ManyParams& p, int f, int64_t r) {
@@ -156,18 +141,25 @@ __device__ __forceinline__ float lane_exact(const ManyParams& p, int f, int64_t 
     return a;
 }
 
-// Per frame (one warp): e_k = the k-th smallest candidate e (a running 64
-// smallest keys in registers), then the exact top k of the candidates with
-// e <= e_k + 2 margin; an overflowed buffer falls back to an exhaustive exact
-// pass over the frame (one row per lane).
-__global__ void many_select_kernel(ManyParams p) {
-    const int lane = threadIdx.x & 31;
-    const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// Per frame, one block of kSelWarps warps: e_k = the k-th smallest candidate e
+// (each warp keeps the 64 smallest of its share of the 64-key chunks in
+// registers, warp 0 merges them), then the exact top k of the candidates with
+// e <= e_k + 2 margin (the warps split the candidates; rows re-scored four at a
+// time, each warp keeping its own top k, merged at the end); an overflowed
+// buffer falls back to an exhaustive exact pass over the frame (the warps split
+// the rows, one row per lane).
+constexpr int kSelWarps = 4;
+
+__global__ void __launch_bounds__(kSelWarps * 32) many_select_kernel(ManyParams p) {
+    __shared__ u64 sh[kSelWarps * 64];
+    __shared__ float s_lim;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+    const int f = blockIdx.x;
     if (f >= p.nq) return;
     const unsigned c = __ldcg(p.cnt + f);
-    u64 L = kKeyEmpty;  // exact (distance, row) top k, lane i = i-th
+    u64 L = kKeyEmpty;  // this warp's exact (distance, row) top k, lane i = i-th
     if (c > (unsigned)kMCap) {
-        for (int64_t base = 0; base < p.n; base += 32) {
+        for (int64_t base = (int64_t)warp * 32; base < p.n; base += kSelWarps * 32) {
             const int64_t r = base + lane;
             const u64 key = r < p.n ? make_key(lane_exact(p, f, r), (uint32_t)r) : kKeyEmpty;
             unsigned m = __ballot_sync(kFull, key < __shfl_sync(kFull, L, p.k - 1));
@@ -180,43 +172,113 @@ __global__ void many_select_kernel(ManyParams p) {
     } else {
         const u64* cf = p.cand + (size_t)f * kMCap;
         u64 best[2] = {kKeyEmpty, kKeyEmpty};
-        for (unsigned base = 0; base < c; base += 64) {
+        for (unsigned base = warp * 64u; base < c; base += kSelWarps * 64u) {
             u64 cur[2];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const unsigned i = base + e * 32 + lane;
                 cur[e] = i < c ? __ldcg(cf + i) : kKeyEmpty;
             }
+            const u64 worst = __shfl_sync(kFull, best[1], 31);
+            if (!__any_sync(kFull, cur[0] < worst || cur[1] < worst)) continue;
             warp_sort64(cur, lane);
             warp_merge64(best, cur, lane);
         }
-        // element k - 1 of the sorted 64 (layout e * 32 + lane)
-        const u64 ek = __shfl_sync(kFull, best[(p.k - 1) / 32], (p.k - 1) % 32);
-        const float lim = (c >= (unsigned)p.k && ek != kKeyEmpty) ? orderable_value(ek) + 2.f * p.mg[f]
-                                                                  : __int_as_float(0x7f800000);
-        for (unsigned base = 0; base < c; base += 32) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) sh[warp * 64 + e * 32 + lane] = best[e];
+        __syncthreads();
+        if (warp == 0) {
+            for (int w = 1; w < kSelWarps; ++w) {
+                const u64 cur[2] = {sh[w * 64 + lane], sh[w * 64 + 32 + lane]};
+                warp_merge64(best, cur, lane);
+            }
+            // element k - 1 of the sorted 64 (layout e * 32 + lane)
+            const u64 ek = __shfl_sync(kFull, best[(p.k - 1) / 32], (p.k - 1) % 32);
+            if (lane == 0)
+                s_lim = (c >= (unsigned)p.k && ek != kKeyEmpty) ? orderable_value(ek) + 2.f * p.mg[f]
+                                                               : __int_as_float(0x7f800000);
+        }
+        __syncthreads();
+        const float lim = s_lim;
+        // the frame's q and w in registers (D <= 256: at most 8 values per lane)
+        constexpr int kMaxPer = 8, kRows = 4;
+        const int per = p.D / 32;
+        float qv[kMaxPer], wv[kMaxPer];
+#pragma unroll
+        for (int t = 0; t < kMaxPer; ++t) {
+            const int d = lane + 32 * t;
+            qv[t] = t < per ? p.Q[(size_t)f * p.D + d] : 0.f;
+            wv[t] = t < per ? (p.w ? p.w[d] : 1.f) : 0.f;
+        }
+        for (unsigned base = warp * 32u; base < c; base += kSelWarps * 32u) {
             const unsigned i = base + lane;
             const u64 v = i < c ? __ldcg(cf + i) : kKeyEmpty;
             unsigned m = __ballot_sync(kFull, i < c && orderable_value(v) <= lim);
             while (m) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                const uint32_t r = (uint32_t)__shfl_sync(kFull, v, j);
-                const float d = warp_exact(p, f, r, lane);
-                const u64 key = make_key(d, r);
-                if (key < __shfl_sync(kFull, L, p.k - 1)) list_insert(L, key, p.k, lane);
+                // up to four rows at a time: their loads in flight together, each summed in
+                // the same order (the lane's dimensions in turn, then the butterfly)
+                uint32_t r[kRows];
+                int nr = 0;
+#pragma unroll
+                for (int t = 0; t < kRows; ++t) {
+                    r[t] = 0u;
+                    if (m) {
+                        const int j = __ffs(m) - 1;
+                        m &= m - 1;
+                        r[t] = (uint32_t)__shfl_sync(kFull, v, j);
+                        nr = t + 1;
+                    }
+                }
+                float a[kRows];
+#pragma unroll
+                for (int t = 0; t < kRows; ++t) a[t] = 0.f;
+#pragma unroll
+                for (int u = 0; u < kMaxPer; ++u) {
+                    if (u < per) {
+                        float x[kRows];
+#pragma unroll
+                        for (int t = 0; t < kRows; ++t)
+                            x[t] = t < nr ? __ldg(p.X + (size_t)r[t] * p.D + lane + 32 * u) : 0.f;
+#pragma unroll
+                        for (int t = 0; t < kRows; ++t) {
+                            const float diff = qv[u] - x[t];
+                            a[t] = p.w ? fmaf(wv[u] * diff, diff, a[t]) : fmaf(diff, diff, a[t]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < kRows; ++t) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) a[t] += __shfl_xor_sync(kFull, a[t], o);
+                }
+                for (int t = 0; t < nr; ++t) {
+                    const u64 key = make_key(a[t], r[t]);
+                    if (key < __shfl_sync(kFull, L, p.k - 1)) list_insert(L, key, p.k, lane);
+                }
             }
         }
     }
-    if (lane < p.k) {
-        const size_t o = (size_t)f * p.k + lane;
-        if (L == kKeyEmpty) {
-            p.idx[o] = -1;
-            p.dist[o] = __int_as_float(0x7f800000);
-        } else {
-            const uint32_t r = key_row(L);
-            p.idx[o] = p.perm ? (int64_t)p.perm[r] : (int64_t)r;
-            p.dist[o] = key_dist(L);
+    // the warps' top-k lists merged: 4 x 32 keys, the smallest k
+    __syncthreads();
+    sh[warp * 32 + lane] = lane < p.k ? L : kKeyEmpty;
+    __syncthreads();
+    if (warp == 0) {
+        static_assert(kSelWarps == 4, "four lists of 32");
+        u64 a2[2] = {sh[lane], sh[32 + lane]}, b2[2] = {sh[64 + lane], sh[96 + lane]};
+        warp_sort64(a2, lane);
+        warp_sort64(b2, lane);
+        warp_merge64(a2, b2, lane);
+        if (lane < p.k) {
+            const u64 Lk = a2[0];
+            const size_t o = (size_t)f * p.k + lane;
+            if (Lk == kKeyEmpty) {
+                p.idx[o] = -1;
+                p.dist[o] = __int_as_float(0x7f800000);
+            } else {
+                const uint32_t r = key_row(Lk);
+                p.idx[o] = p.perm ? (int64_t)p.perm[r] : (int64_t)r;
+                p.dist[o] = key_dist(Lk);
+            }
         }
     }
 }
@@ -756,7 +818,7 @@ cudaError_t launch_many(const lhr_db* db, const float* q, int nq, int k, const f
     if ((e = f16_pass<false>(db, nq, t, stream)) != cudaSuccess) return e;
     {
         ProfScope ps("many_select_kernel", stream);
-        many_select_kernel<<<(nq + 7) / 8, 256, 0, stream>>>(p);
+        many_select_kernel<<<nq, kSelWarps * 32, 0, stream>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

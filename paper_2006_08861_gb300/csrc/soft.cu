@@ -168,12 +168,14 @@ __global__ void __launch_bounds__(kSoftThreads) soft_backward_kernel(const SoftA
             const float qj = q[j], wj = __ldg(a.w + j);
             float gq = 0.f, gw = 0.f;
             int s = 0;
-            for (; s + 4 <= a.kc; s += 4) {
-                float x[4];
+            constexpr int kInFlight = 16;  // candidate rows whose loads are in flight together
+            for (; s + kInFlight <= a.kc; s += kInFlight) {
+                float x[kInFlight];
 #pragma unroll
-                for (int v = 0; v < 4; ++v) x[v] = row_s[s + v] >= 0 ? __ldg(a.X + (size_t)row_s[s + v] * D + j) : qj;
+                for (int v = 0; v < kInFlight; ++v)
+                    x[v] = row_s[s + v] >= 0 ? __ldg(a.X + (size_t)row_s[s + v] * D + j) : qj;
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
+                for (int v = 0; v < kInFlight; ++v) {
                     const float diff = qj - x[v];
                     gq = fmaf(dd_s[s + v], diff, gq);
                     gw = fmaf(dd_s[s + v] * diff, diff, gw);
@@ -199,19 +201,35 @@ __global__ void __launch_bounds__(kSoftThreads) soft_backward_kernel(const SoftA
     if (t == 0) a.dtau_part[b] = dtau;
 }
 
-// dw_j = sum over windows (fixed order), dtau likewise (block 0).
+// dw_j = sum over windows, dtau likewise (the last block), in a fixed order:
+// block x sums dimensions 32x .. 32x + 31, its 8 warps each a strided eighth of
+// the windows (window b goes to warp b mod 8), then the 8 partial sums in warp
+// order; the same inputs give the same bits on every run.
+constexpr int kRedSplit = kSoftThreads / 32;
 __global__ void __launch_bounds__(kSoftThreads) soft_reduce_kernel(const double* dw_part, const double* dtau_part,
                                                                    int nw, int D, float* dw, float* dtau) {
-    const int j = blockIdx.x * kSoftThreads + threadIdx.x;
-    if (j < D) {
-        double s = 0.0;
-        for (int b = 0; b < nw; ++b) s += dw_part[(size_t)b * D + j];
-        dw[j] = (float)s;
+    __shared__ double part[kRedSplit][32];
+    const int lane = threadIdx.x & 31, sw = threadIdx.x / 32;
+    const bool tau_block = blockIdx.x == gridDim.x - 1;
+    const int j = blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (tau_block) {
+        for (int b = sw * 32 + lane; b < nw; b += kSoftThreads) s += dtau_part[b];
+    } else if (j < D) {
+        for (int b = sw; b < nw; b += kRedSplit) s += dw_part[(size_t)b * D + j];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        double s = 0.0;
-        for (int b = 0; b < nw; ++b) s += dtau_part[b];
-        *dtau = (float)s;
+    part[sw][lane] = s;
+    __syncthreads();
+    if (sw == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kRedSplit; ++w) t += part[w][lane];
+        if (tau_block) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) *dtau = (float)t;
+        } else if (j < D) {
+            dw[j] = (float)t;
+        }
     }
 }
 
@@ -300,8 +318,8 @@ cudaError_t launch_soft_backward(const lhr_db* db, const float* frames, const in
         soft_backward_kernel<<<nw, kSoftThreads, 0, stream>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    soft_reduce_kernel<<<(db->dim + kSoftThreads - 1) / kSoftThreads, kSoftThreads, 0, stream>>>(
-        a.dw_part, a.dtau_part, nw, db->dim, dw, dtau);
+    soft_reduce_kernel<<<(db->dim + 31) / 32 + 1, kSoftThreads, 0, stream>>>(a.dw_part, a.dtau_part, nw, db->dim, dw,
+                                                                             dtau);
     return cudaGetLastError();
 }
 
