@@ -48,10 +48,12 @@ METRIC = "queries/s and % of HBM/TC roofline, low-precision vs FP32 at recall@kâ
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each workload's dominant
 # kernel, from one ncu capture of the current kernel: hier_fused_kernel on this very workload;
 # scan_topk_kernel on 500,000 x 256 rows (517.4 MB), scaled by rows to the 2,000,000-row launch;
-# tc_main_kernel (FP8) on 1,000,000 x 256 rows (268.1 + 4.8 MB), scaled by rows to 2,000,000.
+# tc_main_kernel (FP8) on 1,000,000 x 256 rows (268.1 + 4.8 MB), scaled by rows to 2,000,000;
+# f16_many_kernel (main pass) on the differentiation workload itself (104.0 + 3.2 MB).
 # Re-measure (or set None) whenever the kernel changes.
 TRAFFIC = {"hierarchical": ("hier_fused_kernel", 14.02e6), "hbm_scan": ("scan_topk_kernel", 4 * 517.4e6),
-           "precision": ("tc_main_kernel", 2 * (268.1e6 + 4.8e6))}
+           "precision": ("tc_main_kernel", 2 * (268.1e6 + 4.8e6)),
+           "differentiation": ("f16_many_kernel", 104.0e6 + 3.2e6)}
 
 
 # ------------------------------------------------------------------ ranks
@@ -1050,7 +1052,8 @@ def run_differentiation(args, rank, world, local):
                 "peak_source": ("FP32 SGEMM 4096^3 with TF32 off (cuBLAS), best of 10, this run"
                                 if f32_meas else "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (derived)"),
                 "peak_derived": round(derived, 1)}
-    roof.update({"unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None, "avg_launch_us": sel_us,
+    traffic = TRAFFIC["differentiation"][1] if sel == TRAFFIC["differentiation"][0] else None
+    roof.update({"unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic, "avg_launch_us": sel_us,
                  "algorithmic_flops_per_launch": flops, "timed_in": kt.get("timed_in", "event pairs recorded inside the timed steps")})
     # gradient check of one window against the FP64 oracle (selection from the GPU)
     loss, fr = step(0)
