@@ -846,12 +846,19 @@ __global__ void tau_kernel(const u64* __restrict__ pilot, int lists, int nq, int
 #pragma unroll
     for (int i = 0; i < kPilotR; ++i) net[i] = kKeyEmpty;
     const u64* pl = pilot + (size_t)q * lists * kPilotR;
-    for (int c = lane; c < lists; c += 32) {
-        u64 kk[kPilotR];
+    // two of this lane's lists per pass: both lists' loads in flight together
+    for (int c = lane; c < lists; c += 64) {
+        u64 kk[2][kPilotR];
 #pragma unroll
-        for (int i = 0; i < kPilotR; ++i) kk[i] = __ldcg(pl + (size_t)c * kPilotR + i);
+        for (int h = 0; h < 2; ++h) {
+            const int ch = c + 32 * h;
 #pragma unroll
-        for (int i = 0; i < kPilotR; ++i) net_insert(net, kk[i]);
+            for (int i = 0; i < kPilotR; ++i) kk[h][i] = ch < lists ? __ldcg(pl + (size_t)ch * kPilotR + i) : kKeyEmpty;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int i = 0; i < kPilotR; ++i) net_insert(net, kk[h][i]);
     }
     u64 tau = kKeyEmpty;
     for (int r = 0; r < kPilotR; ++r) {
@@ -880,6 +887,7 @@ __global__ void tau_kernel(const u64* __restrict__ pilot, int lists, int nq, int
 // tight.
 constexpr int kSortMax = 16384;
 constexpr int kSortThreads = 512;
+constexpr int kRegSort = 1024;  // up to this many keys: the bitonic network mostly in registers
 
 __global__ void __launch_bounds__(kSortThreads) sort_queries_kernel(const float* __restrict__ tau_s, int nq,
                                                                     int n_sorted, const uint4* __restrict__ codes,
@@ -902,19 +910,70 @@ __global__ void __launch_bounds__(kSortThreads) sort_queries_kernel(const float*
             keys[i] = ((u64)u << 32) | (uint32_t)i;
         }
         __syncthreads();
-        for (int size = 2; size <= n2; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = tid; i < n2 / 2; i += blockDim.x) {
-                    const int lo = 2 * i - (i & (stride - 1));
-                    const int hi = lo + stride;
-                    const bool up = (lo & size) == 0;
-                    const u64 x = keys[lo], y = keys[hi];
-                    if ((x > y) == up) {
-                        keys[lo] = y;
-                        keys[hi] = x;
+        if (n2 <= kRegSort) {
+            // 16 warps x 64 keys in registers (element 64 w + 32 e + lane in v[e]; ~0 past n2 sorts
+            // last): strides below 32 by shuffles, 32 within the lane, 64 and up through shared memory
+            static_assert(kSortThreads == 512 && kRegSort == 1024, "16 warps of 64 keys");
+            const int warp = tid / 32, lane = tid % 32;
+            u64 v[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int idx = 64 * warp + 32 * e + lane;
+                v[e] = idx < n2 ? keys[idx] : ~0ull;
+            }
+            for (int size = 2; size <= kRegSort; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    if (stride >= 64) {
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) keys[64 * warp + 32 * e + lane] = v[e];
+                        __syncthreads();
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int idx = 64 * warp + 32 * e + lane;
+                            const u64 o = keys[idx ^ stride];
+                            const bool asc = (idx & size) == 0;
+                            const bool keep_min = (idx < (idx ^ stride)) == asc;
+                            v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
+                        }
+                        __syncthreads();
+                    } else if (stride == 32) {
+                        const bool asc = ((64 * warp + lane) & size) == 0;
+                        const u64 lo = v[0] < v[1] ? v[0] : v[1], hi = v[0] < v[1] ? v[1] : v[0];
+                        v[0] = asc ? lo : hi;
+                        v[1] = asc ? hi : lo;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int idx = 64 * warp + 32 * e + lane;
+                            const u64 o = __shfl_xor_sync(kFull, v[e], stride);
+                            const bool asc = (idx & size) == 0;
+                            const bool keep_min = ((lane & stride) == 0) == asc;
+                            v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
+                        }
                     }
                 }
-                __syncthreads();
+            }
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int idx = 64 * warp + 32 * e + lane;
+                if (idx < n2) keys[idx] = v[e];
+            }
+            __syncthreads();
+        } else {
+            for (int size = 2; size <= n2; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    for (int i = tid; i < n2 / 2; i += blockDim.x) {
+                        const int lo = 2 * i - (i & (stride - 1));
+                        const int hi = lo + stride;
+                        const bool up = (lo & size) == 0;
+                        const u64 x = keys[lo], y = keys[hi];
+                        if ((x > y) == up) {
+                            keys[lo] = y;
+                            keys[hi] = x;
+                        }
+                    }
+                    __syncthreads();
+                }
             }
         }
         for (int i = tid; i < kQTile; i += blockDim.x) {
@@ -943,13 +1002,28 @@ __global__ void __launch_bounds__(kSortThreads) sort_queries_kernel(const float*
 
 // max |q| over the batch into *amax_bits (the bits of a non-negative float
 // order like unsigned integers; *amax_bits zeroed before the launch).
-__global__ void query_amax_kernel(const float* __restrict__ Q, int64_t count, unsigned* __restrict__ amax_bits) {
+__global__ void __launch_bounds__(256) query_amax_kernel(const float* __restrict__ Q, int64_t count,
+                                                          unsigned* __restrict__ amax_bits) {
+    __shared__ float wmax[8];
     float amax = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    // float4 loads when Q is 16-byte aligned (a caller's view may start anywhere), the rest one by one
+    const int64_t count4 = (reinterpret_cast<uintptr_t>(Q) & 15u) == 0 ? count / 4 : 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(Q) + i);
+        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    for (int64_t i = count4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
         amax = fmaxf(amax, fabsf(__ldg(Q + i)));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(kFull, amax, o));
-    if ((threadIdx.x & 31) == 0 && amax > 0.f) atomicMax(amax_bits, __float_as_uint(amax));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x / 32] = amax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) m = fmaxf(m, wmax[w]);
+        if (m > 0.f) atomicMax(amax_bits, __float_as_uint(m));  // one atomic per block
+    }
 }
 
 // The batch's shared query scale from max |q|: s_Q = the smallest power of two
@@ -1367,7 +1441,7 @@ cudaError_t launch_sort_queries(const float* key, int nq, int n_sorted, const vo
     if (n_sorted % kQTile || row_bytes % 16) return cudaErrorInvalidValue;
     int n2 = 1;
     while (n2 < n_sorted) n2 <<= 1;
-    const size_t ssm = n_sorted <= kSortMax ? (size_t)n2 * sizeof(u64) : 0;
+    const size_t ssm = n_sorted <= kSortMax ? (size_t)std::max(n2, kRegSort) * sizeof(u64) : 0;
     cudaError_t e = cudaFuncSetAttribute(sort_queries_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
     if (e != cudaSuccess) return e;
     ProfScope ps("sort_queries_kernel", stream);
