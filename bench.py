@@ -48,11 +48,11 @@ METRIC = "queries/s and % of HBM/TC roofline, low-precision vs FP32 at recall@kâ
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each workload's dominant
 # kernel, from one ncu capture of the current kernel: hier_fused_kernel on this very workload;
 # scan_topk_kernel on 500,000 x 256 rows (517.4 MB), scaled by rows to the 2,000,000-row launch;
-# tc_main_kernel (FP8) on 1,000,000 x 256 rows (268.1 + 4.8 MB), scaled by rows to 2,000,000;
+# tc_main_kernel (FP8) on 1,000,000 x 256 rows (267.0 + 4.9 MB), scaled by rows to 2,000,000;
 # f16_many_kernel (main pass) on the differentiation workload itself (104.0 + 3.2 MB).
 # Re-measure (or set None) whenever the kernel changes.
 TRAFFIC = {"hierarchical": ("hier_fused_kernel", 14.02e6), "hbm_scan": ("scan_topk_kernel", 4 * 517.4e6),
-           "precision": ("tc_main_kernel", 2 * (268.1e6 + 4.8e6)),
+           "precision": ("tc_main_kernel", 2 * (267.0e6 + 4.9e6)),
            "differentiation": ("f16_many_kernel", 104.0e6 + 3.2e6)}
 
 
