@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kSelWarps * 32) many_select_kernel(ManyParams 
 // e = u + ||q_f||_w^2, row) into the frame's stage in shared memory, appended
 // to the frame's buffer at the end with one atomic.
 //
-// kPilot: the same pipeline over every kTfPilotStride-th row (a strided tensor
+// kPilot: the same pipeline over every kF16PilotStride-th row (a strided tensor
 // map, no copy) writes bucket minima instead: per frame and 32 sample rows the
 // smallest e, clamped at 0, into bucket (sample row / 32) mod 128 by atomic
 // minimum. Minima of distinct buckets are distinct rows, each within the margin
@@ -315,9 +315,9 @@ constexpr int kFThreads = 64 + 32 * kFEpiWarps;
 constexpr int kFMaxStages = 14;
 constexpr int kFStage = 16;              // staged candidates per (frame, epilogue half) of the CTA
 constexpr int kFSlice = kFN * kTcSliceBytes;  // 16 KB: one 128-byte K slice of 128 rows
-constexpr int kTfPilotStride = 8;        // pilot sample: every 8th row
+constexpr int kF16PilotStride = 8;        // pilot sample: every 8th row
 
-struct TfParams {
+struct F16Params {
     int64_t n;            // rows of this pass (sample rows for the pilot)
     int slices, stages;   // D / 64; TMA ring depth
     int nacc;             // accumulators (TMEM columns 0, 128, ...)
@@ -337,7 +337,7 @@ struct TfParams {
 };
 
 // Smallest u = fl(xn_j + c v_j) over a group's 32 rows (xn from shared memory).
-__device__ __forceinline__ float tf_min_u(const uint32_t (&v)[32], float c, const float* sxn) {
+__device__ __forceinline__ float f16_min_u(const uint32_t (&v)[32], float c, const float* sxn) {
     const float4* x4 = reinterpret_cast<const float4*>(sxn);
     float mn = __int_as_float(0x7f800000);
 #pragma unroll
@@ -351,10 +351,10 @@ __device__ __forceinline__ float tf_min_u(const uint32_t (&v)[32], float c, cons
 
 // Main pass, one group of 32 rows (the warp's lanes own frames m0 .. m0 + 31):
 // the frames with a passing row, one at a time, through the warp.
-__device__ __forceinline__ void tf_group(const TfParams& p, const uint32_t (&v)[32], const float* sxn, float* tb,
+__device__ __forceinline__ void f16_group(const F16Params& p, const uint32_t (&v)[32], const float* sxn, float* tb,
                                          float c_own, float T_own, float qn_own, unsigned& cnt_own, u64* stage_h,
                                          int m0, int fbase, int64_t row_g0, int lane) {
-    unsigned ev = __ballot_sync(kFull, tf_min_u(v, c_own, sxn) <= T_own);
+    unsigned ev = __ballot_sync(kFull, f16_min_u(v, c_own, sxn) <= T_own);
     const unsigned lt = (1u << lane) - 1u;
     while (ev) {
         const int L = __ffs(ev) - 1;
@@ -390,7 +390,7 @@ __device__ __forceinline__ void tf_group(const TfParams& p, const uint32_t (&v)[
 }
 
 template <bool kPilot>
-__global__ void __launch_bounds__(kFThreads, 1) f16_many_kernel(const __grid_constant__ CUtensorMap tmX, const TfParams p) {
+__global__ void __launch_bounds__(kFThreads, 1) f16_many_kernel(const __grid_constant__ CUtensorMap tmX, const F16Params p) {
     extern __shared__ unsigned char smem_raw[];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int chunk = blockIdx.x, fblock = blockIdx.y;
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(kFThreads, 1) f16_many_kernel(const __grid_con
             if (lane == 0) mbar_arrive(&acc_empty[a]);
             if (kPilot) {
                 const int bucket = (int)((rg >> 5) & (kMBuckets - 1));
-                const float mna = tf_min_u(va, c_own, sxn), mnb = tf_min_u(vb, c_own, sxn + 32);
+                const float mna = f16_min_u(va, c_own, sxn), mnb = f16_min_u(vb, c_own, sxn + 32);
                 if (f < p.nq) {
                     if (mna < inf) atomicMin(p.bmin + (size_t)f * kMBuckets + bucket, __float_as_uint(fmaxf(mna + qn_own, 0.f)));
                     if (mnb < inf)
@@ -587,8 +587,8 @@ __global__ void __launch_bounds__(kFThreads, 1) f16_many_kernel(const __grid_con
                                   __float_as_uint(fmaxf(mnb + qn_own, 0.f)));
                 }
             } else {
-                tf_group(p, va, sxn, tb, c_own, T_own, qn_own, cnt_own, stage_h, m0, fbase, rg, lane);
-                tf_group(p, vb, sxn + 32, tb, c_own, T_own, qn_own, cnt_own, stage_h, m0, fbase, rg + 32, lane);
+                f16_group(p, va, sxn, tb, c_own, T_own, qn_own, cnt_own, stage_h, m0, fbase, rg, lane);
+                f16_group(p, vb, sxn + 32, tb, c_own, T_own, qn_own, cnt_own, stage_h, m0, fbase, rg + 32, lane);
             }
         }
         if (!kPilot) {
@@ -716,12 +716,12 @@ int f16_chunks(int nfb, int sms, int64_t n) {
     return best;
 }
 
-// One pass of f16_many_kernel (the pilot over every kTfPilotStride-th row, or
+// One pass of f16_many_kernel (the pilot over every kF16PilotStride-th row, or
 // the main pass).
 template <bool kPilot>
-cudaError_t f16_pass(const lhr_db* db, int nq, TfParams t, cudaStream_t stream) {
+cudaError_t f16_pass(const lhr_db* db, int nq, F16Params t, cudaStream_t stream) {
     const int D = db->dim;
-    const int64_t stride = kPilot ? kTfPilotStride : 1;
+    const int64_t stride = kPilot ? kF16PilotStride : 1;
     t.n = (db->n + stride - 1) / stride;
     t.xn_stride = stride;
     CUtensorMap tmX;
@@ -797,7 +797,7 @@ cudaError_t launch_many(const lhr_db* db, const float* q, int nq, int k, const f
         f16_prep_kernel<<<(nq + 7) / 8, 256, 0, stream>>>(q, w, nq, db->dim, db->xh_scale, wqh, p.qn, fc, mabs);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    TfParams t{};
+    F16Params t{};
     t.xn = xn;
     t.wqh = reinterpret_cast<const uint32_t*>(wqh);
     t.fc = fc;
