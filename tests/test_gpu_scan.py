@@ -268,6 +268,29 @@ def test_many_frames_tensor_core_filter(lhr, n, dim, nq, k, weighted):
     assert exact >= nq * k // 2  # ranks separated from both neighbours, compared bit-exactly
 
 
+def test_many_frames_wide_dynamic_range(lhr):
+    # dimensions of magnitude 1e-6 .. 1e3 and weights 1e-2 .. 1e2 through the
+    # FP16 tensor-core filter: the power-of-two scales keep the largest values
+    # below FP16's overflow, most small ones fall into its subnormal range, and
+    # the filter's margin (with its subnormal term) must still keep every row of
+    # the exact weighted top k
+    rng = np.random.default_rng(91)
+    n, dim, nq, k = 70_000, 64, 80, 16
+    mag = (10.0 ** rng.uniform(-6, 3, dim)).astype(np.float32)
+    X = (rng.standard_normal((n, dim)) * mag).astype(np.float32)
+    Q = (X[rng.integers(0, n, nq)] + 0.05 * mag * rng.standard_normal((nq, dim))).astype(np.float32)
+    w = (10.0 ** rng.uniform(-2, 2, dim)).astype(np.float32)
+    db = lhr.lhr_build_db(X, np.zeros((n, 2)))
+    gi, gd = lhr.lhr_query_weighted(db, torch.from_numpy(Q).cuda(), k, torch.from_numpy(w).cuda())
+    torch.cuda.synchronize()
+    assert lhr.lhr_db_error(db) == 0
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    oi, od = oret.exhaustive_topk(Q, X, k + 1, w=w)
+    exact = sum(check_list(Q[qi], X, gi[qi, 0], gd[qi, 0], oi[qi, 0], od[qi, 0], k, where=f"q{qi}", w=w)
+                for qi in range(nq))
+    assert exact >= nq * k // 2
+
+
 def test_pilot_and_plain_scan_agree(lhr):
     # lhr_query seeds from the pilot; lhr_query_static never does
     rng = np.random.default_rng(44)
