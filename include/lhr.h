@@ -104,7 +104,11 @@ typedef struct {
  *   cfg      dimensions, coarse prefix, low-precision copies, tile edge.
  *   out      receives the new handle; unchanged on error.
  * The library copies everything it needs; the caller keeps ownership of its
- * inputs. Synchronizes `cuda_stream` before returning.
+ * inputs. Besides the FP32 rows it keeps, for n >= 65,536 rows with D a
+ * multiple of 64 up to 256, an FP16 copy of the rows scaled by a power of two
+ * (n x D x 2 bytes): the operand of the exhaustive form's tensor-core filter
+ * for many frames at once (lhr_query). Synchronizes `cuda_stream` before
+ * returning.
  */
 lhr_status lhr_build_db(const float* feats, const double* xy, const int32_t* subspace, int64_t n,
                         const lhr_db_config* cfg, void* cuda_stream, lhr_db** out);
@@ -130,6 +134,11 @@ lhr_status lhr_db_info(const lhr_db* db, int64_t* n, int32_t* dim, int32_t* coar
  *         subspace).
  *   idx   nq x n_s x k int64 (device): database rows (caller's numbering).
  *   dist  nq x n_s x k float32 (device): squared distances, FP32 direct form.
+ * The exhaustive form over one subspace with 64 to 8,192 frames and k <= 32,
+ * on a database with the FP16 copy, filters on the tensor cores (FP16
+ * operands, a margin that bounds their rounding) and re-scores every row
+ * that can be in a frame's top k in FP32: the same results as the streaming
+ * FP32 scan, which serves the other cases.
  */
 lhr_status lhr_query(const lhr_db* db, const float* q, int32_t nq, const lhr_query_params* p,
                      int64_t* idx, float* dist, void* cuda_stream);
