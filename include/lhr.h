@@ -137,8 +137,8 @@ lhr_status lhr_db_info(const lhr_db* db, int64_t* n, int32_t* dim, int32_t* coar
  * The exhaustive form over one subspace with 64 to 8,192 frames and k <= 32,
  * on a database with the FP16 copy, filters on the tensor cores (FP16
  * operands, a margin that bounds their rounding) and re-scores every row
- * that can be in a frame's top k in FP32: the same results as the streaming
- * FP32 scan, which serves the other cases.
+ * that can be in a frame's top k with the FP32 direct form: the exact FP32
+ * top k, as the streaming FP32 scan (which serves the other cases) returns.
  */
 lhr_status lhr_query(const lhr_db* db, const float* q, int32_t nq, const lhr_query_params* p,
                      int64_t* idx, float* dist, void* cuda_stream);
