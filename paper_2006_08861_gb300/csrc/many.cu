@@ -338,13 +338,19 @@ struct F16Params {
 
 // Smallest u = fl(xn_j + c v_j) over a group's 32 rows (xn from shared memory).
 __device__ __forceinline__ float f16_min_u(const uint32_t (&v)[32], float c, const float* sxn) {
+    // packed pairs: each half is the same correctly rounded fma as fmaf(c, v_j, xn_j)
     const float4* x4 = reinterpret_cast<const float4*>(sxn);
+    const float2 cc = make_float2(c, c);
     float mn = __int_as_float(0x7f800000);
 #pragma unroll
     for (int j4 = 0; j4 < 8; ++j4) {
         const float4 x = x4[j4];
-        mn = fmin3(mn, fmaf(c, __uint_as_float(v[4 * j4]), x.x), fmaf(c, __uint_as_float(v[4 * j4 + 1]), x.y));
-        mn = fmin3(mn, fmaf(c, __uint_as_float(v[4 * j4 + 2]), x.z), fmaf(c, __uint_as_float(v[4 * j4 + 3]), x.w));
+        const float2 u01 = __ffma2_rn(cc, make_float2(__uint_as_float(v[4 * j4]), __uint_as_float(v[4 * j4 + 1])),
+                                      make_float2(x.x, x.y));
+        const float2 u23 = __ffma2_rn(cc, make_float2(__uint_as_float(v[4 * j4 + 2]), __uint_as_float(v[4 * j4 + 3])),
+                                      make_float2(x.z, x.w));
+        mn = fmin3(mn, u01.x, u01.y);
+        mn = fmin3(mn, u23.x, u23.y);
     }
     return mn;
 }
