@@ -49,11 +49,11 @@ METRIC = "queries/s and % of HBM/TC roofline, low-precision vs FP32 at recall@kâ
 # kernel, from one ncu capture of the current kernel: hier_fused_kernel on this very workload;
 # scan_topk_kernel on 500,000 x 256 rows (517.4 MB), scaled by rows to the 2,000,000-row launch;
 # tc_main_kernel (FP8) on 1,000,000 x 256 rows (267.0 + 4.9 MB), scaled by rows to 2,000,000;
-# f16_many_kernel (main pass) on the differentiation workload itself (104.0 + 3.2 MB).
+# f16_many_kernel (main pass) on the differentiation workload itself (104.0 + 3.3 MB).
 # Re-measure (or set None) whenever the kernel changes.
 TRAFFIC = {"hierarchical": ("hier_fused_kernel", 14.02e6), "hbm_scan": ("scan_topk_kernel", 4 * 517.4e6),
            "precision": ("tc_main_kernel", 2 * (267.0e6 + 4.9e6)),
-           "differentiation": ("f16_many_kernel", 104.0e6 + 3.2e6)}
+           "differentiation": ("f16_many_kernel", 104.0e6 + 3.3e6)}
 
 
 # ------------------------------------------------------------------ ranks
