@@ -150,7 +150,7 @@ __device__ __forceinline__ float lane_exact(const ManyParams& p, int f, int64_t 
 // the rows, one row per lane).
 constexpr int kSelWarps = 4;
 
-__global__ void __launch_bounds__(kSelWarps * 32) many_select_kernel(ManyParams p) {
+__global__ void __launch_bounds__(kSelWarps * 32, 10) many_select_kernel(ManyParams p) {
     __shared__ u64 sh[kSelWarps * 64];
     __shared__ float s_lim;
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
@@ -263,11 +263,13 @@ __global__ void __launch_bounds__(kSelWarps * 32) many_select_kernel(ManyParams 
     sh[warp * 32 + lane] = lane < p.k ? L : kKeyEmpty;
     __syncthreads();
     if (warp == 0) {
-        static_assert(kSelWarps == 4, "four lists of 32");
-        u64 a2[2] = {sh[lane], sh[32 + lane]}, b2[2] = {sh[64 + lane], sh[96 + lane]};
-        warp_sort64(a2, lane);
-        warp_sort64(b2, lane);
-        warp_merge64(a2, b2, lane);
+        // each list is sorted (lane i = i-th), so {list, empty} is a sorted 64-key list and the
+        // lists merge pairwise without sorting
+        u64 a2[2] = {sh[lane], kKeyEmpty};
+        for (int w = 1; w < kSelWarps; ++w) {
+            const u64 b2[2] = {sh[w * 32 + lane], kKeyEmpty};
+            warp_merge64(a2, b2, lane);
+        }
         if (lane < p.k) {
             const u64 Lk = a2[0];
             const size_t o = (size_t)f * p.k + lane;
