@@ -130,6 +130,155 @@ __device__ __forceinline__ int init_sorted(const AggParams& p, long long b0, lon
     return C;
 }
 
+// Tile modes (0, 1) of Algorithm 2 for one window of at most 128 candidate
+// slots, by one warp, without sorting (the short form for latency-bound
+// callers): each candidate's tile key goes into a 256-slot open-addressing
+// table in shared memory (one compare-and-swap, linear probing) whose counts
+// are its bins; lane l keeps table slots l + 32 j, j < 8, in registers, and a
+// draw takes the best untaken tile -- count descending, then key ascending,
+// i.e. ty, tx ascending -- by warp reductions (redux.sync), not shuffles.
+// The same draws, circle test, tie rules and outputs as aggregate_warp.
+// `tab` holds 256 keys, `tcnt` 256 counts, `cand_rows` 128 rows.
+__device__ __forceinline__ unsigned tab_hash(u64 k) {
+    return (((unsigned)k * 0x9E3779B1u) ^ ((unsigned)(k >> 32) * 0x85EBCA77u)) >> 24;
+}
+
+__device__ inline void aggregate_warp_small(const AggParams& p, int w, long long b0, long long total, u64* tab,
+                                            unsigned* tcnt, int* cand_rows) {
+    const AggArgs& a = p.a;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        tab[j * 32 + lane] = kKeyEmpty;
+        tcnt[j * 32 + lane] = 0u;
+    }
+    // initialization: rows -> tiles, padding rows skipped, compacted in order
+    int64_t r[4];
+    u64 v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const long long i = e * 32 + lane;
+        r[e] = i < total ? __ldcg(a.idx + b0 + i) : -1;  // may come from another CTA of the launch
+        v[e] = (i < total && p.tile_keys != nullptr) ? __ldcg(p.tile_keys + b0 + i) : kKeyEmpty;
+    }
+    __syncwarp();
+    int C = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const bool bad = r[e] >= p.n;
+        if (bad) record_error(p.err, kErrInvalidArg);
+        const bool take = r[e] >= 0 && !bad;
+        const unsigned m = __ballot_sync(kFull, take);
+        if (take) {
+            cand_rows[C + __popc(m & below)] = (int)r[e];
+            if (p.tile_keys == nullptr) v[e] = tile_key(p.tile[2 * r[e]], p.tile[2 * r[e] + 1]);
+            unsigned slot = tab_hash(v[e]);
+            for (int probe = 0; probe < 256; ++probe) {  // at most 128 keys in 256 slots: a slot is found
+                const u64 old = atomicCAS(reinterpret_cast<unsigned long long*>(tab + slot), kKeyEmpty, v[e]);
+                if (old == kKeyEmpty || old == v[e]) {
+                    atomicAdd(tcnt + slot, 1u);
+                    break;
+                }
+                slot = (slot + 1u) & 255u;
+            }
+        }
+        C += __popc(m);
+    }
+    __syncwarp();
+    if (C == 0) {
+        if (lane == 0) write_invalid(a, w);
+        return;
+    }
+    u64 kk[8];
+    unsigned cc[8], occupied = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        kk[j] = tab[j * 32 + lane];
+        cc[j] = tcnt[j * 32 + lane];
+        occupied += kk[j] != kKeyEmpty ? 1u : 0u;
+    }
+    const int U = (int)__reduce_add_sync(kFull, occupied);
+    const double tm = a.tile_m;
+    int status = 0, win_tx = 0, win_ty = 0, first_tx = 0, first_ty = 0;
+    bool found = false;
+    unsigned taken = 0u;
+    const int ntop = min(a.top_c, U);
+    for (int rr = 0; rr < ntop; ++rr) {
+        unsigned bc = 0u;
+        u64 bk = kKeyEmpty;
+        int bj = -1;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool live = kk[j] != kKeyEmpty && !((taken >> j) & 1u);
+            if (live && (cc[j] > bc || (cc[j] == bc && kk[j] < bk))) {
+                bc = cc[j];
+                bk = kk[j];
+                bj = j;
+            }
+        }
+        const unsigned mc = __reduce_max_sync(kFull, bc);
+        const unsigned hi = __reduce_min_sync(kFull, bc == mc ? (unsigned)(bk >> 32) : 0xffffffffu);
+        const unsigned lo =
+            __reduce_min_sync(kFull, (bc == mc && (unsigned)(bk >> 32) == hi) ? (unsigned)bk : 0xffffffffu);
+        const u64 ks = ((u64)hi << 32) | (u64)lo;
+        if (bj >= 0 && bk == ks) taken |= 1u << bj;  // the table's keys are distinct: one lane holds ks
+        const int tx0 = key_tx(ks), ty0 = key_ty(ks);
+        if (rr == 0) {
+            first_tx = tx0;
+            first_ty = ty0;
+        }
+        unsigned circ = 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (kk[j] == kKeyEmpty) continue;
+            const long long dx = (long long)key_tx(kk[j]) - tx0, dy = (long long)key_ty(kk[j]) - ty0;
+            if (dx > p.rlim || dx < -p.rlim || dy > p.rlim || dy < -p.rlim) continue;
+            if (dx * dx + dy * dy <= a.r2max) circ += cc[j];
+        }
+        circ = __reduce_add_sync(kFull, circ);
+        if (100ll * (long long)circ > (long long)a.toler_pct * (long long)C) {
+            win_tx = tx0;
+            win_ty = ty0;
+            found = true;
+            break;
+        }
+    }
+    if (!found) {
+        win_tx = first_tx;
+        win_ty = first_ty;
+        status = 1;
+    }
+    double ox, oy;
+    if (a.mode == 0) {
+        ox = ((double)win_tx + 0.5) * tm;
+        oy = ((double)win_ty + 0.5) * tm;
+    } else {
+        double sx = 0.0, sy = 0.0;
+        long long m = 0;
+        for (int i = lane; i < C; i += 32) {
+            const int rw = cand_rows[i];
+            const long long dx = (long long)p.tile[2 * rw] - win_tx, dy = (long long)p.tile[2 * rw + 1] - win_ty;
+            if (dx > p.rlim || dx < -p.rlim || dy > p.rlim || dy < -p.rlim) continue;
+            if (dx * dx + dy * dy <= a.r2max) {
+                sx += p.xy[2 * rw];
+                sy += p.xy[2 * rw + 1];
+                ++m;
+            }
+        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        m = warp_sum(m);
+        ox = sx / (double)m;
+        oy = sy / (double)m;
+    }
+    if (lane == 0) {
+        a.xy_out[2 * w] = ox;
+        a.xy_out[2 * w + 1] = oy;
+        a.status[w] = status;
+    }
+}
+
 // Algorithm 2 for one window of at most kWarpCand candidate slots, by a single
 // warp: the same steps, tie rules and integer tests as the block path of
 // aggregate.cu, with warp shuffles in place of block barriers.

@@ -136,9 +136,10 @@ static void free_db(lhr_db* db) {
     if (!db) return;
     void* bufs[] = {db->X, db->xnorm, db->Xc, db->perm, db->iperm, db->xy, db->tile, db->chunks, db->chunk_off,
                     db->Xb, db->snb, db->X8, db->sn8, db->Xb_s, db->snb_s, db->X8_s, db->sn8_s,
-                    db->Xh, db->Xp, db->sub_p, db->err};
+                    db->Xh, db->Xp, db->sub_p, db->err, db->hws};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    delete db->hws_map;
     delete db;
 }
 
@@ -349,6 +350,13 @@ lhr_status lhr_build_db(const float* feats, const double* xy, const int32_t* sub
         (e = cudaMemsetAsync(db->xnorm, 0, ((size_t)n + kSnPad) * sizeof(float), s)) != cudaSuccess)
         return bail(cuda_fail(e, "allocate norms"));
     if (Dc && (e = dalloc(&db->Xc, (size_t)n * Dc)) != cudaSuccess) return bail(cuda_fail(e, "allocate coarse slab"));
+    if (Dc) {
+        const size_t hb = kHierWsBlocks * hier_ws_block_bytes();
+        if ((e = cudaMalloc(&db->hws, hb)) != cudaSuccess || (e = cudaMemsetAsync(db->hws, 0, hb, s)) != cudaSuccess)
+            return bail(cuda_fail(e, "allocate fused-kernel control blocks"));
+        db->hws_map = new (std::nothrow) HierWsMap();
+        if (!db->hws_map) return bail(fail(LHR_ERR_OOM, "host allocation"));
+    }
     if (cfg->lowp & LHR_LOWP_BF16) {
         if ((e = cudaMalloc(&db->Xb, (size_t)n * D * 2)) != cudaSuccess ||
             (e = dalloc(&db->snb, (size_t)n + kSnPad)) != cudaSuccess ||

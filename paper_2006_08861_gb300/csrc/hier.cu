@@ -20,8 +20,11 @@
 //      alone, over the frame's distances; CTAs with no frame leave;
 //   -- a done counter (only the window CTAs wait for it)
 //   D  CTA w runs Algorithm 2 on window w's candidates (one warp).
-// The grid barrier is a global counter and generation word; every wait gives
-// up after kWaitLimitNs and records LHR_ERR_TIMEOUT.
+// The grid barrier is a global arrival counter; every wait gives up after
+// kWaitLimitNs and records LHR_ERR_TIMEOUT. The words that must be zero at the
+// start (histograms, per-frame counters, grid words) sit in a control block
+// that the launch leaves zeroed (hier_leave), so a stream that keeps its block
+// issues no memset before the next launch.
 #include "aggregate.cuh"
 #include "common.cuh"
 #include "internal.h"
@@ -36,9 +39,12 @@ constexpr int kHT = 512;  // threads per CTA
 constexpr int kHW = kHT / 32;
 constexpr int kHBinCap = 4096;
 constexpr int kHMaxShort = 4096;
-constexpr int kHRegion = 80 * 1024;  // shared region reused by every phase
+constexpr int kHStage = 8 * kBins * 4 + 256;  // phase A: offset of the warps' staging buffers in the region
+constexpr int kHRegion = kHStage + kHW * 2 * 32 * 8 * 16;  // shared region reused by every phase
 constexpr int kHCtl = 8;             // control words per frame
 enum { cDirect = 0, cInBin = 1, cRefine = 2, cNeed = 3 };
+static_assert((2 * kHBinCap + kHMaxShort + 32) * 8 + kBins * 4 <= kHRegion, "phase C's arrays fit the region");
+static_assert(kHStage >= 8 * kBins * 4 + 16 * 4 && kHStage % 16 == 0, "staging follows the histograms");
 
 // Coarse digit of a distance d >= 0: 8 exponent bits and the top 5 mantissa
 // bits, i.e. 1/32-octave bins, over 2^-32 .. 2^32; smaller and larger values
@@ -64,9 +70,9 @@ struct HierParams {
     int nf;
     int S, k;
     float* dcbuf;     // nf x n coarse distances
-    unsigned* hist;   // nf x kBins (zeroed)
-    unsigned* ctl;    // nf x kHCtl (zeroed)
-    unsigned* bar;    // grid barrier count, generation; frames done (zeroed)
+    unsigned* hist;   // nf x kBins    } zero when the launch starts,
+    unsigned* ctl;    // nf x kHCtl    } and zero again when it ends
+    unsigned* bar;    // barrier arrivals, abort flag, frames done, CTAs gone }
     u64* bins;        // nf x kHBinCap coarse keys of the boundary rows
     u64* fkb;         // nf x kHBinCap their full keys (same slots)
     u64* fkd;         // nf x kHMaxShort full keys of the direct rows
@@ -79,8 +85,18 @@ struct HierParams {
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// 16-byte asynchronous global -> shared copy (zero-filled when bytes = 0) and
+// its group bookkeeping.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, unsigned bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Bounded grid-wide barrier (all CTAs are co-resident: cooperative launch).
-// bar[0] counts arrivals over the whole launch (zeroed before it); the j-th
+// bar[0] counts arrivals over the whole launch (zero when it starts); the j-th
 // barrier completes when it reaches j * gridDim.x, so the last arrival has
 // nothing more to do.
 __device__ bool grid_sync(unsigned* bar, unsigned& epoch, volatile int* abort_sm, int* err) {
@@ -169,6 +185,22 @@ __device__ __forceinline__ void warp_dist4(const float* X, int D, const float* Q
 #pragma unroll
         for (int i = 0; i < 4; ++i) out[i] += __shfl_xor_sync(kFull, out[i], o);
     }
+}
+
+// Full-feature key of a row whose phase-B queue was full, by its own thread
+// (rare: the queue holds 8 rows per thread).
+__device__ __forceinline__ void rescore_alone(const float* X, const float* q, int D, int64_t row, u64* out) {
+    const float4* xr = reinterpret_cast<const float4*>(X + (size_t)row * D);
+    const float4* qr = reinterpret_cast<const float4*>(q);
+    float a = 0.f;
+    for (int c = 0; c < D / 4; ++c) {
+        const float4 xv = __ldg(xr + c), qv = __ldg(qr + c);
+        a = fmaf(qv.x - xv.x, qv.x - xv.x, a);
+        a = fmaf(qv.y - xv.y, qv.y - xv.y, a);
+        a = fmaf(qv.z - xv.z, qv.z - xv.z, a);
+        a = fmaf(qv.w - xv.w, qv.w - xv.w, a);
+    }
+    *out = make_key(a, (uint32_t)row);
 }
 
 // Writes frame f's final top k: the keys of fk[0, total) that are <= kth
@@ -391,7 +423,7 @@ __device__ void refine_frame(const HierParams& p, int f, unsigned char* region, 
 }
 
 template <int DC4, int CPL>
-__global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) {
+__device__ __forceinline__ void hier_phases(const HierParams& p) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char* region = smem;                                           // kHRegion
     float4* qsc = reinterpret_cast<float4*>(smem + kHRegion);               // 8 frames x DC4
@@ -399,12 +431,44 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
     unsigned* res = fr + 8 * 8;                                             // 4
     unsigned* tmp = res + 4;                                                // kHW
     volatile int* abort_sm = reinterpret_cast<volatile int*>(tmp + kHW);
+    int* woff = reinterpret_cast<int*>(tmp + kHW + 1);  // window blockIdx.x's frame offsets (phase D)
 
     const int t = threadIdx.x, warp = t / 32, lane = t % 32;
     const int nf = p.nf;
     const int64_t per = (p.n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = min(p.n, (int64_t)blockIdx.x * per), r1 = min(p.n, r0 + per);
+    // Phase A's loads go out first, so that their latency overlaps the set-up.
+    // Warp w scores the 32-row blocks r0 + 32 w + i kHT (lane l: row + l),
+    // each in DC4 / 8 units of 8 16-byte chunks per row. A unit is copied
+    // into one of the warp's two staging buffers with coalesced 16-byte
+    // copies (four rows per instruction), chunk c of row r at slot c ^ (r & 7),
+    // so that both the copies and the reads of one row per lane hit distinct
+    // banks; unit u + 2 is in flight while unit u is scored.
+    constexpr int kUnits = DC4 / 8;
+    const int dc4 = p.dc / 4;
+    float4* stg = reinterpret_cast<float4*>(region + kHStage) + warp * 512;
+    const int64_t wrows = r1 - r0 - 32 * warp;
+    const int nunits = wrows > 0 ? (int)((wrows + kHT - 1) / kHT) * kUnits : 0;
+    auto issue = [&](int u) {
+        const int64_t wb = r0 + 32 * warp + (int64_t)(u / kUnits) * kHT;
+        const int blk = (u % kUnits) * 8;
+        float4* buf = stg + (u & 1) * 256;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int rr = 4 * i + lane / 8, c = blk + (lane & 7);
+            const bool ok = wb + rr < r1 && c < dc4;
+            const float* src = ok ? p.Xc + (wb + rr) * p.dc + 4 * c : p.Xc;
+            cp_async16(buf + rr * 8 + ((lane & 7) ^ (rr & 7)), src, ok ? 16u : 0u);
+        }
+        cp_async_commit();
+    };
+    if (nunits > 0) issue(0);
+    if (nunits > 1) issue(1);
     if (t == 0) *abort_sm = 0;
+    if (t == 0 && (int)blockIdx.x < p.ap.a.nw) {  // read now: phase D starts on them
+        woff[0] = __ldg(p.ap.a.offsets + blockIdx.x);
+        woff[1] = __ldg(p.ap.a.offsets + blockIdx.x + 1);
+    }
     unsigned epoch = 0;  // barrier target (same in every thread)
 
     // ------------------------------------------------ A: coarse distances + histograms
@@ -419,7 +483,6 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
         drange[2 * t] = kBins;
         drange[2 * t + 1] = 0u;
     }
-    const int dc4 = p.dc / 4;
     for (int i = t; i < 8 * DC4; i += kHT) {
         const int f = i / DC4, c = i % DC4;
         qsc[i] = (f < nf && c < dc4) ? reinterpret_cast<const float4*>(p.Q + (size_t)f * p.D)[c]
@@ -433,25 +496,42 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
             dlo[f] = kBins;
             dhi[f] = 0u;
         }
-        int slot = 0;
-        for (int64_t row = r0 + t; row < r1; row += kHT, ++slot) {
-            float4 x[DC4];
-            const float4* xr = reinterpret_cast<const float4*>(p.Xc + row * p.dc);
+        float2 acc[8];
+        for (int u = 0; u < nunits; ++u) {
+            const int blk = (u % kUnits) * 8;
+            if (blk == 0) {
 #pragma unroll
-            for (int c = 0; c < DC4; ++c) x[c] = c < dc4 ? __ldg(xr + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int f = 0; f < 8; ++f) acc[f] = f2(0.f, 0.f);
+            }
+            if (u + 1 < nunits) cp_async_wait<1>();
+            else cp_async_wait<0>();
+            __syncwarp();
+            const float4* buf = stg + (u & 1) * 256;
+            float4 x[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) x[c] = buf[lane * 8 + (c ^ (lane & 7))];
+            __syncwarp();
+            if (u + 2 < nunits) issue(u + 2);
 #pragma unroll
             for (int f = 0; f < 8; ++f) {
                 if (f >= nf) break;
-                float2 acc = f2(0.f, 0.f);
 #pragma unroll
-                for (int c = 0; c < DC4; ++c) {
-                    const float4 qv = qsc[f * DC4 + c];
+                for (int c = 0; c < 8; ++c) {
+                    const float4 qv = qsc[f * DC4 + blk + c];
                     const float2 a = __ffma2_rn(f2(x[c].x, x[c].y), f2(-1.f, -1.f), f2(qv.x, qv.y));
                     const float2 b = __ffma2_rn(f2(x[c].z, x[c].w), f2(-1.f, -1.f), f2(qv.z, qv.w));
-                    acc = __ffma2_rn(a, a, acc);
-                    acc = __ffma2_rn(b, b, acc);
+                    acc[f] = __ffma2_rn(a, a, acc[f]);
+                    acc[f] = __ffma2_rn(b, b, acc[f]);
                 }
-                const float d = acc.x + acc.y;
+            }
+            if (blk + 8 < DC4) continue;  // the row's prefix continues in the next unit
+            const int slot = u / kUnits;
+            const int64_t row = r0 + 32 * warp + (int64_t)slot * kHT + lane;
+            if (row >= r1) continue;
+#pragma unroll
+            for (int f = 0; f < 8; ++f) {
+                if (f >= nf) break;
+                const float d = acc[f].x + acc[f].y;
                 p.dcbuf[(size_t)f * p.n + row] = d;
                 if (slot == 0) dreg[0][f] = d;
                 else if (slot == 1) dreg[1][f] = d;
@@ -638,20 +718,8 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
                             q_row[qi] = kept ? (int)row : -1;
                             q_meta[qi] = (slot << 4) | ((unsigned)f << 1) | (unsigned)kind;
                         } else if (kept) {
-                            // queue full: this thread re-scores the row alone
-                            const float4* xr = reinterpret_cast<const float4*>(p.X + (size_t)row * p.D);
-                            const float4* qr = reinterpret_cast<const float4*>(p.Q + (size_t)f * p.D);
-                            float a = 0.f;
-                            for (int c = 0; c < p.D / 4; ++c) {
-                                const float4 xv = __ldg(xr + c), qv = __ldg(qr + c);
-                                a = fmaf(qv.x - xv.x, qv.x - xv.x, a);
-                                a = fmaf(qv.y - xv.y, qv.y - xv.y, a);
-                                a = fmaf(qv.z - xv.z, qv.z - xv.z, a);
-                                a = fmaf(qv.w - xv.w, qv.w - xv.w, a);
-                            }
-                            const u64 key = make_key(a, (uint32_t)row);
-                            if (kind) p.fkb[(size_t)f * kHBinCap + slot] = key;
-                            else p.fkd[(size_t)f * kHMaxShort + slot] = key;
+                            rescore_alone(p.X, p.Q + (size_t)f * p.D, p.D, row,
+                                          kind ? p.fkb + (size_t)f * kHBinCap + slot : p.fkd + (size_t)f * kHMaxShort + slot);
                         }
                     }
                 }
@@ -677,7 +745,11 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
             u64* fk = sk + kHBinCap;                                    // kHMaxShort full keys
             unsigned* hs = reinterpret_cast<unsigned*>(fk + kHMaxShort); // kBins
             u64* outk = reinterpret_cast<u64*>(hs + kBins);             // 32
-            for (unsigned i = t; i < nb; i += kHT) sk[i] = __ldcg(p.bins + (size_t)f * kHBinCap + i);
+            u64* skf = outk + 32;                                       // kHBinCap full keys of sk's rows
+            for (unsigned i = t; i < nb; i += kHT) {
+                sk[i] = __ldcg(p.bins + (size_t)f * kHBinCap + i);
+                skf[i] = __ldcg(p.fkb + (size_t)f * kHBinCap + i);
+            }
             for (unsigned i = t; i < cd; i += kHT) fk[i] = __ldcg(p.fkd + (size_t)f * kHMaxShort + i);
             __syncthreads();
             unsigned total = cd;
@@ -690,7 +762,7 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
                 for (unsigned i = t; i < nb; i += kHT)
                     if (sk[i] <= cstar) {
                         const unsigned pos = atomicAdd(&res[3], 1u);
-                        if (pos < (unsigned)kHMaxShort) fk[pos] = __ldcg(p.fkb + (size_t)f * kHBinCap + i);
+                        if (pos < (unsigned)kHMaxShort) fk[pos] = skf[i];
                     }
                 __syncthreads();
                 total = min(res[3], (unsigned)kHMaxShort);
@@ -698,6 +770,9 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
             }
             select_topk(p, f, fk, total, hs, outk, res, tmp);
         }
+        // the frame's histogram and counters are not read again: zeroed for the next launch
+        for (int i = t; i < kBins; i += kHT) p.hist[(size_t)f * kBins + i] = 0u;
+        if (t < kHCtl) p.ctl[f * kHCtl + t] = 0u;
         __threadfence();  // this frame's idx / dist before the count
         __syncthreads();
         if (t == 0) atomicAdd(&p.bar[2], 1u);  // frame f done
@@ -722,10 +797,15 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
     if (warp == 0) {
         const AggArgs& a = p.ap.a;
         const int w = blockIdx.x;
-        const long long b0 = (long long)a.offsets[w] * a.per_frame, b1 = (long long)a.offsets[w + 1] * a.per_frame;
+        const long long b0 = (long long)woff[0] * a.per_frame, b1 = (long long)woff[1] * a.per_frame;
         const long long total = b1 - b0;
         if (total <= 0 || total > agg::kWarpCand || b0 < 0 || b1 > a.limit) {
             if (lane == 0) agg::write_invalid(a, w);
+        } else if (total <= 128 && a.mode != 2) {
+            u64* tab = reinterpret_cast<u64*>(region);                       // 256
+            unsigned* tcnt = reinterpret_cast<unsigned*>(tab + 256);         // 256
+            int* rows = reinterpret_cast<int*>(tcnt + 256);                  // 128
+            agg::aggregate_warp_small(p.ap, w, b0, total, tab, tcnt, rows);
         } else {
             u64* keys = reinterpret_cast<u64*>(region);                      // kWarpCand
             int* rows = reinterpret_cast<int*>(keys + agg::kWarpCand);       // kWarpCand
@@ -734,6 +814,48 @@ __global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) 
             agg::aggregate_warp(p.ap, w, b0, total, keys, rows, dd, cnt);
         }
     }
+}
+
+// Every CTA leaves through here. The last one to leave re-zeroes the grid
+// words (barrier arrivals, abort flag, frames done, departures); each frame's
+// histogram and counters were re-zeroed by its CTA in phase C, and are zeroed
+// here again after an abort (a CTA may have left before that step). So the
+// control block is all zero when the next launch on it starts.
+__device__ __forceinline__ void hier_leave(const HierParams& p, volatile int* abort_sm, volatile unsigned* flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (*abort_sm) atomicOr(&p.bar[1], 1u);
+        __threadfence();
+        const unsigned gone = atomicAdd(&p.bar[3], 1u) + 1u;
+        unsigned f = 0u;
+        if (gone == gridDim.x) {
+            __threadfence();
+            f = 1u | (atomicOr(&p.bar[1], 0u) ? 2u : 0u);
+        }
+        *flag = f;
+    }
+    __syncthreads();
+    const unsigned f = *flag;
+    if (!(f & 1u)) return;
+    if (f & 2u) {
+        for (int i = threadIdx.x; i < p.nf * kBins; i += kHT) p.hist[i] = 0u;
+        for (int i = threadIdx.x; i < p.nf * kHCtl; i += kHT) p.ctl[i] = 0u;
+    }
+    if (threadIdx.x == 0) {
+        p.bar[0] = 0u;
+        p.bar[1] = 0u;
+        p.bar[2] = 0u;
+        p.bar[3] = 0u;
+    }
+}
+
+template <int DC4, int CPL>
+__global__ void __launch_bounds__(kHT, 1) hier_fused_kernel(const HierParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    // the tail words after fr, res and tmp: abort flag, window offsets (2), leave flag
+    unsigned* tail = reinterpret_cast<unsigned*>(smem + kHRegion + 8 * DC4 * sizeof(float4)) + 8 * 8 + 4 + kHW;
+    hier_phases<DC4, CPL>(p);
+    hier_leave(p, reinterpret_cast<volatile int*>(tail), tail + 3);
 }
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -758,6 +880,7 @@ HierLayout hlayout(const lhr_db* db, int nf) {
 }
 
 size_t hier_smem(int dc4) {
+    // region, frames' prefixes, then fr (64 words), res (4), tmp (kHW), abort flag (1), window offsets (2)
     return kHRegion + (size_t)8 * dc4 * sizeof(float4) + (8 * 8 + 4 + kHW + 4) * sizeof(unsigned);
 }
 
@@ -790,12 +913,46 @@ bool hier_fused_eligible(const lhr_db* db, int nq, int shortlist) {
 
 size_t hier_scratch_bytes(const lhr_db* db, int nq) { return hlayout(db, nq).total; }
 
+// A control block: histograms (8 frames), counters (8 frames), grid words.
+size_t hier_ws_block_bytes() { return a256((size_t)8 * kBins * 4 + (size_t)8 * kHCtl * 4 + 4 * 4); }
+
+// The control block of `stream`: the one it holds, else a free one (taken for
+// the handle's lifetime), else nullptr.
+static unsigned char* hier_ws_block(const lhr_db* db, cudaStream_t stream) {
+    if (db->hws == nullptr || db->hws_map == nullptr) return nullptr;
+    HierWsMap& m = *db->hws_map;
+    std::lock_guard<std::mutex> lk(m.mu);
+    int slot = -1;
+    for (int i = 0; i < kHierWsBlocks && slot < 0; ++i)
+        if (m.used[i] && m.owner[i] == stream) slot = i;
+    for (int i = 0; i < kHierWsBlocks && slot < 0; ++i)
+        if (!m.used[i]) {
+            m.used[i] = true;
+            m.owner[i] = stream;
+            slot = i;
+        }
+    return slot < 0 ? nullptr : db->hws + (size_t)slot * hier_ws_block_bytes();
+}
+
 cudaError_t launch_hier_fused(const lhr_db* db, const float* q, int nq, int shortlist, int k, int64_t* idx,
                               float* dist, const AggArgs* agg_args, void* scratch, cudaStream_t stream) {
     const HierLayout L = hlayout(db, nq);
     unsigned char* base = reinterpret_cast<unsigned char*>(scratch);
-    cudaError_t e = cudaMemsetAsync(base + L.hist, 0, L.zero_end - L.hist, stream);
-    if (e != cudaSuccess) return e;
+    // the words that must be zero at the start: the stream's control block
+    // (left zeroed by the previous launch on it), else scratch and a memset
+    unsigned char* zb = hier_ws_block(db, stream);
+    unsigned *hist, *ctl, *bar;
+    if (zb != nullptr) {
+        hist = reinterpret_cast<unsigned*>(zb);
+        ctl = hist + 8 * kBins;
+        bar = ctl + 8 * kHCtl;
+    } else {
+        cudaError_t e = cudaMemsetAsync(base + L.hist, 0, L.zero_end - L.hist, stream);
+        if (e != cudaSuccess) return e;
+        hist = reinterpret_cast<unsigned*>(base + L.hist);
+        ctl = reinterpret_cast<unsigned*>(base + L.ctl);
+        bar = reinterpret_cast<unsigned*>(base + L.bar);
+    }
     HierParams hp{};
     hp.Xc = db->Xc;
     hp.dc = db->coarse_dim;
@@ -807,9 +964,9 @@ cudaError_t launch_hier_fused(const lhr_db* db, const float* q, int nq, int shor
     hp.S = shortlist;
     hp.k = k;
     hp.dcbuf = reinterpret_cast<float*>(base + L.dcbuf);
-    hp.hist = reinterpret_cast<unsigned*>(base + L.hist);
-    hp.ctl = reinterpret_cast<unsigned*>(base + L.ctl);
-    hp.bar = reinterpret_cast<unsigned*>(base + L.bar);
+    hp.hist = hist;
+    hp.ctl = ctl;
+    hp.bar = bar;
     hp.bins = reinterpret_cast<u64*>(base + L.bins);
     hp.fkd = reinterpret_cast<u64*>(base + L.fkd);
     hp.fkb = reinterpret_cast<u64*>(base + L.fkb);

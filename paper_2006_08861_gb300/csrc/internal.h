@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -15,6 +16,15 @@ constexpr int kSnPad = 256;
 constexpr int kSampleStride = 64;     // pilot sample: every 64th row
 constexpr int kSampleMinRows = 4096;  // sample only databases of at least 64 x 4096 rows
 constexpr int64_t kPilotMinRows = 65536;  // exhaustive-scan pilot sample for databases of at least this many rows
+constexpr int kHierWsBlocks = 8;          // streams that get a persistent control block of the fused kernel
+
+// Which stream holds which control block of the fused coarse-to-fine kernel
+// (the first kHierWsBlocks streams that call it, for the handle's lifetime).
+struct HierWsMap {
+    std::mutex mu;
+    cudaStream_t owner[kHierWsBlocks] = {};
+    bool used[kHierWsBlocks] = {};
+};
 
 struct lhr_db {
     int device = 0;
@@ -78,6 +88,14 @@ struct lhr_db {
     int32_t* sub_p = nullptr;  // n_pilot: subspace of each sample row
 
     int32_t* err = nullptr;  // device error word (lhr_db_error)
+
+    // Control blocks of the fused coarse-to-fine kernel (hier.cu): words that
+    // must be zero when it starts. A block belongs to one stream (hws_map); the
+    // kernel leaves it zeroed, so a call on that stream needs no memset.
+    // kHierWsBlocks x hier_ws_block_bytes(), zeroed at build; nullptr without a
+    // coarse slab. Views of the handle (subspaces) share both pointers.
+    unsigned char* hws = nullptr;
+    HierWsMap* hws_map = nullptr;
 };
 
 namespace lhr {
@@ -138,6 +156,7 @@ struct AggArgs;
 // frames: one cooperative launch (hier.cu).
 bool hier_fused_eligible(const lhr_db* db, int nq, int shortlist);
 size_t hier_scratch_bytes(const lhr_db* db, int nq);
+size_t hier_ws_block_bytes();
 cudaError_t launch_hier_fused(const lhr_db* db, const float* q, int nq, int shortlist, int k, int64_t* idx,
                               float* dist, const AggArgs* agg_args, void* scratch, cudaStream_t stream);
 

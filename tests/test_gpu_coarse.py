@@ -194,3 +194,96 @@ def test_subspaces_coarse_to_fine_papers_experiment_shape(lhr):
     with pytest.raises(lhr.LhrError):
         lhr.lhr_query_window(h, frames, offs, k, shortlist=int(np.bincount(sub).min()) + 1)
     h.close()
+
+
+def test_fused_control_blocks_left_zeroed(lhr):
+    # The fused kernel's zero-initialised words (histograms, per-frame
+    # counters, grid barrier) live in a per-stream control block that each
+    # launch leaves zeroed, in place of a memset before it. Calls in a row on
+    # one stream, calls on more streams than there are blocks (the others take
+    # scratch and a memset), a captured graph replayed several times, and the
+    # two-window form all give the first call's results, bit for bit.
+    cfg = synth.CONFIGS["hierarchical"]
+    db = synth.make_database(40_000, cfg["dim"], seed=1301)
+    h = lhr.lhr_build_db(db.feats, db.xy, coarse_dim=cfg["coarse_dim"])
+    win = synth.make_windows(db, 2, (3, 4), seed=1302)
+    frames = torch.from_numpy(win.frames).cuda()
+    offs = torch.from_numpy(win.offsets).cuda()
+    S, k = cfg["shortlist"], cfg["k"]
+
+    def call(stream=None, out=None):
+        return lhr.lhr_query_window(h, frames, offs, k, shortlist=S, mode="centroid", stream=stream, out=out)
+
+    ref = [t.clone() for t in call()]
+    torch.cuda.synchronize()
+
+    def same(res):
+        for a, b in zip(ref, res):
+            assert torch.equal(a, b)
+
+    for _ in range(4):
+        same(call())
+    streams = [torch.cuda.Stream() for _ in range(12)]
+    outs = []
+    for s in streams:
+        with torch.cuda.stream(s):
+            outs.append(call(stream=s))
+    torch.cuda.synchronize()
+    for res in outs:
+        same(res)
+    for s in streams[:3]:  # again on streams that hold a block
+        with torch.cuda.stream(s):
+            res = call(stream=s)
+        s.synchronize()
+        same(res)
+    out = [torch.empty_like(t) for t in ref]
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        call(stream=side, out=out)  # warm-up outside the capture
+        side.synchronize()
+        with torch.cuda.graph(g, stream=side):
+            call(stream=side, out=out)
+    for _ in range(3):
+        for t in out:
+            t.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        same(out)
+    assert lhr.lhr_db_error(h) == 0
+    # and the first call agrees with the oracle
+    o_idx, o_dist, _ = oret.hierarchical_topk(win.frames, db.feats, cfg["coarse_dim"], S, k + 1)
+    gi, gd = ref[0].cpu().numpy()[:, 0], ref[1].cpu().numpy()[:, 0]
+    checked = 0
+    for f in range(win.frames.shape[0]):
+        if _shortlist_separated(win.frames[f], db.feats, cfg["coarse_dim"], S):
+            check_list(win.frames[f], db.feats, gi[f], gd[f], o_idx[f], o_dist[f], k, where=f"f{f}")
+            checked += 1
+    assert checked >= 1
+    h.close()
+
+
+@pytest.mark.parametrize("k,m", [(20, (3, 4)), (32, (4, 4)), (32, (3, 5))])
+def test_fused_window_draws_against_oracle(lhr, k, m):
+    # Algorithm 2 inside the fused launch, with parameters that make the draws
+    # run past the first tile or fail (status 1: the first tile is kept):
+    # windows of at most 128 candidate slots take the table form, larger ones
+    # the sorting form. Positions and statuses against the oracle's Algorithm 2
+    # on the same candidates.
+    cfg = synth.CONFIGS["hierarchical"]
+    db = synth.make_database(30_000, cfg["dim"], seed=1401)
+    h = lhr.lhr_build_db(db.feats, db.xy, coarse_dim=cfg["coarse_dim"])
+    win = synth.make_windows(db, 2, m, seed=1402 + k)
+    frames = torch.from_numpy(win.frames).cuda()
+    offs = torch.from_numpy(win.offsets).cuda()
+    for mode in ("tile", "centroid"):
+        for kw in (dict(top_c=10, radius_m=3.0, toler_pct=20), dict(top_c=10, radius_m=3.0, toler_pct=100),
+                   dict(top_c=4, radius_m=0.3, toler_pct=30), dict(top_c=1, radius_m=0.0, toler_pct=0)):
+            idx, _, xy, st = lhr.lhr_query_window(h, frames, offs, k, shortlist=cfg["shortlist"], mode=mode, **kw)
+            torch.cuda.synchronize()
+            cands = oret.window_candidates(idx.cpu().numpy()[:, 0], win.offsets)
+            o_xy, o_st = oagg.aggregate_windows(cands, db.xy, mode=mode, **kw)
+            assert np.array_equal(st.cpu().numpy(), o_st), (mode, kw)
+            assert np.max(np.abs(xy.cpu().numpy() - o_xy)) <= XY_ATOL, (mode, kw)
+    assert lhr.lhr_db_error(h) == 0
+    h.close()
