@@ -159,6 +159,15 @@ lhr_status lhr_query(const lhr_db* db, const float* q, int32_t nq, const lhr_que
  *   idx/dist W x n_s x k (device): every frame's candidates, as lhr_query.
  *   xy       nw x 2 float64 (device): the final position of each window.
  *   status   nw int32 (device): LHR_OK, LHR_WARN_LOW_CONFIDENCE or an error.
+ *
+ * Requests of at most 8 frames on the coarse-to-fine FP32 path (this call or
+ * lhr_query) run as one fused launch whose zero-initialised control words
+ * live in the handle, one block per calling stream (the first 8 streams; the
+ * others get a memset of scratch): each launch leaves its block zeroed for
+ * the next. Calls on one stream are ordered, so they never share a block at
+ * the same time. A CUDA graph captured on a stream keeps that stream's block:
+ * two such graphs, or such a graph and direct calls on its capture stream,
+ * must not run concurrently.
  */
 lhr_status lhr_query_window(const lhr_db* db, const float* frames, const int32_t* offsets, int32_t W,
                             int32_t nw, const lhr_query_params* p, const lhr_agg_params* a,
