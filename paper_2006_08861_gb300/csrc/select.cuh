@@ -54,37 +54,60 @@ __device__ void find_bin(const unsigned* hsm, unsigned need, unsigned* out, unsi
     __syncthreads();
 }
 
-// The same search over a histogram in global memory, by one warp: lane l
-// holds bins [64 l, 64 l + 64) in registers (16 loads in flight per lane).
-// Returns (bin, keys below it, keys in it) on every lane; zeros when the
-// histogram holds fewer than `need` keys.
+// The same search over a histogram in global memory, by one warp. The loads
+// are coalesced (instruction i reads bins [128 i, 128 i + 128), lane l four
+// of them: every SM reads the same histogram at once, so the requests per
+// line matter); the 16 chunk totals come from warp reductions, the chunk
+// holding the need-th key from static selects, the lane and bin inside it
+// from one warp scan. Returns (bin, keys below it, keys in it) on every lane;
+// zeros when the histogram holds fewer than `need` keys.
 __device__ __forceinline__ uint3 warp_find_bin(const unsigned* hist, unsigned need, int lane) {
-    static_assert(kBins == 64 * 32, "one lane per 64 bins");
-    const uint4* h4 = reinterpret_cast<const uint4*>(hist) + lane * 16;
+    static_assert(kBins == 16 * 128, "16 chunks of 128 bins");
+    const uint4* h4 = reinterpret_cast<const uint4*>(hist);
     uint4 v[16];
-    unsigned own = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __ldcg(h4 + i * 32 + lane);
+    unsigned c[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) c[i] = __reduce_add_sync(kFull, v[i].x + v[i].y + v[i].z + v[i].w);
+    // the chunk is the last one starting below `need`
+    unsigned run = 0, cbefore = 0;
+    int ci = 0;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        v[i] = __ldcg(h4 + i);
-        own += v[i].x + v[i].y + v[i].z + v[i].w;
+        if (run < need) {
+            ci = i;
+            cbefore = run;
+        }
+        run += c[i];
     }
+    uint4 q = v[0];
+#pragma unroll
+    for (int i = 1; i < 16; ++i)
+        if (i == ci) q = v[i];
+    const unsigned own = q.x + q.y + q.z + q.w;
     unsigned s = own;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned u = __shfl_up_sync(kFull, s, o);
         if (lane >= o) s += u;
     }
-    unsigned before = s - own;
-    const bool mine = before < need && need <= s;
+    const unsigned before = cbefore + s - own;
+    const bool mine = before < need && need <= before + own;
     uint3 out = make_uint3(0u, 0u, 0u);
     if (mine) {
+        const unsigned cq[4] = {q.x, q.y, q.z, q.w};
+        unsigned bj = 0, bb = before, bc = q.x, r = before;
 #pragma unroll
-        for (int i = 0; i < 64; ++i) {
-            const uint4 q = v[i / 4];
-            const unsigned c = (i % 4) == 0 ? q.x : ((i % 4) == 1 ? q.y : ((i % 4) == 2 ? q.z : q.w));
-            if (before < need && need <= before + c) out = make_uint3((unsigned)(lane * 64 + i), before, c);
-            before += c;
+        for (int j = 0; j < 4; ++j) {
+            if (r < need) {
+                bj = (unsigned)j;
+                bb = r;
+                bc = cq[j];
+            }
+            r += cq[j];
         }
+        out = make_uint3((unsigned)(ci * 128 + lane * 4) + bj, bb, bc);
     }
     const unsigned m = __ballot_sync(kFull, mine);
     const int src = m ? __ffs(m) - 1 : 0;
