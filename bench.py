@@ -51,7 +51,7 @@ METRIC = "queries/s and % of HBM/TC roofline, low-precision vs FP32 at recall@kâ
 # tc_main_kernel (FP8) on 1,000,000 x 256 rows (267.0 + 4.9 MB), scaled by rows to 2,000,000;
 # f16_many_kernel (main pass) on the differentiation workload itself (104.0 + 3.3 MB).
 # Re-measure (or set None) whenever the kernel changes.
-TRAFFIC = {"hierarchical": ("hier_fused_kernel", 14.01e6), "hbm_scan": ("scan_topk_kernel", 4 * 517.4e6),
+TRAFFIC = {"hierarchical": ("hier_fused_kernel", 14.03e6), "hbm_scan": ("scan_topk_kernel", 4 * 517.4e6),
            "precision": ("tc_main_kernel", 2 * (267.0e6 + 4.9e6)),
            "differentiation": ("f16_many_kernel", 104.0e6 + 3.3e6)}
 
