@@ -46,12 +46,13 @@ if ROOT not in sys.path:
 METRIC = "queries/s and % of HBM/TC roofline, low-precision vs FP32 at recall@k≥0.999; p99"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each workload's dominant
-# kernel, from one ncu capture of the current kernel: hier_fused_kernel on this very workload;
+# kernel, from one ncu capture of the current kernel (hier_fused_kernel: none since its last
+# change, so its line carries null; 14.03 MB per launch before it, a change with no global traffic);
 # scan_topk_kernel on 500,000 x 256 rows (517.4 MB), scaled by rows to the 2,000,000-row launch;
 # tc_main_kernel (FP8) on 1,000,000 x 256 rows (267.0 + 4.9 MB), scaled by rows to 2,000,000;
 # f16_many_kernel (main pass) on the differentiation workload itself (104.0 + 3.3 MB).
 # Re-measure (or set None) whenever the kernel changes.
-TRAFFIC = {"hierarchical": ("hier_fused_kernel", 14.03e6), "hbm_scan": ("scan_topk_kernel", 4 * 517.4e6),
+TRAFFIC = {"hbm_scan": ("scan_topk_kernel", 4 * 517.4e6),
            "precision": ("tc_main_kernel", 2 * (267.0e6 + 4.9e6)),
            "differentiation": ("f16_many_kernel", 104.0e6 + 3.3e6)}
 

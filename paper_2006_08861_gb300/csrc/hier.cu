@@ -641,30 +641,49 @@ __device__ __forceinline__ void hier_phases(const HierParams& p) {
             // list << 15 | rank of the row among the warp's appends to that list
             unsigned code[2][8];
             float dv[2][8];  // coarse distances of the two rows
+            // membership first, without warp votes: bit 8 i + f of dm (direct) / bm (boundary)
+            unsigned dm = 0u, bm = 0u;
 #pragma unroll
             for (int f = 0; f < 8; ++f) {
-                unsigned mdv[2], mbv[2];
+                if (f >= nf) break;
+                const bool refine = fr[f * 8 + 4] != 0u;
+                const u64 lo = *reinterpret_cast<const u64*>(&fr[f * 8 + 0]);
+                const u64 hi = *reinterpret_cast<const u64*>(&fr[f * 8 + 2]);
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
                     const int64_t row = base + t + i * kHT;
-                    const bool valid = row < r1;
-                    bool d = false, b = false;
                     dv[i][f] = 0.f;
-                    if (f < nf && !fr[f * 8 + 4] && valid) {
+                    if (!refine && row < r1) {
                         dv[i][f] = in_regs ? dreg[i][f] : __ldcg(p.dcbuf + (size_t)f * p.n + row);
                         const u64 key = ((u64)__float_as_uint(dv[i][f]) << 32) | (u64)row;
-                        const u64 lo = *reinterpret_cast<const u64*>(&fr[f * 8 + 0]);
-                        const u64 hi = *reinterpret_cast<const u64*>(&fr[f * 8 + 2]);
-                        d = take_all || key < lo;
-                        b = !d && key <= hi;
+                        const bool d = take_all || key < lo;
+                        const bool b = !d && key <= hi;
+                        dm |= (d ? 1u : 0u) << (8 * i + f);
+                        bm |= (b ? 1u : 0u) << (8 * i + f);
                     }
-                    mdv[i] = __ballot_sync(kFull, d);
-                    mbv[i] = __ballot_sync(kFull, b);
+                }
+            }
+            // most warps hold no shortlist row at all: then no per-list votes
+            const bool any = __ballot_sync(kFull, (dm | bm) != 0u) != 0u;
+#pragma unroll
+            for (int f = 0; f < 8; ++f) {
+                if (f >= nf) break;
+                unsigned mdv[2] = {0u, 0u}, mbv[2] = {0u, 0u};
+                if (any) {
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        mdv[i] = __ballot_sync(kFull, (dm >> (8 * i + f)) & 1u);
+                        mbv[i] = __ballot_sync(kFull, (bm >> (8 * i + f)) & 1u);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const bool d = (dm >> (8 * i + f)) & 1u, b = (bm >> (8 * i + f)) & 1u;
                     const unsigned pre_d = i ? __popc(mdv[0]) : 0u, pre_b = i ? __popc(mbv[0]) : 0u;
                     code[i][f] = d ? pre_d + __popc(mdv[i] & below)
                                    : (b ? 0x8000u | (pre_b + __popc(mbv[i] & below)) : 0xffffu);
                 }
-                if (lane == 0 && f < nf) {
+                if (lane == 0) {
                     wcnt[(2 * f) * kHW + warp] = __popc(mdv[0]) + __popc(mdv[1]);
                     wcnt[(2 * f + 1) * kHW + warp] = __popc(mbv[0]) + __popc(mbv[1]);
                 }
